@@ -1,0 +1,185 @@
+/*
+ * cil.h -- C ABI of the GB300 point-cloud hot path: k-nearest-neighbour and
+ * radius search over a uniform grid, PCA surface normals, and rigid
+ * point-to-plane ICP.
+ *
+ * The operations follow the cilantro paper (Zampogiannis, Fermueller,
+ * Aloimonos, ACM MM 2018):
+ *   - Sec. 3 "Core operations": k-NN, radius and hybrid queries on a point set;
+ *     surface normal and curvature estimation; PCA;
+ *   - Sec. 3 "Iterative geometric registration": the ICP loop alternating
+ *     correspondence search and a rigid point-to-plane estimator (Low 2004);
+ *   - Sec. 4: 10-NN normal neighbourhoods with viewpoint-consistent
+ *     orientation; ICP with a fixed iteration count and a rejection distance.
+ *
+ * Common conventions
+ *   Points      const float xyz[n][3], x/y/z interleaved, one point after the
+ *               other (the paper's contiguous "one point per column" matrix
+ *               view, Sec. 2).  All point and output arrays are DEVICE pointers
+ *               owned by the caller unless the comment says "host".
+ *   Indices     int32, relative to the reference cloud; n <= 2^31 - 1.
+ *   Ordering    neighbour lists ascend by (squared distance, index): ties in
+ *               FP32 squared distance are broken by the smaller index.
+ *   Distances   squared Euclidean distances in FP32, each coordinate
+ *               difference formed directly (q - p), never via |q|^2 - 2 q.p.
+ *   Transforms  double[16], row-major 4x4 rigid transform mapping SOURCE
+ *               coordinates to TARGET coordinates.
+ *   Streams     every call is enqueued on `stream` (a cudaStream_t passed as
+ *               void*; NULL = legacy default stream).  Calls with host outputs
+ *               synchronise that stream before returning; the others return
+ *               as soon as the work is enqueued.
+ *   Workspace   the library allocates its temporary device memory from its own
+ *               stream-ordered pool on the call's stream and releases it on the
+ *               same stream; nothing persists between calls except handles.
+ *   Errors      argument errors are returned synchronously.  Errors detected
+ *               on the device (non-finite coordinates, a bounded wait that ran
+ *               out) are recorded in a per-device error word: calls that
+ *               synchronise return them; cil_sync_status() returns and clears
+ *               them for the asynchronous calls.  No call falls back to the CPU.
+ */
+#ifndef CIL_H
+#define CIL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CIL_OK = 0,
+  CIL_ERR_INVALID_ARG = 1, /* null pointer, bad size, k out of range, ...   */
+  CIL_ERR_CUDA = 2,        /* a CUDA runtime call failed                      */
+  CIL_ERR_NONFINITE = 3,   /* an input coordinate is NaN or infinite          */
+  CIL_ERR_CAPACITY = 4,    /* output buffer too small (radius search)        */
+  CIL_ERR_DEGENERATE = 5,  /* ICP normal equations singular / < 6 inliers    */
+  CIL_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up              */
+  CIL_ERR_NOMEM = 7        /* device workspace allocation failed              */
+} cil_status;
+
+#define CIL_MAX_K 32
+
+/* Optional tuning knobs (pass NULL for defaults).
+ *   cell_size   > 0: grid cell edge in input units (rounded to the nearest
+ *               power-of-two multiple of the cloud's fine Morton resolution,
+ *               max_extent / 1023); 0: chosen from the data.
+ *   cell_scale  multiplier applied to the data-driven cell size (0 = 1.0).
+ *   block       threads per block of the query kernels (0 = default 128;
+ *               64, 128, 256 accepted). */
+typedef struct {
+  float cell_size;
+  float cell_scale;
+  int block;
+  int reserved;
+} cil_params;
+
+/* Human-readable name of a status code (static storage). */
+const char *cil_status_string(cil_status s);
+
+/* Synchronise `stream`, return the device error word (CIL_OK if clean) and
+ * clear it. */
+cil_status cil_sync_status(void *stream);
+
+/* ---------------------------------------------------------------------------
+ * k nearest neighbours (Sec. 3, KDTree k-NN query; here a uniform grid).
+ *   ref      [n_ref][3]   reference points (device)
+ *   qry      [n_qry][3]   query points (device); may alias ref (self-query: a
+ *                         point is its own first neighbour at distance 0)
+ *   k        1..CIL_MAX_K
+ *   out_idx  [n_qry][k]   int32 neighbour indices into ref (device)
+ *   out_d2   [n_qry][k]   float squared distances (device), may be NULL
+ * Each row ascends by (d2, idx).  When k > n_ref the row is padded with
+ * idx = -1, d2 = +inf.  Exact: the grid search expands until no unvisited
+ * cell can hold a closer point.  n_qry == 0 is a no-op; n_ref == 0 pads.
+ * Asynchronous.
+ */
+cil_status cil_knn(const float *ref, int64_t n_ref, const float *qry, int64_t n_qry, int k,
+                   int32_t *out_idx, float *out_d2, void *stream);
+cil_status cil_knn_ex(const float *ref, int64_t n_ref, const float *qry, int64_t n_qry, int k,
+                      int32_t *out_idx, float *out_d2, const cil_params *params, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Radius search (Sec. 3, KDTree radius query): for every query all reference
+ * points with squared distance <= r*r (inclusive), as CSR:
+ *   out_offsets [n_qry+1] int64 (device): row q is [offsets[q], offsets[q+1])
+ *   out_idx     [capacity] int32 (device), out_d2 [capacity] float (device,
+ *               may be NULL); rows ascend by (d2, idx)
+ *   out_nnz     host int64: total number of neighbours found
+ * If the total exceeds `capacity`, nothing is written to out_idx/out_d2,
+ * out_offsets holds the full CSR offsets, *out_nnz the required size, and the
+ * call returns CIL_ERR_CAPACITY.  r >= 0.  Synchronises the stream.
+ */
+cil_status cil_radius_search(const float *ref, int64_t n_ref, const float *qry, int64_t n_qry,
+                             float r, int64_t *out_offsets, int32_t *out_idx, float *out_d2,
+                             int64_t capacity, int64_t *out_nnz, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * PCA surface normals and curvature (Sec. 3 normal/curvature estimation,
+ * Sec. 4 k-NN neighbourhoods, viewpoint-consistent orientation).
+ *   xyz          [n][3] points (device)
+ *   k            neighbourhood size including the point itself, 1..CIL_MAX_K
+ *   viewpoint    host float[3]; each normal is flipped so that
+ *                normal . (viewpoint - p) >= 0
+ *   out_normals  [n][3] float (device): unit eigenvector of the smallest
+ *                eigenvalue of C = (1/m) sum (p_j - mu)(p_j - mu)^T over the
+ *                m = min(k, n) neighbours
+ *   out_curvature [n] float (device, may be NULL): l0 / (l0 + l1 + l2)
+ * Fewer than 3 neighbours or a zero covariance give NaN normal and curvature.
+ * Asynchronous.
+ */
+cil_status cil_estimate_normals(const float *xyz, int64_t n, int k, const float *viewpoint,
+                                float *out_normals, float *out_curvature, void *stream);
+cil_status cil_estimate_normals_ex(const float *xyz, int64_t n, int k, const float *viewpoint,
+                                   float *out_normals, float *out_curvature,
+                                   const cil_params *params, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Rigid point-to-plane ICP (Sec. 2 ICP base loop; Sec. 3 point-to-plane
+ * estimator after Low 2004; Sec. 4 fixed iterations + rejection distance).
+ * Each of `max_iters` rounds, at the current T:
+ *   p' = R p + t for every source point; q = nearest target point of p';
+ *   the pair is an inlier if |p' - q| <= max_corr_dist and q's normal is
+ *   finite; r = n_q . (p' - q), J = [p' x n_q, n_q];
+ *   H = sum J J^T, g = sum J r (FP32 terms, compensated FP32 sums);
+ *   solve H xi = -g in FP64 (Cholesky), xi = (w, tau);
+ *   T <- [exp(w^), tau; 0 1] * T  (FP64).
+ * A round with < 6 inliers or a Cholesky pivot <= 1e-12 * trace(H) is
+ * skipped and reported as CIL_ERR_DEGENERATE in rep->status.  No early stop.
+ * After the last round one more association pass gives the point-to-plane
+ * RMSE over the inliers.
+ *   src [n_src][3], dst [n_dst][3], dst_normals [n_dst][3]   (device)
+ *   T_init host double[16] (NULL = identity); T_out host double[16]
+ *   rep    host report
+ * Synchronises the stream; returns rep->status's error if the device error
+ * word is set.
+ */
+typedef struct {
+  double rmse;       /* point-to-plane RMSE after the final association   */
+  int64_t n_inliers; /* inliers in the final association                   */
+  int iters_done;    /* rounds executed (== max_iters)                     */
+  int status;        /* CIL_OK or CIL_ERR_DEGENERATE (any round skipped)   */
+} cil_icp_report;
+
+cil_status cil_icp_point_to_plane(const float *src, int64_t n_src, const float *dst,
+                                  const float *dst_normals, int64_t n_dst, const double *T_init,
+                                  int max_iters, float max_corr_dist, double *T_out,
+                                  cil_icp_report *rep, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * One registration of a frame pair, the paper's Sec. 4 pipeline in one call:
+ * build the target grid once, estimate k-NN normals of the target (oriented
+ * to `viewpoint`), then run point-to-plane ICP of `src` against it.
+ * Everything stays on the device; nothing is synchronised:
+ *   out_normals [n_dst][3] float (device, may be NULL: kept internal)
+ *   T_init  device double[16] or NULL (identity)
+ *   T_out   device double[16];  rep  device cil_icp_report
+ */
+cil_status cil_register_pair(const float *src, int64_t n_src, const float *dst, int64_t n_dst,
+                             int k, const float *viewpoint, const double *T_init, int max_iters,
+                             float max_corr_dist, float *out_normals, double *T_out,
+                             cil_icp_report *rep, const cil_params *params, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CIL_H */

@@ -1,0 +1,248 @@
+"""GB300 point-cloud hot path: grid kNN / radius search, PCA normals and
+point-to-plane ICP as sm_103a CUDA kernels behind the C ABI in include/cil.h.
+
+This module is a thin ctypes binding: it checks tensor shapes/devices, passes
+raw device pointers and the current CUDA stream to libcil.so, and turns status
+codes into exceptions.  Every step of the computation runs in the library's
+kernels; there is no CPU path.  If libcil.so is missing it is built with nvcc
+(``paper_1807_00399_gb300.build``); if that is impossible, loading fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = [
+    "CilError", "lib", "knn", "radius_search", "estimate_normals", "icp_point_to_plane",
+    "register_pair", "sync_status", "Params", "STATUS", "MAX_K", "IcpReport",
+]
+
+MAX_K = 32
+STATUS = {
+    0: "CIL_OK", 1: "CIL_ERR_INVALID_ARG", 2: "CIL_ERR_CUDA", 3: "CIL_ERR_NONFINITE",
+    4: "CIL_ERR_CAPACITY", 5: "CIL_ERR_DEGENERATE", 6: "CIL_ERR_TIMEOUT", 7: "CIL_ERR_NOMEM",
+}
+DEGENERATE = 5
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libcil.so")
+_lib = None
+_lock = threading.Lock()
+
+
+class CilError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = int(status)
+        super().__init__(f"{where}: {STATUS.get(self.status, self.status)}")
+
+
+class Params(ctypes.Structure):
+    """cil_params: cell_size (0 = from data), cell_scale (0 = 1.0), block."""
+    _fields_ = [("cell_size", ctypes.c_float), ("cell_scale", ctypes.c_float),
+                ("block", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class IcpReport(ctypes.Structure):
+    _fields_ = [("rmse", ctypes.c_double), ("n_inliers", ctypes.c_int64),
+                ("iters_done", ctypes.c_int), ("status", ctypes.c_int)]
+
+
+def lib():
+    """Load libcil.so (building it first if it is absent or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import build as _build
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        P, I64, I, F = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_float
+        L.cil_status_string.argtypes = [I]
+        L.cil_status_string.restype = ctypes.c_char_p
+        L.cil_sync_status.argtypes = [P]
+        L.cil_knn.argtypes = [P, I64, P, I64, I, P, P, P]
+        L.cil_knn_ex.argtypes = [P, I64, P, I64, I, P, P, P, P]
+        L.cil_radius_search.argtypes = [P, I64, P, I64, F, P, P, P, I64, P, P]
+        L.cil_estimate_normals.argtypes = [P, I64, I, P, P, P, P]
+        L.cil_estimate_normals_ex.argtypes = [P, I64, I, P, P, P, P, P]
+        L.cil_icp_point_to_plane.argtypes = [P, I64, P, P, I64, P, I, F, P, P, P]
+        L.cil_register_pair.argtypes = [P, I64, P, I64, I, P, P, I, F, P, P, P, P, P]
+        for name in ("cil_sync_status", "cil_knn", "cil_knn_ex", "cil_radius_search",
+                     "cil_estimate_normals", "cil_estimate_normals_ex", "cil_icp_point_to_plane",
+                     "cil_register_pair"):
+            getattr(L, name).restype = I
+        _lib = L
+        return L
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _points(t, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32 or t.dim() != 2 or t.shape[1] != 3:
+        raise ValueError(f"{name} must be float32 of shape (N, 3)")
+    return t.contiguous()
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr() if t is not None and t.numel() > 0 else 0)
+
+
+def _check(st, where):
+    if st != 0:
+        raise CilError(st, where)
+
+
+def _params(cell_size=0.0, cell_scale=0.0, block=0):
+    if not (cell_size or cell_scale or block):
+        return None
+    return Params(float(cell_size), float(cell_scale), int(block), 0)
+
+
+# ---------------------------------------------------------------------------
+# public calls
+# ---------------------------------------------------------------------------
+def sync_status(stream=None) -> int:
+    """Synchronise the stream and return (and clear) the device error word."""
+    return int(lib().cil_sync_status(_stream(stream)))
+
+
+def knn(ref, qry, k: int, *, cell_size=0.0, cell_scale=0.0, block=0, with_d2=True, stream=None,
+        out_idx=None, out_d2=None):
+    """k nearest neighbours (cil_knn): (idx int32 (Nq,k), d2 float32 (Nq,k))."""
+    torch = _torch()
+    ref = _points(ref, "ref")
+    same = qry is ref
+    qry = ref if same else _points(qry, "qry")
+    nq = qry.shape[0]
+    if out_idx is None:
+        out_idx = torch.empty((nq, k), dtype=torch.int32, device=qry.device)
+    if with_d2 and out_d2 is None:
+        out_d2 = torch.empty((nq, k), dtype=torch.float32, device=qry.device)
+    prm = _params(cell_size, cell_scale, block)
+    st = lib().cil_knn_ex(_ptr(ref), ref.shape[0], _ptr(qry), nq, int(k), _ptr(out_idx),
+                          _ptr(out_d2) if with_d2 else None,
+                          ctypes.byref(prm) if prm is not None else None, _stream(stream))
+    _check(st, "cil_knn")
+    return out_idx, out_d2
+
+
+def radius_search(ref, qry, r: float, capacity: int | None = None, stream=None):
+    """All neighbours within r (cil_radius_search): CSR (offsets int64, idx
+    int32, d2 float32).  With capacity=None the call is made twice if needed:
+    first to learn the size, then to fill."""
+    torch = _torch()
+    ref = _points(ref, "ref")
+    qry = ref if qry is ref else _points(qry, "qry")
+    nq = qry.shape[0]
+    off = torch.empty(nq + 1, dtype=torch.int64, device=qry.device)
+    cap = int(capacity) if capacity is not None else 0
+    idx = torch.empty(max(cap, 1), dtype=torch.int32, device=qry.device)
+    d2 = torch.empty(max(cap, 1), dtype=torch.float32, device=qry.device)
+    nnz = ctypes.c_int64(0)
+    L = lib()
+    st = L.cil_radius_search(_ptr(ref), ref.shape[0], _ptr(qry), nq, float(r), _ptr(off), _ptr(idx),
+                             _ptr(d2), cap, ctypes.byref(nnz), _stream(stream))
+    if st == 4 and capacity is None:
+        cap = int(nnz.value)
+        idx = torch.empty(max(cap, 1), dtype=torch.int32, device=qry.device)
+        d2 = torch.empty(max(cap, 1), dtype=torch.float32, device=qry.device)
+        st = L.cil_radius_search(_ptr(ref), ref.shape[0], _ptr(qry), nq, float(r), _ptr(off),
+                                 _ptr(idx), _ptr(d2), cap, ctypes.byref(nnz), _stream(stream))
+    _check(st, "cil_radius_search")
+    n = int(nnz.value)
+    return off, idx[:n], d2[:n]
+
+
+def estimate_normals(xyz, k: int, viewpoint, *, cell_size=0.0, cell_scale=0.0, block=0,
+                     stream=None, out_normals=None, out_curvature=None, with_curvature=True):
+    """PCA normals + curvature (cil_estimate_normals)."""
+    torch = _torch()
+    xyz = _points(xyz, "xyz")
+    n = xyz.shape[0]
+    if out_normals is None:
+        out_normals = torch.empty((n, 3), dtype=torch.float32, device=xyz.device)
+    if with_curvature and out_curvature is None:
+        out_curvature = torch.empty(n, dtype=torch.float32, device=xyz.device)
+    vp = (ctypes.c_float * 3)(*[float(v) for v in np.asarray(viewpoint, np.float64).reshape(3)])
+    prm = _params(cell_size, cell_scale, block)
+    st = lib().cil_estimate_normals_ex(_ptr(xyz), n, int(k), vp, _ptr(out_normals),
+                                       _ptr(out_curvature) if with_curvature else None,
+                                       ctypes.byref(prm) if prm is not None else None,
+                                       _stream(stream))
+    _check(st, "cil_estimate_normals")
+    return out_normals, out_curvature
+
+
+def icp_point_to_plane(src, dst, dst_normals, T_init=None, iters: int = 20,
+                       max_corr_dist: float = 0.1, stream=None):
+    """Rigid point-to-plane ICP (cil_icp_point_to_plane).  Returns (T 4x4
+    float64 numpy, report dict).  A degenerate round is reported in
+    report['status'], not raised."""
+    src = _points(src, "src")
+    dst = _points(dst, "dst")
+    nrm = _points(dst_normals, "dst_normals")
+    if nrm.shape != dst.shape:
+        raise ValueError("dst_normals must match dst")
+    T0 = None
+    if T_init is not None:
+        T0 = (ctypes.c_double * 16)(*np.asarray(T_init, np.float64).reshape(16).tolist())
+    Tout = (ctypes.c_double * 16)()
+    rep = IcpReport()
+    st = lib().cil_icp_point_to_plane(_ptr(src), src.shape[0], _ptr(dst), _ptr(nrm), dst.shape[0],
+                                      T0, int(iters), float(max_corr_dist), Tout,
+                                      ctypes.byref(rep), _stream(stream))
+    _check(st, "cil_icp_point_to_plane")
+    return np.array(Tout[:], np.float64).reshape(4, 4), {
+        "rmse": rep.rmse, "n_inliers": int(rep.n_inliers), "iters_done": rep.iters_done,
+        "status": rep.status}
+
+
+def register_pair(src, dst, k: int, viewpoint, iters: int, max_corr_dist: float, *,
+                  T_init=None, out_normals=None, out_T=None, out_report=None, cell_size=0.0,
+                  cell_scale=0.0, block=0, stream=None):
+    """Target grid + k-NN normals + ICP in one enqueue (cil_register_pair).
+    Everything stays on the device: returns (T (16,) float64 CUDA tensor,
+    report (32-byte uint8 CUDA tensor, decode with decode_report), normals)."""
+    torch = _torch()
+    src = _points(src, "src")
+    dst = _points(dst, "dst")
+    dev = dst.device
+    if out_T is None:
+        out_T = torch.empty(16, dtype=torch.float64, device=dev)
+    if out_report is None:
+        out_report = torch.empty(ctypes.sizeof(IcpReport), dtype=torch.uint8, device=dev)
+    vp = (ctypes.c_float * 3)(*[float(v) for v in np.asarray(viewpoint, np.float64).reshape(3)])
+    prm = _params(cell_size, cell_scale, block)
+    st = lib().cil_register_pair(_ptr(src), src.shape[0], _ptr(dst), dst.shape[0], int(k), vp,
+                                 _ptr(T_init) if T_init is not None else None, int(iters),
+                                 float(max_corr_dist), _ptr(out_normals), _ptr(out_T),
+                                 _ptr(out_report), ctypes.byref(prm) if prm is not None else None,
+                                 _stream(stream))
+    _check(st, "cil_register_pair")
+    return out_T, out_report, out_normals
+
+
+def decode_report(buf) -> dict:
+    """Decode a cil_icp_report held in a (host or device) uint8 tensor."""
+    raw = bytes(buf.cpu().numpy().tobytes()) if hasattr(buf, "cpu") else bytes(buf)
+    rep = IcpReport.from_buffer_copy(raw[: ctypes.sizeof(IcpReport)])
+    return {"rmse": rep.rmse, "n_inliers": int(rep.n_inliers), "iters_done": rep.iters_done,
+            "status": rep.status}

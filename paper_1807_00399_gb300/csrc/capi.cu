@@ -1,0 +1,270 @@
+// capi.cu -- the exported C ABI (include/cil.h): argument checks, per-device
+// context, stream-ordered workspaces and the enqueue sequences of each call.
+#include <mutex>
+
+#include "cil_host.h"
+#include "cil_kernels.h"
+
+namespace cil {
+
+// ---------------------------------------------------------------------------
+// device context
+// ---------------------------------------------------------------------------
+static std::mutex g_ctx_mu;
+static DeviceCtx g_ctx[64];
+
+DeviceCtx* device_ctx(cil_status* st) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    *st = CIL_ERR_CUDA;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_ctx_mu);
+  DeviceCtx& c = g_ctx[dev];
+  if (c.device == dev) return &c;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    *st = CIL_ERR_CUDA;
+    return nullptr;
+  }
+  int* err = nullptr;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    *st = CIL_ERR_NOMEM;
+    return nullptr;
+  }
+  if (cudaMemset(err, 0, sizeof(int)) != cudaSuccess) {
+    *st = CIL_ERR_CUDA;
+    return nullptr;
+  }
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+    *st = CIL_ERR_CUDA;
+    return nullptr;
+  }
+  uint64_t keep = ~0ull;  // keep freed blocks cached in the pool
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  c.num_sms = sms;
+  c.err = err;
+  c.pool = pool;
+  c.device = dev;
+  return &c;
+}
+
+cil_status Workspace::allocate(DeviceCtx* ctx, cudaStream_t s) {
+  stream_ = s;
+  if (total_ == 0) total_ = 256;
+  if (cudaMallocFromPoolAsync(reinterpret_cast<void**>(&base_), total_, ctx->pool, s) !=
+      cudaSuccess) {
+    base_ = nullptr;
+    cudaGetLastError();
+    return CIL_ERR_NOMEM;
+  }
+  return CIL_OK;
+}
+
+void Workspace::release(cudaStream_t s) {
+  if (base_) cudaFreeAsync(base_, s);
+  base_ = nullptr;
+}
+
+Workspace::~Workspace() {
+  if (base_) cudaFreeAsync(base_, stream_);
+}
+
+static cil_status read_error_word(DeviceCtx* ctx, cudaStream_t s, bool clear) {
+  int v = 0;
+  if (cudaMemcpyAsync(&v, ctx->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return CIL_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CIL_ERR_CUDA;
+  if (v != 0 && clear) {
+    if (cudaMemsetAsync(ctx->err, 0, sizeof(int), s) != cudaSuccess) return CIL_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CIL_ERR_CUDA;
+  }
+  return (cil_status)v;
+}
+
+static bool bad_count(int64_t n) { return n < 0 || n > (int64_t)0x7fffffff; }
+
+static GridOptions grid_options(const cil_params* prm, int k) {
+  GridOptions o;
+  o.k_est = k;
+  if (prm) {
+    o.cell_size = prm->cell_size > 0.0f ? prm->cell_size : 0.0f;
+    o.cell_scale = prm->cell_scale > 0.0f ? prm->cell_scale : 1.0f;
+  }
+  return o;
+}
+
+static int block_of(const cil_params* prm) { return prm && prm->block ? prm->block : 128; }
+
+}  // namespace cil
+
+using namespace cil;
+
+extern "C" {
+
+const char* cil_status_string(cil_status s) {
+  switch (s) {
+    case CIL_OK: return "CIL_OK";
+    case CIL_ERR_INVALID_ARG: return "CIL_ERR_INVALID_ARG";
+    case CIL_ERR_CUDA: return "CIL_ERR_CUDA";
+    case CIL_ERR_NONFINITE: return "CIL_ERR_NONFINITE";
+    case CIL_ERR_CAPACITY: return "CIL_ERR_CAPACITY";
+    case CIL_ERR_DEGENERATE: return "CIL_ERR_DEGENERATE";
+    case CIL_ERR_TIMEOUT: return "CIL_ERR_TIMEOUT";
+    case CIL_ERR_NOMEM: return "CIL_ERR_NOMEM";
+  }
+  return "CIL_ERR_UNKNOWN";
+}
+
+cil_status cil_sync_status(void* stream) {
+  cil_status st = CIL_OK;
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  return read_error_word(ctx, (cudaStream_t)stream, true);
+}
+
+cil_status cil_knn_ex(const float* ref, int64_t n_ref, const float* qry, int64_t n_qry, int k,
+                      int32_t* out_idx, float* out_d2, const cil_params* params, void* stream) {
+  if (k < 1 || k > CIL_MAX_K || bad_count(n_ref) || bad_count(n_qry)) return CIL_ERR_INVALID_ARG;
+  if (n_qry == 0) return CIL_OK;
+  if (!qry || !out_idx || (n_ref > 0 && !ref)) return CIL_ERR_INVALID_ARG;
+  cil_status st = CIL_OK;
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool self = (qry == ref && n_qry == n_ref);
+  Workspace ws;
+  GridPlan gp;
+  grid_plan(gp, ws, n_ref, 1);
+  OrderPlan op;
+  size_t o_order = 0;
+  if (!self) {
+    order_plan(op, ws, n_qry);
+    o_order = ws.reserve(sizeof(int) * (size_t)n_qry);
+  }
+  if ((st = ws.allocate(ctx, s)) != CIL_OK) return st;
+  if ((st = grid_build(gp, ws, ref, nullptr, grid_options(params, k), ctx, s)) != CIL_OK) return st;
+  const GridView g = grid_view(gp, ws);
+  int* order = nullptr;
+  if (!self) {
+    order = ws.at<int>(o_order);
+    if ((st = order_queries(op, ws, qry, nullptr, 1, g.prm, nullptr, order, s)) != CIL_OK) return st;
+  }
+  st = launch_knn(g, qry, n_qry, order, k, out_idx, out_d2, block_of(params), s);
+  ws.release(s);
+  return st;
+}
+
+cil_status cil_knn(const float* ref, int64_t n_ref, const float* qry, int64_t n_qry, int k,
+                   int32_t* out_idx, float* out_d2, void* stream) {
+  return cil_knn_ex(ref, n_ref, qry, n_qry, k, out_idx, out_d2, nullptr, stream);
+}
+
+cil_status cil_estimate_normals_ex(const float* xyz, int64_t n, int k, const float* viewpoint,
+                                   float* out_normals, float* out_curvature,
+                                   const cil_params* params, void* stream) {
+  if (k < 1 || k > CIL_MAX_K || bad_count(n) || !viewpoint) return CIL_ERR_INVALID_ARG;
+  if (n == 0) return CIL_OK;
+  if (!xyz || !out_normals) return CIL_ERR_INVALID_ARG;
+  cil_status st = CIL_OK;
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace ws;
+  GridPlan gp;
+  grid_plan(gp, ws, n, 1);
+  if ((st = ws.allocate(ctx, s)) != CIL_OK) return st;
+  if ((st = grid_build(gp, ws, xyz, nullptr, grid_options(params, k), ctx, s)) != CIL_OK) return st;
+  st = launch_normals(grid_view(gp, ws), 1, n, k, nullptr, viewpoint, xyz, out_normals,
+                      out_curvature, block_of(params), s);
+  ws.release(s);
+  return st;
+}
+
+cil_status cil_estimate_normals(const float* xyz, int64_t n, int k, const float* viewpoint,
+                                float* out_normals, float* out_curvature, void* stream) {
+  return cil_estimate_normals_ex(xyz, n, k, viewpoint, out_normals, out_curvature, nullptr, stream);
+}
+
+cil_status cil_icp_point_to_plane(const float* src, int64_t n_src, const float* dst,
+                                  const float* dst_normals, int64_t n_dst, const double* T_init,
+                                  int max_iters, float max_corr_dist, double* T_out,
+                                  cil_icp_report* rep, void* stream) {
+  if (bad_count(n_src) || bad_count(n_dst) || max_iters < 0 || !(max_corr_dist >= 0.0f) || !T_out ||
+      !rep)
+    return CIL_ERR_INVALID_ARG;
+  if ((n_src > 0 && !src) || (n_dst > 0 && (!dst || !dst_normals))) return CIL_ERR_INVALID_ARG;
+  cil_status st = CIL_OK;
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace ws;
+  GridPlan gp;
+  grid_plan(gp, ws, n_dst, 1);
+  IcpPlan ip;
+  const int64_t counts[1] = {n_src};
+  icp_plan(ip, ws, counts, 1);
+  const size_t o_out = ws.reserve(sizeof(double) * 16 + sizeof(cil_icp_report));
+  if ((st = ws.allocate(ctx, s)) != CIL_OK) return st;
+  if ((st = grid_build(gp, ws, dst, nullptr, grid_options(nullptr, 10), ctx, s)) != CIL_OK) return st;
+  if ((st = icp_run(ip, ws, grid_view(gp, ws), src, nullptr, dst_normals, nullptr, T_init, max_iters,
+                    nullptr, max_corr_dist, ctx, s)) != CIL_OK)
+    return st;
+  double* Td = ws.at<double>(o_out);
+  cil_icp_report* rd = reinterpret_cast<cil_icp_report*>(Td + 16);
+  if ((st = icp_export(ip, ws, Td, rd, s)) != CIL_OK) return st;
+  struct {
+    double T[16];
+    cil_icp_report r;
+  } h;
+  if (cudaMemcpyAsync(&h, Td, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CIL_ERR_CUDA;
+  ws.release(s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CIL_ERR_CUDA;
+  for (int j = 0; j < 16; ++j) T_out[j] = h.T[j];
+  *rep = h.r;
+  cil_status dev = read_error_word(ctx, s, true);
+  if (dev != CIL_OK) return dev;
+  return CIL_OK;
+}
+
+cil_status cil_register_pair(const float* src, int64_t n_src, const float* dst, int64_t n_dst, int k,
+                             const float* viewpoint, const double* T_init, int max_iters,
+                             float max_corr_dist, float* out_normals, double* T_out,
+                             cil_icp_report* rep, const cil_params* params, void* stream) {
+  if (bad_count(n_src) || bad_count(n_dst) || k < 1 || k > CIL_MAX_K || max_iters < 0 ||
+      !(max_corr_dist >= 0.0f) || !viewpoint || !T_out || !rep)
+    return CIL_ERR_INVALID_ARG;
+  if ((n_src > 0 && !src) || (n_dst > 0 && !dst)) return CIL_ERR_INVALID_ARG;
+  cil_status st = CIL_OK;
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace ws;
+  GridPlan gp;
+  grid_plan(gp, ws, n_dst, 1);
+  IcpPlan ip;
+  const int64_t counts[1] = {n_src};
+  icp_plan(ip, ws, counts, 1);
+  size_t o_nrm = 0;
+  if (!out_normals) o_nrm = ws.reserve(sizeof(float) * 3 * (size_t)(n_dst > 0 ? n_dst : 1));
+  if ((st = ws.allocate(ctx, s)) != CIL_OK) return st;
+  float* nrm = out_normals ? out_normals : ws.at<float>(o_nrm);
+  if ((st = grid_build(gp, ws, dst, nullptr, grid_options(params, k), ctx, s)) != CIL_OK) return st;
+  const GridView g = grid_view(gp, ws);
+  if ((st = launch_normals(g, 1, n_dst, k, nullptr, viewpoint, dst, nrm, nullptr, block_of(params),
+                           s)) != CIL_OK)
+    return st;
+  if ((st = icp_run(ip, ws, g, src, nullptr, nrm, T_init, nullptr, max_iters, nullptr, max_corr_dist,
+                    ctx, s)) != CIL_OK)
+    return st;
+  st = icp_export(ip, ws, T_out, rep, s);
+  ws.release(s);
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,363 @@
+// cil_dev.cuh -- device-side building blocks of the grid index and searches.
+//
+// Spatial index (replaces the paper's kd-tree, Sec. 3 "KDTree"):
+//   * every cloud gets a cubic "fine" lattice over its bounding box with
+//     1024 cells on the longest axis (fine = max_extent / 1023);
+//   * points are sorted (stable LSD radix sort) by the 30-bit Morton code of
+//     their fine cell, with the cloud id above bit 30 in batched mode;
+//   * a search grid of level L uses cells of edge fine * 2^L; each such cell is
+//     a Morton prefix, hence a contiguous run of the sorted points;
+//   * an open-addressing hash table maps (cloud, cell x, y, z) -> (start, count).
+// Searches visit cells in growing Chebyshev shells around the query's cell and
+// stop only when no unvisited cell can hold a closer point (exact results).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cil {
+
+typedef unsigned long long u64;
+
+constexpr u64 kEmptyKey = ~0ull;
+constexpr int kFineBits = 10;          // fine lattice: 1024 cells per axis
+constexpr int kFineDim = 1 << kFineBits;
+
+// Per-cloud parameters, written on the device by the grid build.
+struct GridParams {
+  float o[3];          // origin = bounding-box minimum
+  float fine;          // fine cell edge
+  float inv_fine;      // 1 / fine
+  float eps;           // absolute slack for cell-boundary tests
+  float bmax[3];       // bounding-box maximum
+  int hi_fine[3];      // fine cell index of bmax per axis (<= 1023)
+  int level;           // search-grid level: cell edge = fine * 2^level
+  float cell;          // fine * 2^level
+  int n;               // points of this cloud
+  int start;           // offset of this cloud in the concatenated arrays
+  unsigned bbox_enc[6];// order-preserving integer encodings (min x,y,z, max x,y,z)
+  int nonfinite;       // number of non-finite coordinates seen
+  int pad;
+};
+
+struct __align__(16) CellEntry {
+  u64 key;
+  int start;
+  int count;
+};
+
+// Read-only view of a built grid (passed by value to kernels).
+struct GridView {
+  const GridParams* prm;  // [n_clouds]
+  const float4* pts;      // sorted points: x, y, z, local index (int bits)
+  const CellEntry* tab;   // hash table
+  unsigned mask;          // table size - 1 (power of two)
+};
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned float_to_ordered(float f) {
+  unsigned u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ordered_to_float(unsigned u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// spread the low 10 bits of v so that bit i lands on bit 3i
+__device__ __forceinline__ unsigned spread3(unsigned v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000ffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+__device__ __forceinline__ unsigned compact3(unsigned v) {
+  v &= 0x09249249u;
+  v = (v | (v >> 2)) & 0x030c30c3u;
+  v = (v | (v >> 4)) & 0x0300f00fu;
+  v = (v | (v >> 8)) & 0x030000ffu;
+  v = (v | (v >> 16)) & 0x000003ffu;
+  return v;
+}
+__device__ __forceinline__ unsigned morton3(unsigned x, unsigned y, unsigned z) {
+  return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+}
+
+// fine lattice coordinate of one axis (clamped into [0, 1023]);
+// NaN maps to 0, so corrupt inputs never index out of range
+__device__ __forceinline__ int fine_coord(float v, float o, float inv_fine) {
+  float f = floorf((v - o) * inv_fine);
+  f = fminf(fmaxf(f, 0.0f), (float)(kFineDim - 1));
+  return (int)f;
+}
+
+// 64-bit mixer (MurmurHash3 finaliser)
+__device__ __forceinline__ unsigned hash_key(u64 k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return (unsigned)k;
+}
+
+__device__ __forceinline__ u64 cell_key(int cloud, int x, int y, int z) {
+  return ((u64)(unsigned)cloud << 30) | ((u64)(unsigned)z << 20) | ((u64)(unsigned)y << 10) |
+         (u64)(unsigned)x;
+}
+
+__device__ __forceinline__ bool cell_lookup(const GridView& g, u64 K, int& start, int& count) {
+  unsigned h = hash_key(K) & g.mask;
+  for (unsigned probe = 0; probe <= g.mask; ++probe) {
+    const int4 v = __ldg(reinterpret_cast<const int4*>(g.tab + h));
+    const u64 key = (u64)(unsigned)v.x | ((u64)(unsigned)v.y << 32);
+    if (key == K) {
+      start = v.z;
+      count = v.w;
+      return true;
+    }
+    if (key == kEmptyKey) return false;
+    h = (h + 1) & g.mask;
+  }
+  return false;
+}
+
+// squared distance of two points from exact per-axis differences
+__device__ __forceinline__ float sqdist(float px, float py, float pz, float qx, float qy, float qz) {
+  const float dx = px - qx, dy = py - qy, dz = pz - qz;
+  return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+
+// (squared distance, index) packed so that unsigned order == lexicographic order
+// (squared distances are >= 0, whose IEEE bit patterns are monotone)
+__device__ __forceinline__ u64 pack_key(float d2, int idx) {
+  return ((u64)__float_as_uint(d2) << 32) | (u64)(unsigned)idx;
+}
+__device__ __forceinline__ float key_d2(u64 k) { return __uint_as_float((unsigned)(k >> 32)); }
+__device__ __forceinline__ int key_idx(u64 k) { return (int)(unsigned)(k & 0xffffffffu); }
+
+// squared distance from q to the box [lo, hi] (per axis), 0 inside
+__device__ __forceinline__ float box_d2(const float q[3], const float lo[3], const float hi[3]) {
+  float s = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float d = fmaxf(fmaxf(lo[a] - q[a], q[a] - hi[a]), 0.0f);
+    s = fmaf(d, d, s);
+  }
+  return s;
+}
+
+// Geometry of one cloud's search grid at its level, in registers.
+struct CellFrame {
+  float o[3];
+  float c;      // cell edge
+  float eps;
+  int hi[3];    // largest occupied-range cell index per axis
+  int level;
+  int cloud;
+
+  __device__ __forceinline__ void load(const GridParams& P, int cloud_id) {
+    o[0] = P.o[0];
+    o[1] = P.o[1];
+    o[2] = P.o[2];
+    c = P.cell;
+    eps = P.eps;
+    level = P.level;
+    hi[0] = P.hi_fine[0] >> level;
+    hi[1] = P.hi_fine[1] >> level;
+    hi[2] = P.hi_fine[2] >> level;
+    cloud = cloud_id;
+  }
+  __device__ __forceinline__ int cell_of(float v, int a, float inv_fine) const {
+    int f = fine_coord(v, o[a], inv_fine) >> level;
+    return min(f, hi[a]);
+  }
+  // squared distance from q to the cells [lo_c, hi_c] (inclusive indices),
+  // padded by eps
+  __device__ __forceinline__ float range_d2(const float q[3], const int lo_c[3],
+                                            const int hi_c[3]) const {
+    float lo[3], hh[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = fmaf((float)lo_c[a], c, o[a]) - eps;
+      hh[a] = fmaf((float)(hi_c[a] + 1), c, o[a]) + eps;
+    }
+    return box_d2(q, lo, hh);
+  }
+  // squared distance from q to the part of the grid outside the explored cube
+  // [e0, e1] (cell indices, may exceed the grid); +inf when nothing is left
+  __device__ __forceinline__ float unexplored_d2(const float q[3], const int e0[3],
+                                                 const int e1[3]) const {
+    float best = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      int lo_c[3] = {0, 0, 0};
+      int hi_c[3] = {hi[0], hi[1], hi[2]};
+      if (e0[a] > 0) {  // slab below the explored cube on axis a
+        hi_c[a] = e0[a] - 1;
+        best = fminf(best, range_d2(q, lo_c, hi_c));
+        hi_c[a] = hi[a];
+      }
+      if (e1[a] < hi[a]) {  // slab above
+        lo_c[a] = e1[a] + 1;
+        best = fminf(best, range_d2(q, lo_c, hi_c));
+      }
+    }
+    return best;
+  }
+};
+
+// Iterate (x, y, z) over every cell of the Chebyshev shell of radius r around
+// (cx, cy, cz) that lies in the grid.  Rows on the shell's faces are walked
+// cell by cell, interior rows contribute their two end cells (stride 2r).
+// Written as a loop header/footer pair so the body stays inline and all search
+// state stays in registers; `continue` in the body skips to the next cell.
+#define CIL_SHELL_FOR(f, cx, cy, cz, r, x, y, z)                                      \
+  for (int z = max((cz) - (r), 0), z##_end = min((cz) + (r), (f).hi[2]); z <= z##_end; ++z) \
+    for (int y = max((cy) - (r), 0), y##_end = min((cy) + (r), (f).hi[1]); y <= y##_end; ++y) \
+      for (int x##_edge = (z == (cz) - (r)) || (z == (cz) + (r)) || (y == (cy) - (r)) ||      \
+                          (y == (cy) + (r)),                                                \
+               x = x##_edge ? max((cx) - (r), 0) : (cx) - (r),                              \
+               x##_end = x##_edge ? min((cx) + (r), (f).hi[0]) : (cx) + (r),               \
+               x##_step = x##_edge ? 1 : 2 * (r);                                           \
+           x <= x##_end; x += x##_step)                                                     \
+        if (x >= 0 && x <= (f).hi[0])
+
+// ---------------------------------------------------------------------------
+// register top-k: sorted ascending array of packed (d2, idx) keys
+// ---------------------------------------------------------------------------
+template <int KMAX>
+struct TopK {
+  u64 v[KMAX];
+  u64 thr;  // == v[k-1]: a candidate enters only if its key is smaller
+  int k;
+
+  __device__ __forceinline__ void init(int kk) {
+    k = kk;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) v[j] = kEmptyKey;
+    thr = kEmptyKey;
+  }
+  // branch-free insertion (selects, no predicated stores) so the array stays
+  // in registers; slots j >= k never change
+  __device__ __forceinline__ void push(u64 key) {
+    if (key < thr) {
+#pragma unroll
+      for (int j = KMAX - 1; j > 0; --j) {
+        const u64 prev = v[j - 1];
+        const u64 cur = v[j];
+        const u64 nv = (key < prev) ? prev : ((key < cur) ? key : cur);
+        v[j] = (j < k) ? nv : cur;
+      }
+      v[0] = (key < v[0]) ? key : v[0];
+      u64 t = v[0];
+#pragma unroll
+      for (int j = 1; j < KMAX; ++j) t = (j < k) ? v[j] : t;
+      thr = t;
+    }
+  }
+  __device__ __forceinline__ bool full() const { return thr != kEmptyKey; }
+  __device__ __forceinline__ float thr_d2() const { return key_d2(thr); }
+};
+
+// Exact k nearest neighbours of q among the points of cloud `cloud`.
+template <int KMAX>
+__device__ __forceinline__ void grid_knn(const GridView& g, int cloud, const float q[3], TopK<KMAX>& top,
+                         int* visited_cells = nullptr) {
+  const GridParams& P = g.prm[cloud];
+  CellFrame f;
+  f.load(P, cloud);
+  const float inv_fine = P.inv_fine;
+  const int cx = f.cell_of(q[0], 0, inv_fine);
+  const int cy = f.cell_of(q[1], 1, inv_fine);
+  const int cz = f.cell_of(q[2], 2, inv_fine);
+  const int rmax = max(max(max(cx, f.hi[0] - cx), max(cy, f.hi[1] - cy)), max(cz, f.hi[2] - cz));
+  int nvis = 0;
+  for (int r = 0; r <= rmax; ++r) {
+    CIL_SHELL_FOR(f, cx, cy, cz, r, x, y, z) {
+      if (top.full()) {
+        const int c3[3] = {x, y, z};
+        if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > top.thr_d2()) continue;
+      }
+      int s, n;
+      if (!cell_lookup(g, cell_key(cloud, x, y, z), s, n)) continue;
+      ++nvis;
+      for (int j = s; j < s + n; ++j) {
+        const float4 p = __ldg(g.pts + j);
+        top.push(pack_key(sqdist(p.x, p.y, p.z, q[0], q[1], q[2]), __float_as_int(p.w)));
+      }
+    }
+    if (top.full()) {
+      const int e0[3] = {cx - r, cy - r, cz - r};
+      const int e1[3] = {cx + r, cy + r, cz + r};
+      const float b2 = f.unexplored_d2(q, e0, e1);
+      if (top.thr_d2() < b2 * (1.0f - 1e-6f)) break;
+    }
+  }
+  if (visited_cells) *visited_cells = nvis;
+}
+
+// Exact nearest neighbour of q within squared distance dmax2 (inclusive).
+// Returns the packed key, or kEmptyKey when no point lies within dmax2.
+__device__ __forceinline__ u64 grid_nn(const GridView& g, int cloud, const float q[3], float dmax2) {
+  const GridParams& P = g.prm[cloud];
+  CellFrame f;
+  f.load(P, cloud);
+  const float inv_fine = P.inv_fine;
+  const int cx = f.cell_of(q[0], 0, inv_fine);
+  const int cy = f.cell_of(q[1], 1, inv_fine);
+  const int cz = f.cell_of(q[2], 2, inv_fine);
+  const int rmax = max(max(max(cx, f.hi[0] - cx), max(cy, f.hi[1] - cy)), max(cz, f.hi[2] - cz));
+  u64 best = kEmptyKey;
+  float lim = dmax2;  // min(best d2, dmax2)
+  for (int r = 0; r <= rmax; ++r) {
+    {
+      // the whole shell lies farther than the limit: nothing left to find
+      const int e0[3] = {cx - r + 1, cy - r + 1, cz - r + 1};
+      const int e1[3] = {cx + r - 1, cy + r - 1, cz + r - 1};
+      if (r > 0 && f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim) break;
+    }
+    CIL_SHELL_FOR(f, cx, cy, cz, r, x, y, z) {
+      const int c3[3] = {x, y, z};
+      if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > lim) continue;
+      int s, n;
+      if (!cell_lookup(g, cell_key(cloud, x, y, z), s, n)) continue;
+      for (int j = s; j < s + n; ++j) {
+        const float4 p = __ldg(g.pts + j);
+        const float d2 = sqdist(p.x, p.y, p.z, q[0], q[1], q[2]);
+        if (d2 <= dmax2) {
+          const u64 key = pack_key(d2, __float_as_int(p.w));
+          if (key < best) {
+            best = key;
+            lim = fminf(lim, d2);
+          }
+        }
+      }
+    }
+  }
+  return best;
+}
+
+// ---------------------------------------------------------------------------
+// compensated FP32 summation (error-free TwoSum transformation)
+// ---------------------------------------------------------------------------
+struct KSum {
+  float s, c;
+  __device__ __forceinline__ void zero() { s = c = 0.0f; }
+  __device__ __forceinline__ void add(float x) {
+    const float t = __fadd_rn(s, x);
+    const float bp = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    s = t;
+    c = __fadd_rn(c, e);
+  }
+  __device__ __forceinline__ void merge(float s2, float c2) {
+    add(s2);
+    c = __fadd_rn(c, c2);
+  }
+};
+
+}  // namespace cil

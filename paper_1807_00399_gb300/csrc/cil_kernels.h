@@ -1,0 +1,67 @@
+// cil_kernels.h -- host launchers of the query, normals, ICP and radius kernels.
+#pragma once
+
+#include "cil_host.h"
+
+namespace cil {
+
+cil_status launch_knn(const GridView& g, const float* qry, int64_t nq, const int* order, int k,
+                      int* out_idx, float* out_d2, int block, cudaStream_t s);
+
+// viewpoints: vp_dev (device float[3 * clouds]) or, when null, vp_host[3]
+cil_status launch_normals(const GridView& g, int clouds, int64_t n, int k, const float* vp_dev,
+                          const float* vp_host, const float* xyz, float* out_n, float* out_c,
+                          int block, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// point-to-plane ICP over B pairs (B = 1 for a single registration)
+// ---------------------------------------------------------------------------
+struct Mat4 {
+  double m[16];
+};
+
+struct IcpPairState {
+  double T[16];     // current transform (source -> target), row-major
+  double rmse;      // final point-to-plane RMSE
+  long long n_inl;  // final inlier count
+  float Rt[12];     // T as float rows [R | t] for the association passes
+  float dmax2;      // squared rejection distance
+  int tile_begin, tile_end;
+  int tiles_done;   // tiles of the current round finished
+  int iter_done;    // rounds published (the next round may start)
+  int status;       // CIL_OK or CIL_ERR_DEGENERATE
+  int iters;        // rounds requested
+};
+
+struct IcpPlan {
+  int pairs = 1;
+  int64_t n_src = 0;
+  int n_tiles = 0;
+  int tile = 0;     // source points per tile
+  size_t o_state, o_order, o_tile_off, o_rt, o_part_s, o_part_c, o_part_n, o_work;
+  OrderPlan order;
+};
+
+constexpr int kIcpThreads = 256;
+constexpr int kIcpPPT = 4;
+constexpr int kIcpQ = 28;  // 21 (H upper) + 6 (g) + 1 (sum r^2)
+
+// Reserve workspace; `src_counts` host array of per-pair source sizes.
+void icp_plan(IcpPlan& p, Workspace& ws, const int64_t* src_counts, int pairs);
+
+// Enqueue: order the sources, initialise per-pair state from T_init (device
+// double[16 * pairs], or host double[16] for one pair, or both null =
+// identity) and run all rounds plus the final RMSE pass in one persistent
+// launch.  `src_start_dev`: device int[pairs+1] (null for one pair).
+cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt,
+                   const float* src, const int* src_start_dev, const float* dst_normals,
+                   const double* T_init_dev, const double* T_init_host, int iters,
+                   const float* dmax_dev, float dmax, DeviceCtx* ctx, cudaStream_t s);
+
+IcpPairState* icp_state(const IcpPlan& p, const Workspace& ws);
+
+// copy results of pair b to T_out (device double[16]) and rep (device)
+cil_status icp_export(const IcpPlan& p, const Workspace& ws, double* T_out_dev,
+                      cil_icp_report* rep_dev, cudaStream_t s);
+
+}  // namespace cil

@@ -1,0 +1,314 @@
+// knn.cu -- k-nearest-neighbour queries and fused PCA normals.
+//
+// One thread per query.  Queries are visited in the Morton order of the
+// reference grid (self-queries: the sorted points themselves; external
+// queries: a stable Morton sort of the queries), so the threads of a warp
+// search neighbouring cells and share their loads through L1.  Each thread
+// keeps its k best (squared distance, index) keys sorted in registers.
+//
+// Normals (Sec. 3 normal/curvature estimation, Sec. 4 10-NN neighbourhoods):
+// the k neighbours' offsets from the query give shifted first and second
+// moments, hence the covariance C = (1/m) sum (p - mu)(p - mu)^T; its smallest
+// eigenpair comes from the closed-form trigonometric solution of the
+// characteristic cubic plus a cross product of two rows of C - l0 I.
+#include <math.h>
+
+#include "cil_host.h"
+#include "cil_kernels.h"
+
+namespace cil {
+
+template <int KMAX>
+__global__ void __launch_bounds__(256) k_knn(GridView g, const float* __restrict__ qry, int64_t nq,
+                                             const int* __restrict__ order, int k,
+                                             int* __restrict__ out_idx, float* __restrict__ out_d2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq) return;
+  int64_t qi;
+  float q[3];
+  if (order) {
+    qi = order[i];
+    q[0] = qry[3 * qi];
+    q[1] = qry[3 * qi + 1];
+    q[2] = qry[3 * qi + 2];
+  } else {
+    const float4 p = g.pts[i];
+    qi = __float_as_int(p.w);
+    q[0] = p.x;
+    q[1] = p.y;
+    q[2] = p.z;
+  }
+  TopK<KMAX> top;
+  top.init(k);
+  grid_knn<KMAX>(g, 0, q, top);
+  int* oi = out_idx + qi * k;
+  float* od = out_d2 ? out_d2 + qi * k : nullptr;
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    if (j < k) {
+      const u64 key = top.v[j];
+      const bool none = key == kEmptyKey;
+      oi[j] = none ? -1 : key_idx(key);
+      if (od) od[j] = none ? __int_as_float(0x7f800000) : key_d2(key);
+    }
+  }
+}
+
+// Smallest eigenpair of a symmetric 3x3 (c00, c01, c02, c11, c12, c22).
+// Returns false (and NaN) for a zero matrix.
+__device__ __forceinline__ bool sym3_smallest(const float C[6], float ev[3], float nv[3]) {
+  float s = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) s = fmaxf(s, fabsf(C[j]));
+  if (!(s > 0.0f) || !isfinite(s)) {
+    ev[0] = ev[1] = ev[2] = __int_as_float(0x7fc00000);
+    nv[0] = nv[1] = nv[2] = __int_as_float(0x7fc00000);
+    return false;
+  }
+  const float inv = 1.0f / s;
+  const float a00 = C[0] * inv, a01 = C[1] * inv, a02 = C[2] * inv;
+  const float a11 = C[3] * inv, a12 = C[4] * inv, a22 = C[5] * inv;
+  const float q = (a00 + a11 + a22) * (1.0f / 3.0f);
+  const float b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+  const float p1 = a01 * a01 + a02 * a02 + a12 * a12;
+  const float p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.0f * p1;
+  const float p = sqrtf(p2 * (1.0f / 6.0f));
+  float l0, l1, l2;
+  if (!(p > 1e-30f)) {  // isotropic: every direction is an eigenvector
+    l0 = l1 = l2 = q;
+    nv[0] = 0.0f;
+    nv[1] = 0.0f;
+    nv[2] = 1.0f;
+  } else {
+    const float ip = 1.0f / p;
+    const float B00 = b00 * ip, B11 = b11 * ip, B22 = b22 * ip;
+    const float B01 = a01 * ip, B02 = a02 * ip, B12 = a12 * ip;
+    const float det = B00 * (B11 * B22 - B12 * B12) - B01 * (B01 * B22 - B12 * B02) +
+                      B02 * (B01 * B12 - B11 * B02);
+    const float r = fminf(fmaxf(0.5f * det, -1.0f), 1.0f);
+    const float phi = acosf(r) * (1.0f / 3.0f);
+    l2 = q + 2.0f * p * cosf(phi);
+    l0 = q + 2.0f * p * cosf(phi + 2.0943951023931957f);
+    l1 = 3.0f * q - l0 - l2;
+    // eigenvector of l0: the largest cross product of two rows of A - l0 I
+    // (selects only: no dynamically indexed arrays, everything in registers)
+    const float r0x = a00 - l0, r0y = a01, r0z = a02;
+    const float r1x = a01, r1y = a11 - l0, r1z = a12;
+    const float r2x = a02, r2y = a12, r2z = a22 - l0;
+    const float ax = r0y * r1z - r0z * r1y, ay = r0z * r1x - r0x * r1z, az = r0x * r1y - r0y * r1x;
+    const float bx = r0y * r2z - r0z * r2y, by = r0z * r2x - r0x * r2z, bz = r0x * r2y - r0y * r2x;
+    const float cx = r1y * r2z - r1z * r2y, cy = r1z * r2x - r1x * r2z, cz = r1x * r2y - r1y * r2x;
+    const float ma = ax * ax + ay * ay + az * az;
+    const float mb = bx * bx + by * by + bz * bz;
+    const float mc = cx * cx + cy * cy + cz * cz;
+    float vx = ax, vy = ay, vz = az, best = ma;
+    if (mb > best) {
+      vx = bx;
+      vy = by;
+      vz = bz;
+      best = mb;
+    }
+    if (mc > best) {
+      vx = cx;
+      vy = cy;
+      vz = cz;
+      best = mc;
+    }
+    if (best > 0.0f) {
+      const float in = rsqrtf(best);
+      nv[0] = vx * in;
+      nv[1] = vy * in;
+      nv[2] = vz * in;
+    } else {
+      // A - l0 I has rank <= 1 (l0 = l1): any unit vector orthogonal to its
+      // largest row is an eigenvector of l0
+      const float m0 = r0x * r0x + r0y * r0y + r0z * r0z;
+      const float m1 = r1x * r1x + r1y * r1y + r1z * r1z;
+      const float m2 = r2x * r2x + r2y * r2y + r2z * r2z;
+      float ex = r0x, ey = r0y, ez = r0z, em = m0;
+      if (m1 > em) {
+        ex = r1x;
+        ey = r1y;
+        ez = r1z;
+        em = m1;
+      }
+      if (m2 > em) {
+        ex = r2x;
+        ey = r2y;
+        ez = r2z;
+      }
+      float ux, uy, uz;
+      if (fabsf(ex) <= fabsf(ey) && fabsf(ex) <= fabsf(ez)) {
+        ux = 0.0f;
+        uy = ez;
+        uz = -ey;
+      } else if (fabsf(ey) <= fabsf(ez)) {
+        ux = -ez;
+        uy = 0.0f;
+        uz = ex;
+      } else {
+        ux = ey;
+        uy = -ex;
+        uz = 0.0f;
+      }
+      const float mu = ux * ux + uy * uy + uz * uz;
+      if (mu > 0.0f) {
+        const float in = rsqrtf(mu);
+        nv[0] = ux * in;
+        nv[1] = uy * in;
+        nv[2] = uz * in;
+      } else {
+        nv[0] = 0.0f;
+        nv[1] = 0.0f;
+        nv[2] = 1.0f;
+      }
+    }
+  }
+  ev[0] = l0 * s;
+  ev[1] = l1 * s;
+  ev[2] = l2 * s;
+  return true;
+}
+
+// PCA normal + curvature of one point from its neighbour keys.  `xyz` and the
+// key indices are relative to the same cloud.
+template <int KMAX>
+__device__ __forceinline__ void normal_from_topk(const TopK<KMAX>& top, int k,
+                                                 const float* __restrict__ xyz, const float q[3],
+                                                 const float vp[3], float out_n[3], float& out_c) {
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  float sxx = 0.f, sxy = 0.f, sxz = 0.f, syy = 0.f, syz = 0.f, szz = 0.f;
+  int m = 0;
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    if (j < k && top.v[j] != kEmptyKey) {
+      const int64_t id = key_idx(top.v[j]);
+      const float dx = xyz[3 * id] - q[0];
+      const float dy = xyz[3 * id + 1] - q[1];
+      const float dz = xyz[3 * id + 2] - q[2];
+      sx += dx;
+      sy += dy;
+      sz += dz;
+      sxx = fmaf(dx, dx, sxx);
+      sxy = fmaf(dx, dy, sxy);
+      sxz = fmaf(dx, dz, sxz);
+      syy = fmaf(dy, dy, syy);
+      syz = fmaf(dy, dz, syz);
+      szz = fmaf(dz, dz, szz);
+      ++m;
+    }
+  }
+  const float nan = __int_as_float(0x7fc00000);
+  if (m < 3) {
+    out_n[0] = out_n[1] = out_n[2] = nan;
+    out_c = nan;
+    return;
+  }
+  const float im = 1.0f / (float)m;
+  const float mx = sx * im, my = sy * im, mz = sz * im;
+  const float C[6] = {fmaf(-mx, mx, sxx * im), fmaf(-mx, my, sxy * im), fmaf(-mx, mz, sxz * im),
+                      fmaf(-my, my, syy * im), fmaf(-my, mz, syz * im), fmaf(-mz, mz, szz * im)};
+  float ev[3], nv[3];
+  if (!sym3_smallest(C, ev, nv)) {
+    out_n[0] = out_n[1] = out_n[2] = nan;
+    out_c = nan;
+    return;
+  }
+  const float tr = ev[0] + ev[1] + ev[2];
+  const float s = nv[0] * (vp[0] - q[0]) + nv[1] * (vp[1] - q[1]) + nv[2] * (vp[2] - q[2]);
+  const float sg = s < 0.0f ? -1.0f : 1.0f;
+  out_n[0] = sg * nv[0];
+  out_n[1] = sg * nv[1];
+  out_n[2] = sg * nv[2];
+  out_c = tr > 0.0f ? fmaxf(ev[0], 0.0f) / tr : nan;
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(256) k_normals(GridView g, int cloud_count, int64_t n, int k,
+                                                 const float* __restrict__ vp_all, float vx,
+                                                 float vy, float vz,
+                                                 const float* __restrict__ xyz,
+                                                 float* __restrict__ out_n, float* __restrict__ out_c) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 p = g.pts[i];
+  // the sorted array is grouped by cloud; find this point's cloud
+  int cloud = 0;
+  if (cloud_count > 1) {
+    int lo = 0, hi = cloud_count;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if ((int64_t)g.prm[mid].start <= i) lo = mid;
+      else hi = mid;
+    }
+    cloud = lo;
+  }
+  const int start = g.prm[cloud].start;
+  const int64_t local = __float_as_int(p.w);
+  const float q[3] = {p.x, p.y, p.z};
+  TopK<KMAX> top;
+  top.init(k);
+  grid_knn<KMAX>(g, cloud, q, top);
+  const float vp[3] = {vp_all ? vp_all[3 * cloud] : vx, vp_all ? vp_all[3 * cloud + 1] : vy,
+                       vp_all ? vp_all[3 * cloud + 2] : vz};
+  float nv[3], c;
+  normal_from_topk<KMAX>(top, k, xyz + 3 * (int64_t)start, q, vp, nv, c);
+  const int64_t gi = start + local;
+  out_n[3 * gi] = nv[0];
+  out_n[3 * gi + 1] = nv[1];
+  out_n[3 * gi + 2] = nv[2];
+  if (out_c) out_c[gi] = c;
+}
+
+// ---------------------------------------------------------------------------
+// host launchers: dispatch on the smallest compiled register capacity >= k
+// ---------------------------------------------------------------------------
+#define CIL_FOR_K(k, CALL)          \
+  do {                              \
+    if ((k) <= 1) {                 \
+      constexpr int KM = 1;         \
+      CALL;                         \
+    } else if ((k) <= 4) {          \
+      constexpr int KM = 4;         \
+      CALL;                         \
+    } else if ((k) <= 8) {          \
+      constexpr int KM = 8;         \
+      CALL;                         \
+    } else if ((k) <= 10) {         \
+      constexpr int KM = 10;        \
+      CALL;                         \
+    } else if ((k) <= 16) {         \
+      constexpr int KM = 16;        \
+      CALL;                         \
+    } else if ((k) <= 24) {         \
+      constexpr int KM = 24;        \
+      CALL;                         \
+    } else {                        \
+      constexpr int KM = 32;        \
+      CALL;                         \
+    }                               \
+  } while (0)
+
+cil_status launch_knn(const GridView& g, const float* qry, int64_t nq, const int* order, int k,
+                      int* out_idx, float* out_d2, int block, cudaStream_t s) {
+  if (nq <= 0) return CIL_OK;
+  if (block != 64 && block != 128 && block != 256) block = 128;
+  const int grid = ceil_div(nq, block);
+  CIL_FOR_K(k, (k_knn<KM><<<grid, block, 0, s>>>(g, qry, nq, order, k, out_idx, out_d2)));
+  return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
+}
+
+cil_status launch_normals(const GridView& g, int clouds, int64_t n, int k, const float* vp_dev,
+                          const float* vp_host, const float* xyz, float* out_n, float* out_c,
+                          int block, cudaStream_t s) {
+  if (n <= 0) return CIL_OK;
+  if (block != 64 && block != 128 && block != 256) block = 128;
+  const int grid = ceil_div(n, block);
+  const float vx = vp_host ? vp_host[0] : 0.0f, vy = vp_host ? vp_host[1] : 0.0f,
+              vz = vp_host ? vp_host[2] : 0.0f;
+  CIL_FOR_K(k, (k_normals<KM><<<grid, block, 0, s>>>(g, clouds, n, k, vp_dev, vx, vy, vz, xyz,
+                                                     out_n, out_c)));
+  return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
+}
+
+}  // namespace cil

@@ -1,0 +1,132 @@
+"""Point-to-plane ICP parity: libcil (cil_icp_point_to_plane, cil_register_pair)
+against the FP64 Gauss-Newton oracle, both fed the same float32 inputs (the
+target normals come from the oracle).
+
+Bar: rotation within 1e-5 rad (geodesic angle of R_gpu R_oracle^T) and
+translation within 1e-6 of the target's bounding-box diagonal.  The library
+evaluates residual terms in FP32 with compensated FP32 sums and solves in
+FP64; its per-round error is ~1e-7 relative, far inside the bar unless a
+nearest-neighbour decision flips on an FP32 near-tie."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1807_00399_gb300 as cil
+from paper_1807_00399_gb300 import synth
+from parity import extent, rot_angle
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_icp(src, dst, nrm, **kw):
+    s = torch.from_numpy(np.ascontiguousarray(src)).cuda()
+    d = torch.from_numpy(np.ascontiguousarray(dst)).cuda()
+    n = torch.from_numpy(np.ascontiguousarray(nrm)).cuda()
+    return cil.icp_point_to_plane(s, d, n, **kw)
+
+
+def _assert_same(Tg, To, dst, rot_tol=1e-5, trans_rel=1e-6):
+    ang = rot_angle(Tg[:3, :3], To[:3, :3])
+    dt = np.abs(Tg[:3, 3] - To[:3, 3]).max()
+    assert ang <= rot_tol, f"rotation differs by {ang:.3g} rad"
+    assert dt <= trans_rel * extent(dst), f"translation differs by {dt:.3g}"
+
+
+@pytest.fixture(scope="module")
+def surface():
+    p = synth.surface_pair(0, n=10_000)
+    on, _, _ = oracle.normals(p.target, 10, p.viewpoint)
+    return p, on.astype(np.float32)
+
+
+def test_surface_pair_matches_oracle(surface):
+    p, nrm = surface
+    Tg, rg = _gpu_icp(p.source, p.target, nrm, iters=20, max_corr_dist=0.1)
+    o = oracle.icp(p.source, p.target, nrm, iters=20, max_corr_dist=0.1)
+    _assert_same(Tg, o["T"], p.target)
+    assert rg["status"] == 0 and rg["iters_done"] == 20
+    assert abs(rg["n_inliers"] - o["n_inliers"]) <= 2
+    assert abs(rg["rmse"] - o["rmse"]) <= 1e-6 * max(o["rmse"], 1e-3) + 1e-9
+
+
+@pytest.mark.parametrize("iters", [0, 1, 3])
+def test_few_rounds_and_initial_transform(surface, iters):
+    p, nrm = surface
+    T0 = np.eye(4)
+    T0[:3, :3] = synth.rotation_from_axis_angle([0.3, 0.2, -1.0], 0.04)
+    T0[:3, 3] = [0.02, -0.01, 0.005]
+    Tg, rg = _gpu_icp(p.source, p.target, nrm, T_init=T0, iters=iters, max_corr_dist=0.1)
+    o = oracle.icp(p.source, p.target, nrm, T_init=T0, iters=iters, max_corr_dist=0.1)
+    _assert_same(Tg, o["T"], p.target)
+    if iters == 0:
+        assert np.array_equal(Tg, T0)
+    assert abs(rg["rmse"] - o["rmse"]) <= 1e-6 * o["rmse"] + 1e-9
+
+
+def test_noiseless_copy_exact():
+    rng = np.random.default_rng(1)
+    tgt = synth.surface_points(rng, 8000, noise=0.0).astype(np.float32)
+    nrm, _, _ = oracle.normals(tgt, 10, [0, 0, 10])
+    T_gen = synth.random_rigid(rng, 8.0, 0.05)
+    src = synth.apply_rigid(T_gen, tgt).astype(np.float32)
+    Tg, rg = _gpu_icp(src, tgt, nrm.astype(np.float32), iters=30, max_corr_dist=0.2)
+    Ti = np.linalg.inv(T_gen)
+    assert rot_angle(Tg[:3, :3], Ti[:3, :3]) < 2e-6
+    assert np.abs(Tg[:3, 3] - Ti[:3, 3]).max() < 2e-6
+    assert rg["rmse"] < 1e-5 and rg["n_inliers"] == 8000
+
+
+def test_planar_target_degenerate_and_no_inliers():
+    rng = np.random.default_rng(2)
+    xy = rng.uniform(-1, 1, (3000, 2))
+    tgt = np.column_stack([xy, np.zeros(len(xy))]).astype(np.float32)
+    nrm = np.tile(np.float32([0, 0, 1]), (len(tgt), 1))
+    Tg, rg = _gpu_icp(tgt + np.float32([0, 0, 0.01]), tgt, nrm, iters=3, max_corr_dist=0.1)
+    assert rg["status"] == cil.DEGENERATE and np.array_equal(Tg, np.eye(4))
+    Tg, rg = _gpu_icp(tgt + np.float32(5.0), tgt, nrm, iters=2, max_corr_dist=0.1)
+    assert rg["status"] == cil.DEGENERATE and rg["n_inliers"] == 0 and np.isnan(rg["rmse"])
+
+
+def test_nan_normals_are_rejected(surface):
+    p, nrm = surface
+    bad = nrm.copy()
+    bad[::7] = np.nan
+    Tg, rg = _gpu_icp(p.source, p.target, bad, iters=5, max_corr_dist=0.1)
+    o = oracle.icp(p.source, p.target, bad, iters=5, max_corr_dist=0.1)
+    _assert_same(Tg, o["T"], p.target)
+    assert abs(rg["n_inliers"] - o["n_inliers"]) <= 2
+
+
+def test_deterministic(surface):
+    p, nrm = surface
+    a = _gpu_icp(p.source, p.target, nrm, iters=10, max_corr_dist=0.1)
+    b = _gpu_icp(p.source, p.target, nrm, iters=10, max_corr_dist=0.1)
+    assert np.array_equal(a[0], b[0]) and a[1] == b[1]
+
+
+def test_depth_frame_full_size():
+    p = synth.depth_frame_pair(0)
+    on, _, _ = oracle.normals(p.target, 10, p.viewpoint, method="kdtree")
+    nrm = on.astype(np.float32)
+    Tg, rg = _gpu_icp(p.source, p.target, nrm, iters=30, max_corr_dist=0.05)
+    o = oracle.icp(p.source, p.target, nrm, iters=30, max_corr_dist=0.05, method="kdtree")
+    _assert_same(Tg, o["T"], p.target)
+    assert abs(rg["n_inliers"] - o["n_inliers"]) <= 5
+    # and the registration itself is right: close to the generator transform
+    assert rot_angle(Tg[:3, :3], p.T_gt[:3, :3]) < 2e-3
+
+
+def test_register_pair_equals_separate_calls(surface):
+    p, _ = surface
+    s = torch.from_numpy(p.source).cuda()
+    d = torch.from_numpy(p.target).cuda()
+    nrm = torch.empty_like(d)
+    T, rep, _ = cil.register_pair(s, d, 10, p.viewpoint, 20, 0.1, out_normals=nrm)
+    torch.cuda.synchronize()
+    r = cil.decode_report(rep)
+    n_sep, _ = cil.estimate_normals(d, 10, p.viewpoint)
+    assert torch.equal(nrm, n_sep)
+    T2, r2 = cil.icp_point_to_plane(s, d, n_sep, iters=20, max_corr_dist=0.1)
+    assert np.array_equal(T.cpu().numpy().reshape(4, 4), T2)
+    assert r == r2
