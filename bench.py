@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""Benchmark of the point-cloud hot path on GB300.
+
+One step = one pass of the whole hot path over one depth-frame pair (the
+640x480 workload, ~3.07e5 points per frame): target grid build, 10-NN PCA
+normals of every target point, 30 rounds of point-to-plane ICP (rejection
+0.05 m) plus the final RMSE pass -- the library's cil_register_pair.
+
+Reported metric: k-NN (k=10) queries per second of whole-pipeline time, i.e.
+target points whose 10-NN normal is computed per second, with ICP included in
+every step (pairs/s is reported beside it).
+
+  value   inputs resident in HBM, CUDA events around each step, L2 flushed
+          (256 MiB write) between steps outside the timed events;
+  e2e     same metric through the same C-ABI call with pinned host buffers:
+          each step copies both frames host->device and reads T + report back;
+  roofline  the dominant kernel's algorithmic bytes per launch / its average
+          CUDA-event duration (events recorded by the library on the launching
+          stream during the timed region), against the measured HBM copy
+          bandwidth;
+  cpu_baseline  the FP64 oracle (C, all host cores) on the same frame pair.
+
+--impl reference runs the oracle itself as the reference arm (the paper ships
+no GPU code): each step is the oracle pipeline on a 1/4 sample of the frame
+(normals of a quarter of the target points against the full cloud, ICP of a
+quarter of the source points), whose rate in queries/s is the per-query cost
+of the full step.
+Multi-GPU (torchrun): every rank registers its own frame pair (seed + rank);
+no data-path collective; value = all ranks' queries / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "kNN queries/s (k=10); ICP pairs/s at fixed RMSE, batched+learned vs plain"
+K_NN = 10
+ICP_ITERS = 30
+DMAX = 0.05
+WORKLOAD = ("depth-frame pair 640x480 (pinhole 525/319.5/239.5, ground + 20 boxes + 10 spheres, "
+            "depth noise 0.001 z^2, second camera moved <=3 deg / <=3 cm): target grid + 10-NN "
+            "PCA normals of every target point + 30 point-to-plane ICP rounds (d_max 0.05 m) + "
+            "final RMSE pass")
+
+# DRAM traffic per k_icp launch measured by ncu on this workload (bytes), with
+# the hash of the kernel sources it was measured on; reported only while the
+# sources are unchanged.
+ICP_TRAFFIC = {"bytes": None, "src_sha": None}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _src_sha():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1807_00399_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms",
+                 "100", "-i", str(self.idx)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier_max(x: float, ws: int) -> float:
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# oracle pipeline (reference arm and CPU baseline)
+# ---------------------------------------------------------------------------
+def oracle_step(pair, frac: float, rng_seed: int = 0):
+    """The oracle's pipeline on a sample: normals of frac * N_t target points
+    (neighbourhoods in the full cloud) and ICP of frac * N_s source points
+    against the full target.  Returns (queries, seconds, rmse)."""
+    import oracle
+    rng = np.random.default_rng(rng_seed)
+    nt, ns = len(pair.target), len(pair.source)
+    m_t = max(1, int(round(frac * nt)))
+    m_s = max(1, int(round(frac * ns)))
+    sel_t = np.sort(rng.choice(nt, m_t, replace=False)) if m_t < nt else np.arange(nt)
+    sel_s = np.sort(rng.choice(ns, m_s, replace=False)) if m_s < ns else np.arange(ns)
+    t0 = time.perf_counter()
+    if m_t < nt:
+        on, _, _ = oracle.normals_subset(pair.target, sel_t, K_NN, pair.viewpoint, method="kdtree")
+        nrm = np.full((nt, 3), np.nan, np.float32)
+        nrm[sel_t] = on
+        # ICP needs normals at every target point it may match: compute the rest
+        # outside the timed part would undercount; instead time the full normals
+        # share proportionally (frac of the full normals pass)
+    else:
+        on, _, _ = oracle.normals(pair.target, K_NN, pair.viewpoint, method="kdtree")
+        nrm = on.astype(np.float32)
+    t_norm = time.perf_counter() - t0
+    if m_t < nt:
+        # normals for all target points (untimed) so the ICP sample matches
+        on_all, _, _ = oracle.normals(pair.target, K_NN, pair.viewpoint, method="kdtree")
+        nrm = on_all.astype(np.float32)
+    t1 = time.perf_counter()
+    out = oracle.icp(pair.source[sel_s], pair.target, nrm, iters=ICP_ITERS, max_corr_dist=DMAX,
+                     method="kdtree")
+    t_icp = time.perf_counter() - t1
+    return m_t, t_norm + t_icp, out["rmse"]
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1807_00399_gb300 import synth
+    pair = synth.depth_frame_pair(args.seed)
+    frac = 0.25
+    for _ in range(args.warmup):
+        oracle_step(pair, frac)
+    q_tot, t_tot, rmse = 0, 0.0, float("nan")
+    for i in range(args.steps):
+        q, t, rmse = oracle_step(pair, frac, rng_seed=i)
+        q_tot += q
+        t_tot += t
+    value = q_tot / t_tot
+    cores = oracle.default_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_target": len(pair.target), "n_source": len(pair.source),
+                   "k": K_NN, "icp_iters": ICP_ITERS, "max_corr_dist": DMAX, "seed": args.seed,
+                   "sample": "1/4 of the target points (normals) and of the source points (ICP)"},
+        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                         "sample": "per step: normals of 1/4 of the target points + 30-round ICP of "
+                                   "1/4 of the source points (kd-tree route), rate per target query"},
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "final_rmse": rmse,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_1807_00399_gb300 as cil
+    from paper_1807_00399_gb300 import synth
+
+    L = cil.lib()
+    L.cil_launch_count.restype = __import__("ctypes").c_int64
+    pair = synth.depth_frame_pair(args.seed + rank)
+    nt, ns = len(pair.target), len(pair.source)
+    src = torch.from_numpy(pair.source).to(dev)
+    dst = torch.from_numpy(pair.target).to(dev)
+    nrm = torch.empty_like(dst)
+    T = torch.empty(16, dtype=torch.float64, device=dev)
+    rep = torch.empty(32, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    vp = pair.viewpoint
+
+    def step(s=src, d=dst):
+        cil.register_pair(s, d, K_NN, vp, ICP_ITERS, DMAX, out_normals=nrm, out_T=T,
+                          out_report=rep)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region ----
+    import ctypes
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    L.cil_timing_reset()
+    L.cil_timing_enable(1)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    _barrier(ws)
+    torch.cuda.synchronize()
+    n0 = L.cil_launch_count()
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record()
+        step()
+        evs[i][1].record()
+    torch.cuda.synchronize()
+    n1 = L.cil_launch_count()
+    _barrier(ws)
+    clocks = sampler.stop()
+    L.cil_timing_enable(0)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    tot_ms = float(sum(step_ms))
+    kern = {}
+    for name in ("grid_build", "k_normals", "order_queries", "k_icp"):
+        t = ctypes.c_double(0)
+        c = ctypes.c_int64(0)
+        L.cil_timing_read(name.encode(), ctypes.byref(t), ctypes.byref(c))
+        kern[name] = {"ms_total": t.value, "launches": int(c.value)}
+    L.cil_timing_reset()
+    rep_h = cil.decode_report(rep)
+    tot_max = _barrier_max(tot_ms, ws)
+    value = ws * nt * args.steps / (tot_max / 1e3)
+
+    # ---- end to end through the same call with host buffers ----
+    src_h = torch.from_numpy(pair.source).pin_memory()
+    dst_h = torch.from_numpy(pair.target).pin_memory()
+    T_h = torch.empty(16, dtype=torch.float64).pin_memory()
+    rep_h_buf = torch.empty(32, dtype=torch.uint8).pin_memory()
+    src_d = torch.empty_like(src)
+    dst_d = torch.empty_like(dst)
+    e2e_steps = max(1, min(args.steps, 200))
+    for _ in range(3):
+        src_d.copy_(src_h, non_blocking=True)
+        dst_d.copy_(dst_h, non_blocking=True)
+        step(src_d, dst_d)
+    torch.cuda.synchronize()
+    e_evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(e2e_steps)]
+    _barrier(ws)
+    m0 = L.cil_launch_count()
+    for i in range(e2e_steps):
+        flush.zero_()
+        e_evs[i][0].record()
+        src_d.copy_(src_h, non_blocking=True)
+        dst_d.copy_(dst_h, non_blocking=True)
+        step(src_d, dst_d)
+        T_h.copy_(T, non_blocking=True)
+        rep_h_buf.copy_(rep, non_blocking=True)
+        e_evs[i][1].record()
+    torch.cuda.synchronize()
+    e2e_ms = _barrier_max(float(sum(a.elapsed_time(b) for a, b in e_evs)), ws)
+    e2e_value = ws * nt * e2e_steps / (e2e_ms / 1e3)
+
+    # ---- roofline of the dominant kernel ----
+    peaks, peak_kind = _peaks()
+    dom = max(kern, key=lambda k: kern[k]["ms_total"])
+    per_launch_ms = {k: (v["ms_total"] / v["launches"] if v["launches"] else None)
+                     for k, v in kern.items()}
+    rounds = ICP_ITERS + 1
+    alg = {  # algorithmic bytes per launch (roofline section)
+        "k_icp": rounds * (12 * ns + 24 * nt),
+        "k_normals": 40 * nt,
+        "grid_build": 52 * nt + 16 * (1 << math.ceil(math.log2(2 * nt))),
+        "order_queries": 52 * ns,
+    }
+    traffic = None
+    if dom == "k_icp" and ICP_TRAFFIC["bytes"] and ICP_TRAFFIC["src_sha"] == _src_sha():
+        traffic = ICP_TRAFFIC["bytes"]
+    achieved = alg[dom] / (per_launch_ms[dom] / 1e3) / 1e9
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "algorithmic_bytes_per_launch": alg[dom], "ms_per_launch": per_launch_ms[dom],
+                "peak_kind": peak_kind}
+
+    # ---- CPU baseline (oracle, rank 0, N = 1 only) ----
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        q_tot, t_tot = 0, 0.0
+        while t_tot < 10.0:
+            q, t, _ = oracle_step(pair, 1.0)
+            q_tot += q
+            t_tot += t
+        cpu = {"value": q_tot / t_tot, "unit": "queries/s", "cores": oracle.default_threads(),
+               "kind": "oracle",
+               "sample": f"full frame pair, oracle kd-tree route, {q_tot // nt} step(s), "
+                         f"{t_tot:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_target": nt, "n_source": ns, "k": K_NN,
+                       "icp_iters": ICP_ITERS, "max_corr_dist": DMAX, "seed": args.seed,
+                       "parallelism": f"replicas x{ws} (independent frame pairs)",
+                       "l2": "flushed between timed steps (256 MiB write outside the events)"},
+            "pairs_per_s": ws * args.steps / (tot_max / 1e3),
+            "final_rmse": rep_h["rmse"], "final_inliers": rep_h["n_inliers"],
+            "icp_status": rep_h["status"],
+            "e2e": {"value": e2e_value, "unit": "queries/s",
+                    "h2d_bytes_per_step": int(src.numel() * 4 + dst.numel() * 4),
+                    "d2h_bytes_per_step": 16 * 8 + 32},
+            "roofline": roofline,
+            "kernels_ms_per_launch": per_launch_ms,
+            "cpu_baseline": cpu,
+            "gpu_launches": int(n1 - n0),
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -179,6 +179,61 @@ cil_status cil_register_pair(const float *src, int64_t n_src, const float *dst, 
                              float max_corr_dist, float *out_normals, double *T_out,
                              cil_icp_report *rep, const cil_params *params, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched registration of B independent pairs of uneven sizes (no counterpart
+ * in the paper, which registers one pair at a time, Sec. 4).  Per pair: the
+ * same target grid + k-NN normals + point-to-plane ICP as cil_register_pair,
+ * all pairs in one CUDA graph launch: one grid build over the concatenated
+ * targets (one cell level per pair), one normals kernel, one persistent ICP
+ * kernel whose per-pair rounds are scheduled independently.
+ *   cil_icp_batch_create  n_src, n_dst: host int64[B] point counts; allocates
+ *                         the handle's device workspace (synchronous)
+ *   cil_icp_batch_run     src_cat [sum n_src][3], dst_cat [sum n_dst][3]:
+ *                         device, pairs concatenated in order;
+ *                         T_init  device double[B][16] or NULL (identity);
+ *                         T_out   device double[B][16];
+ *                         rep     device cil_icp_report[B];
+ *                         normals_out device float[sum n_dst][3] or NULL.
+ *                         Asynchronous.  The first run with a given set of
+ *                         pointers captures a CUDA graph (call it outside any
+ *                         stream capture); later runs with the same pointers
+ *                         replay it.
+ *   cil_icp_batch_destroy waits for the device to be idle, frees everything.
+ * Runs of one handle must not overlap on the device (they share workspace).
+ */
+typedef struct {
+  int k;               /* normals neighbourhood, 1..CIL_MAX_K                */
+  int iters;           /* ICP rounds                                         */
+  float max_corr_dist; /* rejection distance for every pair                  */
+  float viewpoint[3];  /* normal orientation for every pair                  */
+  cil_params tune;     /* grid cell size / scale, query block size           */
+} cil_batch_params;
+
+typedef struct cil_batch cil_batch;
+
+cil_status cil_icp_batch_create(const int64_t *n_src, const int64_t *n_dst, int B,
+                                const cil_batch_params *params, cil_batch **out);
+cil_status cil_icp_batch_run(cil_batch *h, const float *src_cat, const float *dst_cat,
+                             const double *T_init, double *T_out, cil_icp_report *rep,
+                             float *normals_out, void *stream);
+void cil_icp_batch_destroy(cil_batch *h);
+
+/* ---------------------------------------------------------------------------
+ * Instrumentation (benchmarks, profiling; no counterpart in the paper).
+ *   cil_launch_count   kernels this library has launched since it was loaded
+ *   cil_timing_enable  1: record a pair of CUDA events on the launching stream
+ *                      around each instrumented kernel ("k_icp", "k_knn",
+ *                      "k_normals", "k_radius") and the grid build
+ *                      ("grid_build"); 0: stop recording
+ *   cil_timing_read    wait for the recorded events of `name` and return their
+ *                      summed duration (ms) and count
+ *   cil_timing_reset   wait for and drop every record
+ */
+int64_t cil_launch_count(void);
+void cil_timing_enable(int on);
+cil_status cil_timing_read(const char *name, double *total_ms, int64_t *launches);
+void cil_timing_reset(void);
+
 #ifdef __cplusplus
 }
 #endif

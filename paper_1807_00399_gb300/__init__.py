@@ -17,7 +17,8 @@ import numpy as np
 
 __all__ = [
     "CilError", "lib", "knn", "radius_search", "estimate_normals", "icp_point_to_plane",
-    "register_pair", "sync_status", "Params", "STATUS", "MAX_K", "IcpReport",
+    "register_pair", "sync_status", "Params", "STATUS", "MAX_K", "IcpReport", "Batch",
+    "decode_report", "decode_reports",
 ]
 
 MAX_K = 32
@@ -45,6 +46,11 @@ class Params(ctypes.Structure):
                 ("block", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
+class BatchParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("iters", ctypes.c_int), ("max_corr_dist", ctypes.c_float),
+                ("viewpoint", ctypes.c_float * 3), ("tune", Params)]
+
+
 class IcpReport(ctypes.Structure):
     _fields_ = [("rmse", ctypes.c_double), ("n_inliers", ctypes.c_int64),
                 ("iters_done", ctypes.c_int), ("status", ctypes.c_int)]
@@ -70,9 +76,19 @@ def lib():
         L.cil_estimate_normals_ex.argtypes = [P, I64, I, P, P, P, P, P]
         L.cil_icp_point_to_plane.argtypes = [P, I64, P, P, I64, P, I, F, P, P, P]
         L.cil_register_pair.argtypes = [P, I64, P, I64, I, P, P, I, F, P, P, P, P, P]
+        L.cil_icp_batch_create.argtypes = [P, P, I, P, P]
+        L.cil_icp_batch_run.argtypes = [P, P, P, P, P, P, P, P]
+        L.cil_icp_batch_destroy.argtypes = [P]
+        L.cil_icp_batch_destroy.restype = None
+        L.cil_launch_count.restype = I64
+        L.cil_timing_enable.argtypes = [I]
+        L.cil_timing_enable.restype = None
+        L.cil_timing_read.argtypes = [ctypes.c_char_p, P, P]
+        L.cil_timing_reset.restype = None
         for name in ("cil_sync_status", "cil_knn", "cil_knn_ex", "cil_radius_search",
                      "cil_estimate_normals", "cil_estimate_normals_ex", "cil_icp_point_to_plane",
-                     "cil_register_pair"):
+                     "cil_register_pair", "cil_icp_batch_create", "cil_icp_batch_run",
+                     "cil_timing_read"):
             getattr(L, name).restype = I
         _lib = L
         return L
@@ -246,3 +262,65 @@ def decode_report(buf) -> dict:
     rep = IcpReport.from_buffer_copy(raw[: ctypes.sizeof(IcpReport)])
     return {"rmse": rep.rmse, "n_inliers": int(rep.n_inliers), "iters_done": rep.iters_done,
             "status": rep.status}
+
+
+def decode_reports(buf, B: int) -> list:
+    raw = bytes(buf.cpu().numpy().tobytes()) if hasattr(buf, "cpu") else bytes(buf)
+    sz = ctypes.sizeof(IcpReport)
+    out = []
+    for b in range(B):
+        rep = IcpReport.from_buffer_copy(raw[b * sz:(b + 1) * sz])
+        out.append({"rmse": rep.rmse, "n_inliers": int(rep.n_inliers),
+                    "iters_done": rep.iters_done, "status": rep.status})
+    return out
+
+
+class Batch:
+    """Batched registration handle (cil_icp_batch_*): B pairs of uneven sizes,
+    one graph launch per run.  Inputs are the pairs' clouds concatenated."""
+
+    def __init__(self, n_src, n_dst, *, k: int = 10, iters: int = 30, max_corr_dist: float = 0.1,
+                 viewpoint=(0.0, 0.0, 10.0), cell_size=0.0, cell_scale=0.0, block=0):
+        self.n_src = np.ascontiguousarray(n_src, np.int64)
+        self.n_dst = np.ascontiguousarray(n_dst, np.int64)
+        if self.n_src.shape != self.n_dst.shape or self.n_src.ndim != 1:
+            raise ValueError("n_src and n_dst must be 1-D of equal length")
+        self.B = int(self.n_src.shape[0])
+        self.params = BatchParams(int(k), int(iters), float(max_corr_dist),
+                                  (ctypes.c_float * 3)(*[float(v) for v in viewpoint]),
+                                  Params(float(cell_size), float(cell_scale), int(block), 0))
+        h = ctypes.c_void_p()
+        st = lib().cil_icp_batch_create(self.n_src.ctypes.data_as(ctypes.c_void_p),
+                                        self.n_dst.ctypes.data_as(ctypes.c_void_p), self.B,
+                                        ctypes.byref(self.params), ctypes.byref(h))
+        _check(st, "cil_icp_batch_create")
+        self._h = h
+
+    def run(self, src_cat, dst_cat, T_init=None, T_out=None, rep=None, normals_out=None,
+            stream=None):
+        torch = _torch()
+        src_cat = _points(src_cat, "src_cat")
+        dst_cat = _points(dst_cat, "dst_cat")
+        if src_cat.shape[0] != int(self.n_src.sum()) or dst_cat.shape[0] != int(self.n_dst.sum()):
+            raise ValueError("concatenated sizes do not match the handle")
+        dev = dst_cat.device
+        if T_out is None:
+            T_out = torch.empty((self.B, 16), dtype=torch.float64, device=dev)
+        if rep is None:
+            rep = torch.empty((self.B, ctypes.sizeof(IcpReport)), dtype=torch.uint8, device=dev)
+        st = lib().cil_icp_batch_run(self._h, _ptr(src_cat), _ptr(dst_cat),
+                                     _ptr(T_init) if T_init is not None else None, _ptr(T_out),
+                                     _ptr(rep), _ptr(normals_out), _stream(stream))
+        _check(st, "cil_icp_batch_run")
+        return T_out, rep
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cil_icp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

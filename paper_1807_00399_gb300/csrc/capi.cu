@@ -1,6 +1,10 @@
 // capi.cu -- the exported C ABI (include/cil.h): argument checks, per-device
 // context, stream-ordered workspaces and the enqueue sequences of each call.
+#include <atomic>
+#include <cstring>
 #include <mutex>
+#include <string>
+#include <vector>
 
 #include "cil_host.h"
 #include "cil_kernels.h"
@@ -75,6 +79,42 @@ Workspace::~Workspace() {
   if (base_) cudaFreeAsync(base_, stream_);
 }
 
+// ---------------------------------------------------------------------------
+// instrumentation
+// ---------------------------------------------------------------------------
+static std::atomic<long long> g_launches{0};
+static std::atomic<int> g_timing{0};
+static std::mutex g_timing_mu;
+struct TimedRecord {
+  std::string name;
+  cudaEvent_t a, b;
+};
+static std::vector<TimedRecord> g_records;
+
+void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+TimedRegion::TimedRegion(const char* name, cudaStream_t s) : name_(name), s_(s) {
+  if (!g_timing.load(std::memory_order_relaxed)) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+  cudaEvent_t* ev = new cudaEvent_t[2];
+  if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) {
+    delete[] ev;
+    return;
+  }
+  cudaEventRecord(ev[0], s);
+  ev_ = ev;
+}
+
+TimedRegion::~TimedRegion() {
+  if (!ev_) return;
+  cudaEvent_t* ev = static_cast<cudaEvent_t*>(ev_);
+  cudaEventRecord(ev[1], s_);
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  g_records.push_back({name_, ev[0], ev[1]});
+  delete[] ev;
+}
+
 static cil_status read_error_word(DeviceCtx* ctx, cudaStream_t s, bool clear) {
   int v = 0;
   if (cudaMemcpyAsync(&v, ctx->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -119,6 +159,38 @@ const char* cil_status_string(cil_status s) {
     case CIL_ERR_NOMEM: return "CIL_ERR_NOMEM";
   }
   return "CIL_ERR_UNKNOWN";
+}
+
+void cil_timing_enable(int on) { g_timing.store(on ? 1 : 0); }
+
+int64_t cil_launch_count(void) { return g_launches.load(); }
+
+cil_status cil_timing_read(const char* name, double* total_ms, int64_t* launches) {
+  if (!name || !total_ms || !launches) return CIL_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  double tot = 0.0;
+  int64_t cnt = 0;
+  for (auto& r : g_records) {
+    if (r.name != name) continue;
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return CIL_ERR_CUDA;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) return CIL_ERR_CUDA;
+    tot += ms;
+    ++cnt;
+  }
+  *total_ms = tot;
+  *launches = cnt;
+  return CIL_OK;
+}
+
+void cil_timing_reset(void) {
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  for (auto& r : g_records) {
+    cudaEventSynchronize(r.b);
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g_records.clear();
 }
 
 cil_status cil_sync_status(void* stream) {

@@ -100,6 +100,19 @@ void scan_exclusive(int* data, int64_t L, int* tmp, cudaStream_t s);
 void scan_exclusive_i64(long long* data, int64_t L, long long* tmp, cudaStream_t s);
 
 int ceil_div(int64_t a, int64_t b);
+
+// ---------------------------------------------------------------------------
+// instrumentation: count of kernel launches and optional per-kernel CUDA-event
+// timing on the launching stream (used by benchmarks and profiling)
+// ---------------------------------------------------------------------------
+void note_launches(int n);
+struct TimedRegion {
+  TimedRegion(const char* name, cudaStream_t s);
+  ~TimedRegion();
+  const char* name_;
+  cudaStream_t s_;
+  void* ev_ = nullptr;  // opaque pair of events when timing is on
+};
 unsigned next_pow2_u32(uint64_t v);
 
 }  // namespace cil

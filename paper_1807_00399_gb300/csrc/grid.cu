@@ -378,8 +378,10 @@ static void scan_exclusive_t(T* data, int64_t L, T* tmp, cudaStream_t s) {
   const int nb = ceil_div(L, ScanCfg<T>::chunk);
   if (nb == 1) {
     k_scan_apply<T><<<1, kScanThreads, 0, s>>>(data, L, nullptr, 1);
+    note_launches(1);
     return;
   }
+  note_launches(3);
   k_scan_reduce<T><<<nb, kScanThreads, 0, s>>>(data, L, tmp);
   k_scan_apply<T><<<1, kScanThreads, 0, s>>>(tmp, nb, nullptr, ceil_div(nb, ScanCfg<T>::chunk));
   k_scan_apply<T><<<nb, kScanThreads, 0, s>>>(data, L, tmp, 1);
@@ -415,6 +417,7 @@ static int radix_sort(u64* k0, int* v0, u64* k1, int* v1, int64_t n, int passes,
     scan_exclusive(counts, (int64_t)kRadix * nblk, scan_tmp, s);
     k_radix_scatter<<<nblk, kRsThreads, 0, s>>>(ka[cur], va[cur], n, shift, counts, nblk,
                                                 ka[cur ^ 1], va[cur ^ 1]);
+    note_launches(2);
     cur ^= 1;
   }
   return cur;
@@ -592,8 +595,10 @@ GridView grid_view(const GridPlan& p, const Workspace& ws) {
 cil_status grid_build(const GridPlan& p, const Workspace& ws, const float* xyz,
                       const int* cloud_start_dev, const GridOptions& opt, DeviceCtx* ctx,
                       cudaStream_t s) {
+  TimedRegion timer("grid_build", s);
   GridParams* prm = ws.at<GridParams>(p.o_prm);
   const int64_t n = p.n;
+  note_launches(n > 0 ? 9 : 2);
   k_init_params<<<ceil_div(p.clouds, 128), 128, 0, s>>>(prm, p.clouds, cloud_start_dev, n);
   if (n > 0) {
     const int64_t threads = (n + 7) / 8;
@@ -645,8 +650,10 @@ cil_status order_queries(const OrderPlan& p, const Workspace& ws, const float* q
   u64* k1 = ws.at<u64>(p.o_keys1);
   int* v0 = ws.at<int>(p.o_vals0);
   int* v1 = ws.at<int>(p.o_vals1);
+  TimedRegion timer("order_queries", s);
   k_morton_keys<<<ceil_div(n, 256), 256, 0, s>>>(qry, n, q_cloud_start_dev, clouds, ref_prm, Rt_dev,
                                                  k0, v0);
+  note_launches(1);
   const int which = radix_sort(k0, v0, k1, v1, n, radix_passes(clouds), ws.at<int>(p.o_counts),
                                ws.at<int>(p.o_scan), p.radix_blocks, s);
   if (cudaMemcpyAsync(order_out, which ? v1 : v0, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice,

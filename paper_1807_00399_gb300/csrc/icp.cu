@@ -491,6 +491,7 @@ cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt, c
   int* tile_off = ws.at<int>(p.o_tile_off);
   float* rt = ws.at<float>(p.o_rt);
   unsigned* work = ws.at<unsigned>(p.o_work);
+  note_launches(1);
   k_icp_setup<<<1, 1024, 0, s>>>(st, p.pairs, src_start_dev, p.n_src, tile_off, T_init_dev, Th,
                                  T_init_host != nullptr, dmax_dev, dmax, iters, rt);
   if (cudaMemsetAsync(work, 0, sizeof(unsigned) * 4, s) != cudaSuccess) return CIL_ERR_CUDA;
@@ -522,12 +523,17 @@ cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt, c
   const long long want = (long long)p.n_tiles * a.rounds;
   int grid = ctx->num_sms * per_sm;
   if (want < grid) grid = (int)want;
-  k_icp<<<grid, kIcpThreads, 0, s>>>(a);
+  {
+    TimedRegion timer("k_icp", s);
+    note_launches(1);
+    k_icp<<<grid, kIcpThreads, 0, s>>>(a);
+  }
   return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
 }
 
 cil_status icp_export(const IcpPlan& p, const Workspace& ws, double* T_out_dev,
                       cil_icp_report* rep_dev, cudaStream_t s) {
+  note_launches(1);
   k_icp_export<<<ceil_div(p.pairs, 128), 128, 0, s>>>(ws.at<IcpPairState>(p.o_state), p.pairs,
                                                       T_out_dev, rep_dev);
   return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;

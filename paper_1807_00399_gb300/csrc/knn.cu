@@ -294,6 +294,8 @@ cil_status launch_knn(const GridView& g, const float* qry, int64_t nq, const int
   if (nq <= 0) return CIL_OK;
   if (block != 64 && block != 128 && block != 256) block = 128;
   const int grid = ceil_div(nq, block);
+  TimedRegion timer("k_knn", s);
+  note_launches(1);
   CIL_FOR_K(k, (k_knn<KM><<<grid, block, 0, s>>>(g, qry, nq, order, k, out_idx, out_d2)));
   return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
 }
@@ -304,6 +306,8 @@ cil_status launch_normals(const GridView& g, int clouds, int64_t n, int k, const
   if (n <= 0) return CIL_OK;
   if (block != 64 && block != 128 && block != 256) block = 128;
   const int grid = ceil_div(n, block);
+  TimedRegion timer("k_normals", s);
+  note_launches(1);
   const float vx = vp_host ? vp_host[0] : 0.0f, vy = vp_host ? vp_host[1] : 0.0f,
               vz = vp_host ? vp_host[2] : 0.0f;
   CIL_FOR_K(k, (k_normals<KM><<<grid, block, 0, s>>>(g, clouds, n, k, vp_dev, vx, vy, vz, xyz,

@@ -181,7 +181,11 @@ extern "C" cil_status cil_radius_search(const float* ref, int64_t n_ref, const f
   if ((st = order_queries(op, ws, qry, nullptr, 1, g.prm, nullptr, order, s)) != CIL_OK) return st;
   long long* off = reinterpret_cast<long long*>(out_offsets);
   const int grid = ceil_div(n_qry, 128);
-  k_radius<false><<<grid, 128, 0, s>>>(g, qry, n_qry, order, r, off, nullptr, nullptr);
+  {
+    TimedRegion timer("k_radius", s);
+    note_launches(1);
+    k_radius<false><<<grid, 128, 0, s>>>(g, qry, n_qry, order, r, off, nullptr, nullptr);
+  }
   if (cudaMemsetAsync(off + n_qry, 0, sizeof(long long), s) != cudaSuccess) return CIL_ERR_CUDA;
   scan_exclusive_i64(off, n_qry + 1, ws.at<long long>(o_tmp), s);
   long long nnz = 0;
@@ -203,6 +207,8 @@ extern "C" cil_status cil_radius_search(const float* ref, int64_t n_ref, const f
         return CIL_ERR_NOMEM;
       d2 = static_cast<float*>(d2_tmp);
     }
+    TimedRegion timer("k_radius", s);
+    note_launches(2);
     k_radius<true><<<grid, 128, 0, s>>>(g, qry, n_qry, order, r, off, out_idx, d2);
     k_sort_rows<<<(unsigned)n_qry, kSortThreads, 0, s>>>(off, n_qry, out_idx, d2);
     if (d2_tmp) cudaFreeAsync(d2_tmp, s);
