@@ -219,6 +219,41 @@ cil_status cil_icp_batch_run(cil_batch *h, const float *src_cat, const float *ds
 void cil_icp_batch_destroy(cil_batch *h);
 
 /* ---------------------------------------------------------------------------
+ * Learned warm start (no counterpart in the paper; it seeds the Sec. 3 ICP).
+ * A PointNet-style regressor of the source -> target transform:
+ *   encoder, shared by both clouds of a pair: 3 -> 64 (FP32), 64 -> 128 and
+ *   128 -> 256 (BF16 tensor cores, FP32 accumulation), ReLU after each,
+ *   global max-pool over the points;
+ *   head: [f_src, f_dst] (512) -> 256 (ReLU) -> 9; R = Gram-Schmidt of the
+ *   first two 3-vectors (columns b1, b2, b1 x b2), t = last three;
+ *   loss: mean over pairs of mean over source points |(R p + t) - (Rg p + tg)|^2.
+ * Parameters: one FP32 vector of cil_pointnet_num_params() values in the order
+ * W1[64][3] b1 W2[128][64] b2 W3[256][128] b3 W4[256][512] b4 W5[9][256] b5.
+ *   clouds  device float[B][2][P][3]: per pair the source then the target cloud
+ *           (P = n_points, a multiple of 128)
+ *   T_gt    device double[B][16] row-major source -> target labels
+ *   T_out   device double[B][16] predicted transforms (may be NULL)
+ *   cil_pointnet_forward   prediction only (features to feat_out [B][512] if
+ *                          not NULL)
+ *   cil_pointnet_backward  forward + loss (per pair, device float[B]) +
+ *                          gradient of the mean loss (device float[n_params])
+ *   cil_pointnet_adam_step Adam (0.9, 0.999, 1e-8) on the FP32 master weights
+ *                          with the last gradient, then refreshes the BF16 copies
+ * All asynchronous on `stream`; a handle's calls must not overlap.
+ */
+typedef struct cil_pointnet cil_pointnet;
+int cil_pointnet_num_params(void);
+cil_status cil_pointnet_create(int max_pairs, int n_points, cil_pointnet **out);
+void cil_pointnet_destroy(cil_pointnet *h);
+cil_status cil_pointnet_set_params(cil_pointnet *h, const float *params, void *stream);
+cil_status cil_pointnet_get_params(cil_pointnet *h, float *params, void *stream);
+cil_status cil_pointnet_forward(cil_pointnet *h, const float *clouds, int B, double *T_out,
+                                float *feat_out, void *stream);
+cil_status cil_pointnet_backward(cil_pointnet *h, const float *clouds, const double *T_gt, int B,
+                                 float *loss_out, float *grad_out, void *stream);
+cil_status cil_pointnet_adam_step(cil_pointnet *h, float lr, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Instrumentation (benchmarks, profiling; no counterpart in the paper).
  *   cil_launch_count   kernels this library has launched since it was loaded
  *   cil_timing_enable  1: record a pair of CUDA events on the launching stream

@@ -81,6 +81,15 @@ def lib():
         L.cil_icp_batch_destroy.argtypes = [P]
         L.cil_icp_batch_destroy.restype = None
         L.cil_launch_count.restype = I64
+        L.cil_pointnet_num_params.restype = I
+        L.cil_pointnet_create.argtypes = [I, I, P]
+        L.cil_pointnet_destroy.argtypes = [P]
+        L.cil_pointnet_destroy.restype = None
+        L.cil_pointnet_set_params.argtypes = [P, P, P]
+        L.cil_pointnet_get_params.argtypes = [P, P, P]
+        L.cil_pointnet_forward.argtypes = [P, P, I, P, P, P]
+        L.cil_pointnet_backward.argtypes = [P, P, P, I, P, P, P]
+        L.cil_pointnet_adam_step.argtypes = [P, F, P]
         L.cil_timing_enable.argtypes = [I]
         L.cil_timing_enable.restype = None
         L.cil_timing_read.argtypes = [ctypes.c_char_p, P, P]
@@ -88,7 +97,9 @@ def lib():
         for name in ("cil_sync_status", "cil_knn", "cil_knn_ex", "cil_radius_search",
                      "cil_estimate_normals", "cil_estimate_normals_ex", "cil_icp_point_to_plane",
                      "cil_register_pair", "cil_icp_batch_create", "cil_icp_batch_run",
-                     "cil_timing_read"):
+                     "cil_timing_read", "cil_pointnet_create", "cil_pointnet_set_params",
+                     "cil_pointnet_get_params", "cil_pointnet_forward", "cil_pointnet_backward",
+                     "cil_pointnet_adam_step"):
             getattr(L, name).restype = I
         _lib = L
         return L
@@ -317,6 +328,80 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             lib().cil_icp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PointNet:
+    """Learned warm start (cil_pointnet_*): a PointNet-style regressor of the
+    source -> target transform with hand-written BF16 tensor-core forward,
+    sparse max-pool backward and Adam.  Clouds are (B, 2, P, 3) float32 CUDA
+    tensors (source, target per pair)."""
+
+    def __init__(self, max_pairs: int, n_points: int = 4096, params=None):
+        torch = _torch()
+        L = lib()
+        self.n_params = int(L.cil_pointnet_num_params())
+        self.max_pairs = int(max_pairs)
+        self.P = int(n_points)
+        h = ctypes.c_void_p()
+        _check(L.cil_pointnet_create(self.max_pairs, self.P, ctypes.byref(h)), "cil_pointnet_create")
+        self._h = h
+        if params is not None:
+            self.set_params(params)
+
+    def set_params(self, params, stream=None):
+        torch = _torch()
+        t = torch.as_tensor(params, dtype=torch.float32).reshape(-1).cuda().contiguous()
+        if t.numel() != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters")
+        self._params_keep = t
+        _check(lib().cil_pointnet_set_params(self._h, _ptr(t), _stream(stream)),
+               "cil_pointnet_set_params")
+
+    def get_params(self, stream=None):
+        torch = _torch()
+        out = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        _check(lib().cil_pointnet_get_params(self._h, _ptr(out), _stream(stream)),
+               "cil_pointnet_get_params")
+        return out
+
+    def forward(self, clouds, T_out=None, feat_out=None, stream=None):
+        torch = _torch()
+        B = int(clouds.shape[0])
+        if clouds.dtype != torch.float32 or tuple(clouds.shape[1:]) != (2, self.P, 3):
+            raise ValueError("clouds must be float32 (B, 2, P, 3)")
+        clouds = clouds.contiguous()
+        if T_out is None:
+            T_out = torch.empty((B, 16), dtype=torch.float64, device=clouds.device)
+        _check(lib().cil_pointnet_forward(self._h, _ptr(clouds), B, _ptr(T_out), _ptr(feat_out),
+                                          _stream(stream)), "cil_pointnet_forward")
+        return T_out
+
+    def backward(self, clouds, T_gt, loss_out=None, grad_out=None, stream=None):
+        torch = _torch()
+        B = int(clouds.shape[0])
+        clouds = clouds.contiguous()
+        T_gt = T_gt.reshape(B, 16).to(torch.float64).contiguous()
+        if loss_out is None:
+            loss_out = torch.empty(B, dtype=torch.float32, device=clouds.device)
+        _check(lib().cil_pointnet_backward(self._h, _ptr(clouds), _ptr(T_gt), B, _ptr(loss_out),
+                                           _ptr(grad_out), _stream(stream)),
+               "cil_pointnet_backward")
+        return loss_out, grad_out
+
+    def adam_step(self, lr: float, stream=None):
+        _check(lib().cil_pointnet_adam_step(self._h, float(lr), _stream(stream)),
+               "cil_pointnet_adam_step")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cil_pointnet_destroy(self._h)
             self._h = None
 
     def __del__(self):

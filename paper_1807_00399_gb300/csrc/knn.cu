@@ -7,8 +7,8 @@
 // keeps its k best (squared distance, index) keys sorted in registers.
 //
 // Normals (Sec. 3 normal/curvature estimation, Sec. 4 10-NN neighbourhoods):
-// the k neighbours' offsets from the query give shifted first and second
-// moments, hence the covariance C = (1/m) sum (p - mu)(p - mu)^T; its smallest
+// the k neighbours' offsets from the query give their mean, then the centred
+// covariance C = (1/m) sum (p - mu)(p - mu)^T in a second pass; its smallest
 // eigenpair comes from the closed-form trigonometric solution of the
 // characteristic cubic plus a cross product of two rows of C - l0 I.
 #include <math.h>
@@ -176,25 +176,18 @@ template <int KMAX>
 __device__ __forceinline__ void normal_from_topk(const TopK<KMAX>& top, int k,
                                                  const float* __restrict__ xyz, const float q[3],
                                                  const float vp[3], float out_n[3], float& out_c) {
+  // pass 1: mean offset of the neighbours from the query (offsets of nearby
+  // points are exact in FP32); pass 2: covariance about that mean (centred,
+  // so no cancellation between second moments and the squared mean)
   float sx = 0.f, sy = 0.f, sz = 0.f;
-  float sxx = 0.f, sxy = 0.f, sxz = 0.f, syy = 0.f, syz = 0.f, szz = 0.f;
   int m = 0;
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) {
     if (j < k && top.v[j] != kEmptyKey) {
       const int64_t id = key_idx(top.v[j]);
-      const float dx = xyz[3 * id] - q[0];
-      const float dy = xyz[3 * id + 1] - q[1];
-      const float dz = xyz[3 * id + 2] - q[2];
-      sx += dx;
-      sy += dy;
-      sz += dz;
-      sxx = fmaf(dx, dx, sxx);
-      sxy = fmaf(dx, dy, sxy);
-      sxz = fmaf(dx, dz, sxz);
-      syy = fmaf(dy, dy, syy);
-      syz = fmaf(dy, dz, syz);
-      szz = fmaf(dz, dz, szz);
+      sx += xyz[3 * id] - q[0];
+      sy += xyz[3 * id + 1] - q[1];
+      sz += xyz[3 * id + 2] - q[2];
       ++m;
     }
   }
@@ -206,8 +199,23 @@ __device__ __forceinline__ void normal_from_topk(const TopK<KMAX>& top, int k,
   }
   const float im = 1.0f / (float)m;
   const float mx = sx * im, my = sy * im, mz = sz * im;
-  const float C[6] = {fmaf(-mx, mx, sxx * im), fmaf(-mx, my, sxy * im), fmaf(-mx, mz, sxz * im),
-                      fmaf(-my, my, syy * im), fmaf(-my, mz, syz * im), fmaf(-mz, mz, szz * im)};
+  float cxx = 0.f, cxy = 0.f, cxz = 0.f, cyy = 0.f, cyz = 0.f, czz = 0.f;
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    if (j < k && top.v[j] != kEmptyKey) {
+      const int64_t id = key_idx(top.v[j]);
+      const float ex = (xyz[3 * id] - q[0]) - mx;
+      const float ey = (xyz[3 * id + 1] - q[1]) - my;
+      const float ez = (xyz[3 * id + 2] - q[2]) - mz;
+      cxx = fmaf(ex, ex, cxx);
+      cxy = fmaf(ex, ey, cxy);
+      cxz = fmaf(ex, ez, cxz);
+      cyy = fmaf(ey, ey, cyy);
+      cyz = fmaf(ey, ez, cyz);
+      czz = fmaf(ez, ez, czz);
+    }
+  }
+  const float C[6] = {cxx * im, cxy * im, cxz * im, cyy * im, cyz * im, czz * im};
   float ev[3], nv[3];
   if (!sym3_smallest(C, ev, nv)) {
     out_n[0] = out_n[1] = out_n[2] = nan;
