@@ -37,6 +37,8 @@ struct GridParams {
   int start;           // offset of this cloud in the concatenated arrays
   unsigned bbox_enc[6];// order-preserving integer encodings (min x,y,z, max x,y,z)
   int nonfinite;       // number of non-finite coordinates seen
+  int level2;          // correspondence-search level (ICP), -1 if not built
+  float cell2;         // fine * 2^level2
   int pad;
 };
 
@@ -50,8 +52,10 @@ struct __align__(16) CellEntry {
 struct GridView {
   const GridParams* prm;  // [n_clouds]
   const float4* pts;      // sorted points: x, y, z, local index (int bits)
-  const CellEntry* tab;   // hash table
+  const CellEntry* tab;   // hash table of the k-NN level
   unsigned mask;          // table size - 1 (power of two)
+  const CellEntry* tab2;  // hash table of the correspondence level (or null)
+  unsigned mask2;
 };
 
 // ---------------------------------------------------------------------------
@@ -109,10 +113,11 @@ __device__ __forceinline__ u64 cell_key(int cloud, int x, int y, int z) {
          (u64)(unsigned)x;
 }
 
-__device__ __forceinline__ bool cell_lookup(const GridView& g, u64 K, int& start, int& count) {
-  unsigned h = hash_key(K) & g.mask;
-  for (unsigned probe = 0; probe <= g.mask; ++probe) {
-    const int4 v = __ldg(reinterpret_cast<const int4*>(g.tab + h));
+__device__ __forceinline__ bool table_lookup(const CellEntry* tab, unsigned mask, u64 K, int& start,
+                                             int& count) {
+  unsigned h = hash_key(K) & mask;
+  for (unsigned probe = 0; probe <= mask; ++probe) {
+    const int4 v = __ldg(reinterpret_cast<const int4*>(tab + h));
     const u64 key = (u64)(unsigned)v.x | ((u64)(unsigned)v.y << 32);
     if (key == K) {
       start = v.z;
@@ -120,9 +125,13 @@ __device__ __forceinline__ bool cell_lookup(const GridView& g, u64 K, int& start
       return true;
     }
     if (key == kEmptyKey) return false;
-    h = (h + 1) & g.mask;
+    h = (h + 1) & mask;
   }
   return false;
+}
+
+__device__ __forceinline__ bool cell_lookup(const GridView& g, u64 K, int& start, int& count) {
+  return table_lookup(g.tab, g.mask, K, start, count);
 }
 
 // squared distance of two points from exact per-axis differences
@@ -160,12 +169,15 @@ struct CellFrame {
   int cloud;
 
   __device__ __forceinline__ void load(const GridParams& P, int cloud_id) {
+    load_level(P, cloud_id, P.level, P.cell);
+  }
+  __device__ __forceinline__ void load_level(const GridParams& P, int cloud_id, int lvl, float cell) {
     o[0] = P.o[0];
     o[1] = P.o[1];
     o[2] = P.o[2];
-    c = P.cell;
+    c = cell;
     eps = P.eps;
-    level = P.level;
+    level = lvl;
     hi[0] = P.hi_fine[0] >> level;
     hi[1] = P.hi_fine[1] >> level;
     hi[2] = P.hi_fine[2] >> level;

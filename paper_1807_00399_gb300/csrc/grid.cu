@@ -67,6 +67,8 @@ __global__ void k_init_params(GridParams* prm, int clouds, const int* cs, int64_
   P.level = 0;
   P.cell = 1.0f;
   P.nonfinite = 0;
+  P.level2 = -1;
+  P.cell2 = 1.0f;
   P.pad = 0;
   prm[b] = P;
 }
@@ -443,7 +445,8 @@ __global__ void k_gather_sorted(const u64* __restrict__ keys, const int* __restr
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_choose_level(GridParams* prm, const float4* __restrict__ pts,
                                                       int k_default, const int* cloud_k,
-                                                      float cell_size, float cell_scale) {
+                                                      float cell_size, float cell_scale,
+                                                      float icp_dmax, float icp_scale) {
   constexpr int S = 1024;
   __shared__ float est[S];
   GridParams& P = prm[blockIdx.x];
@@ -500,17 +503,30 @@ __global__ void __launch_bounds__(256) k_choose_level(GridParams* prm, const flo
     L = max(0, min(L, kFineBits));
     P.level = L;
     P.cell = ldexpf(fine, L);
+    if (icp_dmax > 0.0f) {
+      // correspondence level: cells of at least icp_scale * d_max, so a search
+      // bounded by d_max never visits more than (2 ceil(1/icp_scale) + 1)^3 cells
+      const float r2 = (icp_dmax * icp_scale) / fine;
+      int L2 = r2 <= 1.0f ? 0 : (int)ceilf(log2f(r2));
+      L2 = max(0, min(L2, kFineBits));
+      P.level2 = L2;
+      P.cell2 = ldexpf(fine, L2);
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
 // 6. cell table
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void cell_of_key(u64 key, const GridParams* prm, int& c, unsigned& prefix,
-                                            int& x, int& y, int& z) {
+__device__ __forceinline__ int level_of(const GridParams& P, int which) {
+  return which ? P.level2 : P.level;
+}
+
+__device__ __forceinline__ void cell_of_key(u64 key, const GridParams* prm, int which, int& c,
+                                            unsigned& prefix, int& x, int& y, int& z) {
   c = (int)(key >> 30);
   const unsigned m = (unsigned)(key & 0x3fffffffu);
-  const int L = prm[c].level;
+  const int L = level_of(prm[c], which);
   prefix = m >> (3 * L);
   x = (int)(compact3(m) >> L);
   y = (int)(compact3(m >> 1) >> L);
@@ -523,14 +539,14 @@ __device__ __forceinline__ bool same_cell(u64 a, u64 b, int L) {
 }
 
 __global__ void k_cells_insert(const u64* __restrict__ keys, int64_t n, const GridParams* prm,
-                               CellEntry* tab, unsigned mask) {
+                               int which, CellEntry* tab, unsigned mask) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const u64 key = keys[i];
   int c, x, y, z;
   unsigned prefix;
-  cell_of_key(key, prm, c, prefix, x, y, z);
-  if (i > 0 && same_cell(keys[i - 1], key, prm[c].level)) return;
+  cell_of_key(key, prm, which, c, prefix, x, y, z);
+  if (i > 0 && same_cell(keys[i - 1], key, level_of(prm[c], which))) return;
   const u64 K = cell_key(c, x, y, z);
   unsigned h = hash_key(K) & mask;
   for (unsigned probe = 0; probe <= mask; ++probe) {
@@ -543,14 +559,14 @@ __global__ void k_cells_insert(const u64* __restrict__ keys, int64_t n, const Gr
 }
 
 __global__ void k_cells_count(const u64* __restrict__ keys, int64_t n, const GridParams* prm,
-                              CellEntry* tab, unsigned mask) {
+                              int which, CellEntry* tab, unsigned mask) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const u64 key = keys[i];
   int c, x, y, z;
   unsigned prefix;
-  cell_of_key(key, prm, c, prefix, x, y, z);
-  if (i + 1 < n && same_cell(keys[i + 1], key, prm[c].level)) return;
+  cell_of_key(key, prm, which, c, prefix, x, y, z);
+  if (i + 1 < n && same_cell(keys[i + 1], key, level_of(prm[c], which))) return;
   const u64 K = cell_key(c, x, y, z);
   unsigned h = hash_key(K) & mask;
   for (unsigned probe = 0; probe <= mask; ++probe) {
@@ -565,9 +581,10 @@ __global__ void k_cells_count(const u64* __restrict__ keys, int64_t n, const Gri
 // ---------------------------------------------------------------------------
 // host drivers
 // ---------------------------------------------------------------------------
-void grid_plan(GridPlan& p, Workspace& ws, int64_t n, int clouds) {
+void grid_plan(GridPlan& p, Workspace& ws, int64_t n, int clouds, bool icp_table) {
   p.n = n;
   p.clouds = clouds;
+  p.icp_table = icp_table;
   const uint64_t slots = next_pow2_u32((uint64_t)(n > 0 ? 2 * n : 2));
   p.mask = (unsigned)(slots - 1);
   p.radix_blocks = ceil_div(n > 0 ? n : 1, kRsTile);
@@ -581,6 +598,7 @@ void grid_plan(GridPlan& p, Workspace& ws, int64_t n, int clouds) {
   p.o_counts = ws.reserve(sizeof(int) * (size_t)kRadix * p.radix_blocks);
   p.o_scan = ws.reserve(sizeof(int) * scan_tmp_ints((int64_t)kRadix * p.radix_blocks));
   p.o_starts = 0;
+  p.o_tab2 = icp_table ? ws.reserve(sizeof(CellEntry) * slots) : 0;
 }
 
 GridView grid_view(const GridPlan& p, const Workspace& ws) {
@@ -589,6 +607,8 @@ GridView grid_view(const GridPlan& p, const Workspace& ws) {
   g.pts = ws.at<float4>(p.o_pts);
   g.tab = ws.at<CellEntry>(p.o_tab);
   g.mask = p.mask;
+  g.tab2 = p.icp_table ? ws.at<CellEntry>(p.o_tab2) : nullptr;
+  g.mask2 = p.mask;
   return g;
 }
 
@@ -609,6 +629,10 @@ cil_status grid_build(const GridPlan& p, const Workspace& ws, const float* xyz,
   if (cudaMemsetAsync(ws.at<CellEntry>(p.o_tab), 0xff, sizeof(CellEntry) * (size_t)slots, s) !=
       cudaSuccess)
     return CIL_ERR_CUDA;
+  if (p.icp_table &&
+      cudaMemsetAsync(ws.at<CellEntry>(p.o_tab2), 0xff, sizeof(CellEntry) * (size_t)slots, s) !=
+          cudaSuccess)
+    return CIL_ERR_CUDA;
   if (n > 0) {
     u64* k0 = ws.at<u64>(p.o_keys0);
     u64* k1 = ws.at<u64>(p.o_keys1);
@@ -623,9 +647,17 @@ cil_status grid_build(const GridPlan& p, const Workspace& ws, const float* xyz,
     float4* pts = ws.at<float4>(p.o_pts);
     k_gather_sorted<<<ceil_div(n, 256), 256, 0, s>>>(ks, vs, n, xyz, prm, pts);
     k_choose_level<<<p.clouds, 256, 0, s>>>(prm, pts, opt.k_est, nullptr, opt.cell_size,
-                                            opt.cell_scale);
-    k_cells_insert<<<ceil_div(n, 256), 256, 0, s>>>(ks, n, prm, ws.at<CellEntry>(p.o_tab), p.mask);
-    k_cells_count<<<ceil_div(n, 256), 256, 0, s>>>(ks, n, prm, ws.at<CellEntry>(p.o_tab), p.mask);
+                                            opt.cell_scale, p.icp_table ? opt.icp_dmax : 0.0f,
+                                            opt.icp_scale > 0.0f ? opt.icp_scale : 0.5f);
+    k_cells_insert<<<ceil_div(n, 256), 256, 0, s>>>(ks, n, prm, 0, ws.at<CellEntry>(p.o_tab), p.mask);
+    k_cells_count<<<ceil_div(n, 256), 256, 0, s>>>(ks, n, prm, 0, ws.at<CellEntry>(p.o_tab), p.mask);
+    if (p.icp_table) {
+      note_launches(2);
+      k_cells_insert<<<ceil_div(n, 256), 256, 0, s>>>(ks, n, prm, 1, ws.at<CellEntry>(p.o_tab2),
+                                                      p.mask);
+      k_cells_count<<<ceil_div(n, 256), 256, 0, s>>>(ks, n, prm, 1, ws.at<CellEntry>(p.o_tab2),
+                                                     p.mask);
+    }
   }
   return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
 }

@@ -56,12 +56,16 @@ struct IcpArgs {
   int* err;
 };
 
-// nearest target point within dmax2, also returning the point itself
+// nearest target point within dmax2, also returning the point itself; uses
+// the correspondence level (cells >= d_max / 2) when its table was built
 __device__ __forceinline__ u64 nearest_within(const GridView& g, int cloud, const float q[3],
                                               float dmax2, float4& bp) {
   const GridParams& P = g.prm[cloud];
+  const bool lvl2 = g.tab2 != nullptr && P.level2 >= 0;
+  const CellEntry* tab = lvl2 ? g.tab2 : g.tab;
+  const unsigned mask = lvl2 ? g.mask2 : g.mask;
   CellFrame f;
-  f.load(P, cloud);
+  f.load_level(P, cloud, lvl2 ? P.level2 : P.level, lvl2 ? P.cell2 : P.cell);
   const int cx = f.cell_of(q[0], 0, P.inv_fine);
   const int cy = f.cell_of(q[1], 1, P.inv_fine);
   const int cz = f.cell_of(q[2], 2, P.inv_fine);
@@ -78,7 +82,7 @@ __device__ __forceinline__ u64 nearest_within(const GridView& g, int cloud, cons
       const int c3[3] = {x, y, z};
       if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > lim) continue;
       int s, n;
-      if (!cell_lookup(g, cell_key(cloud, x, y, z), s, n)) continue;
+      if (!table_lookup(tab, mask, cell_key(cloud, x, y, z), s, n)) continue;
       for (int j = s; j < s + n; ++j) {
         const float4 p = __ldg(g.pts + j);
         const float d2 = sqdist(p.x, p.y, p.z, q[0], q[1], q[2]);

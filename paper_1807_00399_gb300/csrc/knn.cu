@@ -10,7 +10,8 @@
 // the k neighbours' offsets from the query give their mean, then the centred
 // covariance C = (1/m) sum (p - mu)(p - mu)^T in a second pass; its smallest
 // eigenpair comes from the closed-form trigonometric solution of the
-// characteristic cubic plus a cross product of two rows of C - l0 I.
+// characteristic cubic, a cross product of two rows of C - l0 I and one
+// Rayleigh-quotient refinement of l0.
 #include <math.h>
 
 #include "cil_host.h"
@@ -54,8 +55,90 @@ __global__ void __launch_bounds__(256) k_knn(GridView g, const float* __restrict
   }
 }
 
+// Unit null vector of the symmetric matrix A - l I: the largest cross product
+// of two of its rows (selects only, so everything stays in registers).  When
+// A - l I has rank <= 1, any unit vector orthogonal to its largest row.
+__device__ __forceinline__ void null_vector3(float a00, float a01, float a02, float a11, float a12,
+                                             float a22, float l, float nv[3]) {
+  const float r0x = a00 - l, r0y = a01, r0z = a02;
+  const float r1x = a01, r1y = a11 - l, r1z = a12;
+  const float r2x = a02, r2y = a12, r2z = a22 - l;
+  const float ax = r0y * r1z - r0z * r1y, ay = r0z * r1x - r0x * r1z, az = r0x * r1y - r0y * r1x;
+  const float bx = r0y * r2z - r0z * r2y, by = r0z * r2x - r0x * r2z, bz = r0x * r2y - r0y * r2x;
+  const float cx = r1y * r2z - r1z * r2y, cy = r1z * r2x - r1x * r2z, cz = r1x * r2y - r1y * r2x;
+  const float ma = ax * ax + ay * ay + az * az;
+  const float mb = bx * bx + by * by + bz * bz;
+  const float mc = cx * cx + cy * cy + cz * cz;
+  float vx = ax, vy = ay, vz = az, best = ma;
+  if (mb > best) {
+    vx = bx;
+    vy = by;
+    vz = bz;
+    best = mb;
+  }
+  if (mc > best) {
+    vx = cx;
+    vy = cy;
+    vz = cz;
+    best = mc;
+  }
+  if (best > 0.0f) {
+    const float in = rsqrtf(best);
+    nv[0] = vx * in;
+    nv[1] = vy * in;
+    nv[2] = vz * in;
+    return;
+  }
+  const float m0 = r0x * r0x + r0y * r0y + r0z * r0z;
+  const float m1 = r1x * r1x + r1y * r1y + r1z * r1z;
+  const float m2 = r2x * r2x + r2y * r2y + r2z * r2z;
+  float ex = r0x, ey = r0y, ez = r0z, em = m0;
+  if (m1 > em) {
+    ex = r1x;
+    ey = r1y;
+    ez = r1z;
+    em = m1;
+  }
+  if (m2 > em) {
+    ex = r2x;
+    ey = r2y;
+    ez = r2z;
+  }
+  float ux, uy, uz;
+  if (fabsf(ex) <= fabsf(ey) && fabsf(ex) <= fabsf(ez)) {
+    ux = 0.0f;
+    uy = ez;
+    uz = -ey;
+  } else if (fabsf(ey) <= fabsf(ez)) {
+    ux = -ez;
+    uy = 0.0f;
+    uz = ex;
+  } else {
+    ux = ey;
+    uy = -ex;
+    uz = 0.0f;
+  }
+  const float mu = ux * ux + uy * uy + uz * uz;
+  if (mu > 0.0f) {
+    const float in = rsqrtf(mu);
+    nv[0] = ux * in;
+    nv[1] = uy * in;
+    nv[2] = uz * in;
+  } else {
+    nv[0] = 0.0f;
+    nv[1] = 0.0f;
+    nv[2] = 1.0f;
+  }
+}
+
 // Smallest eigenpair of a symmetric 3x3 (c00, c01, c02, c11, c12, c22).
-// Returns false (and NaN) for a zero matrix.
+// Eigenvalues from the closed-form trigonometric solution of the
+// characteristic cubic (matrix scaled to max |entry| = 1); the eigenvector of
+// the smallest as the null vector of A - l0 I.  The trigonometric l0 carries
+// an absolute error of tens of ulps of the largest eigenvalue, which would
+// tilt the vector by that error over the gap l1 - l0; one Rayleigh-quotient
+// step l0 <- v^T A v (error quadratic in the tilt) and a second null-vector
+// solve remove it.  Returns false (and NaN) for a zero matrix.
 __device__ __forceinline__ bool sym3_smallest(const float C[6], float ev[3], float nv[3]) {
   float s = 0.0f;
 #pragma unroll
@@ -89,80 +172,15 @@ __device__ __forceinline__ bool sym3_smallest(const float C[6], float ev[3], flo
     const float phi = acosf(r) * (1.0f / 3.0f);
     l2 = q + 2.0f * p * cosf(phi);
     l0 = q + 2.0f * p * cosf(phi + 2.0943951023931957f);
+    null_vector3(a00, a01, a02, a11, a12, a22, l0, nv);
+    // Rayleigh-quotient refinement of l0, then the vector again
+    const float v0 = nv[0], v1 = nv[1], v2 = nv[2];
+    const float w0 = a00 * v0 + a01 * v1 + a02 * v2;
+    const float w1 = a01 * v0 + a11 * v1 + a12 * v2;
+    const float w2 = a02 * v0 + a12 * v1 + a22 * v2;
+    l0 = v0 * w0 + v1 * w1 + v2 * w2;
+    null_vector3(a00, a01, a02, a11, a12, a22, l0, nv);
     l1 = 3.0f * q - l0 - l2;
-    // eigenvector of l0: the largest cross product of two rows of A - l0 I
-    // (selects only: no dynamically indexed arrays, everything in registers)
-    const float r0x = a00 - l0, r0y = a01, r0z = a02;
-    const float r1x = a01, r1y = a11 - l0, r1z = a12;
-    const float r2x = a02, r2y = a12, r2z = a22 - l0;
-    const float ax = r0y * r1z - r0z * r1y, ay = r0z * r1x - r0x * r1z, az = r0x * r1y - r0y * r1x;
-    const float bx = r0y * r2z - r0z * r2y, by = r0z * r2x - r0x * r2z, bz = r0x * r2y - r0y * r2x;
-    const float cx = r1y * r2z - r1z * r2y, cy = r1z * r2x - r1x * r2z, cz = r1x * r2y - r1y * r2x;
-    const float ma = ax * ax + ay * ay + az * az;
-    const float mb = bx * bx + by * by + bz * bz;
-    const float mc = cx * cx + cy * cy + cz * cz;
-    float vx = ax, vy = ay, vz = az, best = ma;
-    if (mb > best) {
-      vx = bx;
-      vy = by;
-      vz = bz;
-      best = mb;
-    }
-    if (mc > best) {
-      vx = cx;
-      vy = cy;
-      vz = cz;
-      best = mc;
-    }
-    if (best > 0.0f) {
-      const float in = rsqrtf(best);
-      nv[0] = vx * in;
-      nv[1] = vy * in;
-      nv[2] = vz * in;
-    } else {
-      // A - l0 I has rank <= 1 (l0 = l1): any unit vector orthogonal to its
-      // largest row is an eigenvector of l0
-      const float m0 = r0x * r0x + r0y * r0y + r0z * r0z;
-      const float m1 = r1x * r1x + r1y * r1y + r1z * r1z;
-      const float m2 = r2x * r2x + r2y * r2y + r2z * r2z;
-      float ex = r0x, ey = r0y, ez = r0z, em = m0;
-      if (m1 > em) {
-        ex = r1x;
-        ey = r1y;
-        ez = r1z;
-        em = m1;
-      }
-      if (m2 > em) {
-        ex = r2x;
-        ey = r2y;
-        ez = r2z;
-      }
-      float ux, uy, uz;
-      if (fabsf(ex) <= fabsf(ey) && fabsf(ex) <= fabsf(ez)) {
-        ux = 0.0f;
-        uy = ez;
-        uz = -ey;
-      } else if (fabsf(ey) <= fabsf(ez)) {
-        ux = -ez;
-        uy = 0.0f;
-        uz = ex;
-      } else {
-        ux = ey;
-        uy = -ex;
-        uz = 0.0f;
-      }
-      const float mu = ux * ux + uy * uy + uz * uz;
-      if (mu > 0.0f) {
-        const float in = rsqrtf(mu);
-        nv[0] = ux * in;
-        nv[1] = uy * in;
-        nv[2] = uz * in;
-      } else {
-        nv[0] = 0.0f;
-        nv[1] = 0.0f;
-        nv[2] = 1.0f;
-      }
-    }
   }
   ev[0] = l0 * s;
   ev[1] = l1 * s;
