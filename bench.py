@@ -155,36 +155,32 @@ def _barrier(ws: int):
 # ---------------------------------------------------------------------------
 # oracle pipeline (reference arm and CPU baseline)
 # ---------------------------------------------------------------------------
-def oracle_step(pair, frac: float, rng_seed: int = 0):
+def oracle_step(pair, frac: float, rng_seed: int = 0, full_normals=None):
     """The oracle's pipeline on a sample: normals of frac * N_t target points
-    (neighbourhoods in the full cloud) and ICP of frac * N_s source points
-    against the full target.  Returns (queries, seconds, rmse)."""
+    (neighbourhoods searched in the full cloud) and 30-round ICP of frac * N_s
+    source points against the full target.  With frac < 1 the ICP uses normals
+    of every target point, computed once outside the timing (`full_normals`).
+    Returns (target queries, seconds, final rmse)."""
     import oracle
     rng = np.random.default_rng(rng_seed)
     nt, ns = len(pair.target), len(pair.source)
     m_t = max(1, int(round(frac * nt)))
     m_s = max(1, int(round(frac * ns)))
-    sel_t = np.sort(rng.choice(nt, m_t, replace=False)) if m_t < nt else np.arange(nt)
-    sel_s = np.sort(rng.choice(ns, m_s, replace=False)) if m_s < ns else np.arange(ns)
     t0 = time.perf_counter()
     if m_t < nt:
-        on, _, _ = oracle.normals_subset(pair.target, sel_t, K_NN, pair.viewpoint, method="kdtree")
-        nrm = np.full((nt, 3), np.nan, np.float32)
-        nrm[sel_t] = on
-        # ICP needs normals at every target point it may match: compute the rest
-        # outside the timed part would undercount; instead time the full normals
-        # share proportionally (frac of the full normals pass)
+        sel_t = np.sort(rng.choice(nt, m_t, replace=False))
+        sel_s = np.sort(rng.choice(ns, m_s, replace=False))
+        oracle.normals_subset(pair.target, sel_t, K_NN, pair.viewpoint, method="kdtree")
+        t_norm = time.perf_counter() - t0
+        nrm = full_normals
+        src = pair.source[sel_s]
     else:
         on, _, _ = oracle.normals(pair.target, K_NN, pair.viewpoint, method="kdtree")
+        t_norm = time.perf_counter() - t0
         nrm = on.astype(np.float32)
-    t_norm = time.perf_counter() - t0
-    if m_t < nt:
-        # normals for all target points (untimed) so the ICP sample matches
-        on_all, _, _ = oracle.normals(pair.target, K_NN, pair.viewpoint, method="kdtree")
-        nrm = on_all.astype(np.float32)
+        src = pair.source
     t1 = time.perf_counter()
-    out = oracle.icp(pair.source[sel_s], pair.target, nrm, iters=ICP_ITERS, max_corr_dist=DMAX,
-                     method="kdtree")
+    out = oracle.icp(src, pair.target, nrm, iters=ICP_ITERS, max_corr_dist=DMAX, method="kdtree")
     t_icp = time.perf_counter() - t1
     return m_t, t_norm + t_icp, out["rmse"]
 
@@ -197,11 +193,13 @@ def run_reference(args):
     from paper_1807_00399_gb300 import synth
     pair = synth.depth_frame_pair(args.seed)
     frac = 0.25
+    on, _, _ = oracle.normals(pair.target, K_NN, pair.viewpoint, method="kdtree")
+    nrm = on.astype(np.float32)
     for _ in range(args.warmup):
-        oracle_step(pair, frac)
+        oracle_step(pair, frac, full_normals=nrm)
     q_tot, t_tot, rmse = 0, 0.0, float("nan")
     for i in range(args.steps):
-        q, t, rmse = oracle_step(pair, frac, rng_seed=i)
+        q, t, rmse = oracle_step(pair, frac, rng_seed=i, full_normals=nrm)
         q_tot += q
         t_tot += t
     value = q_tot / t_tot
@@ -348,6 +346,11 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": alg[dom], "ms_per_launch": per_launch_ms[dom],
                 "peak_kind": peak_kind}
 
+    # ---- batched registration vs sequential plain calls (256 uneven pairs) ----
+    batched = None
+    if not args.no_batch:
+        batched = run_batched(args, rank)
+
     # ---- CPU baseline (oracle, rank 0, N = 1 only) ----
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
@@ -381,6 +384,7 @@ def run_ours(args):
             "roofline": roofline,
             "kernels_ms_per_launch": per_launch_ms,
             "cpu_baseline": cpu,
+            "batched": batched,
             "gpu_launches": int(n1 - n0),
             "clocks": clocks,
         }
@@ -391,6 +395,72 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args, rank: int, B: int = 256, runs: int = 5):
+    """256 wavy-surface pairs with point counts log-uniform in [2e3, 2e5]:
+    one graph launch (grid + 10-NN normals + 30 ICP rounds for every pair)
+    against 256 sequential single-pair calls of the same pipeline; both reach
+    the same per-pair RMSE (the batched results are bitwise those of the
+    single-pair calls)."""
+    import torch
+
+    import paper_1807_00399_gb300 as cil
+    from paper_1807_00399_gb300 import synth
+
+    sizes = synth.batch_sizes(args.seed + rank, B)
+    src, dst, T_gt = synth.surface_batch_torch(1000 + args.seed + rank, sizes)
+    h = cil.Batch(sizes, sizes, k=K_NN, iters=ICP_ITERS, max_corr_dist=0.1,
+                  viewpoint=(0.0, 0.0, 10.0))
+    T = torch.empty((B, 16), dtype=torch.float64, device="cuda")
+    rep = torch.empty((B, 32), dtype=torch.uint8, device="cuda")
+    h.run(src, dst, T_out=T, rep=rep)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(runs)]
+    for a, b in ev:
+        a.record()
+        h.run(src, dst, T_out=T, rep=rep)
+        b.record()
+    torch.cuda.synchronize()
+    ms_b = float(np.median([a.elapsed_time(b) for a, b in ev]))
+    reps_b = cil.decode_reports(rep, B)
+    # sequential plain calls
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    Ts = torch.empty((B, 16), dtype=torch.float64, device="cuda")
+    reps_s = torch.empty((B, 32), dtype=torch.uint8, device="cuda")
+    nrm = torch.empty_like(dst)
+
+    def seq():
+        for i in range(B):
+            s0, s1 = int(off[i]), int(off[i + 1])
+            cil.register_pair(src[s0:s1], dst[s0:s1], K_NN, (0.0, 0.0, 10.0), ICP_ITERS, 0.1,
+                              out_normals=nrm[s0:s1], out_T=Ts[i], out_report=reps_s[i])
+    seq()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    seq()
+    b.record()
+    torch.cuda.synchronize()
+    ms_s = a.elapsed_time(b)
+    rs = cil.decode_reports(reps_s, B)
+    rb = np.array([r["rmse"] for r in reps_b])
+    rq = np.array([r["rmse"] for r in rs])
+    h.close()
+    Tb = T.cpu().numpy().reshape(B, 4, 4)
+    Rg = T_gt.cpu().numpy()
+    M = Tb[:, :3, :3] @ np.transpose(Rg[:, :3, :3], (0, 2, 1))
+    rot_err = np.degrees(np.arccos(np.clip((np.trace(M, axis1=1, axis2=2) - 1) / 2, -1, 1)))
+    return {"pairs": B, "points_per_side": int(sizes.sum()),
+            "ms_batched_graph": ms_b, "pairs_per_s_batched": B / (ms_b / 1e3),
+            "ms_sequential_plain": ms_s, "pairs_per_s_plain": B / (ms_s / 1e3),
+            "speedup": ms_s / ms_b,
+            "max_abs_rmse_diff": float(np.nanmax(np.abs(rb - rq))),
+            "median_rmse": float(np.nanmedian(rb)),
+            "success_rate_rmse_lt_0.005": float(np.mean(np.nan_to_num(rb, nan=1.0) < 0.005)),
+            "median_rot_err_deg_vs_generator": float(np.median(rot_err))}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -399,6 +469,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the 256-pair batched-vs-sequential measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -71,8 +71,11 @@ def _load():
     lib.oracle_normals.argtypes = [P, I64, I, P, P, P, P, I, I]
     lib.oracle_normals_subset.argtypes = [P, I64, P, I64, I, P, P, P, P, I, I]
     lib.oracle_icp.argtypes = [P, I64, P, P, I64, P, I, D, P, P, P, P, P, P, I, I]
+    lib.oracle_knn_hybrid.argtypes = [P, I64, P, I64, I, D, P, P, I]
+    lib.oracle_normals_radius.argtypes = [P, I64, D, P, P, P, P, P, I]
     for f in ("oracle_knn", "oracle_knn_kdtree", "oracle_radius", "oracle_sym3_eigen",
-              "oracle_normals", "oracle_normals_subset", "oracle_icp"):
+              "oracle_normals", "oracle_normals_subset", "oracle_icp", "oracle_knn_hybrid",
+              "oracle_normals_radius"):
         getattr(lib, f).restype = I
     _lib = lib
     return lib
@@ -129,6 +132,39 @@ def radius(ref, qry, r: float, threads: int = 0):
     if rc:
         raise RuntimeError("oracle radius failed")
     return off, idx[:nnz], d2[:nnz]
+
+
+def knn_hybrid(ref, qry, k: int, r: float, threads: int = 0):
+    """The k nearest neighbours among those within r (inclusive): (idx, d2),
+    padded with -1 / inf.  r is taken as its float32 value, promoted."""
+    lib = _load()
+    ref = _pts(ref)
+    qry = _pts(qry)
+    idx = np.empty((qry.shape[0], k), np.int32)
+    d2 = np.empty((qry.shape[0], k), np.float64)
+    rc = lib.oracle_knn_hybrid(_p(ref), ref.shape[0], _p(qry), qry.shape[0], int(k),
+                               float(np.float32(r)), _p(idx), _p(d2), int(threads))
+    if rc:
+        raise RuntimeError("oracle knn_hybrid failed")
+    return idx, d2
+
+
+def normals_radius(xyz, r: float, viewpoint, threads: int = 0):
+    """PCA normals over radius neighbourhoods (every point within r, itself
+    included): (normals, curvature, evals, neighbour counts)."""
+    lib = _load()
+    xyz = _pts(xyz)
+    n = xyz.shape[0]
+    vp = np.ascontiguousarray(viewpoint, np.float64).reshape(3)
+    nrm = np.empty((n, 3), np.float64)
+    cur = np.empty(n, np.float64)
+    ev = np.empty((n, 3), np.float64)
+    cnt = np.empty(n, np.int64)
+    rc = lib.oracle_normals_radius(_p(xyz), n, float(np.float32(r)), _p(vp), _p(nrm), _p(cur),
+                                   _p(ev), _p(cnt), int(threads))
+    if rc:
+        raise RuntimeError("oracle normals_radius failed")
+    return nrm, cur, ev, cnt
 
 
 def sym3_eigen(C):

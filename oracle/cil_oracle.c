@@ -835,3 +835,117 @@ int oracle_icp(const float *src, int64_t n_src, const float *dst, const float *d
   if (use_kdtree) kd_free(&tree);
   return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* hybrid query: the k nearest points among those within distance r           */
+/* (Sec. 3, KDTree "hybrid" queries): exhaustive search, (d2, idx) order,      */
+/* missing entries padded with -1 / +inf                                        */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  const float *ref, *qry;
+  int64_t n_ref;
+  int k;
+  double r2;
+  int32_t *out_idx;
+  double *out_d2;
+} hyb_ctx;
+
+static void hyb_range(void *vctx, int64_t lo, int64_t hi, int tid) {
+  (void)tid;
+  hyb_ctx *c = (hyb_ctx *)vctx;
+  for (int64_t q = lo; q < hi; ++q) {
+    double *d = c->out_d2 + q * c->k;
+    int32_t *ix = c->out_idx + q * c->k;
+    int len = 0;
+    for (int64_t i = 0; i < c->n_ref; ++i) {
+      double dd = dist2(c->qry + 3 * q, c->ref + 3 * i);
+      if (dd <= c->r2) topk_insert(d, ix, &len, c->k, dd, (int32_t)i);
+    }
+    pad_topk(d, ix, len, c->k);
+  }
+}
+
+int oracle_knn_hybrid(const float *ref, int64_t n_ref, const float *qry, int64_t n_qry, int k,
+                      double r, int32_t *out_idx, double *out_d2, int n_threads) {
+  if (k <= 0 || r < 0 || n_ref < 0 || n_qry < 0) return 1;
+  hyb_ctx c = {ref, qry, n_ref, k, r * r, out_idx, out_d2};
+  parallel_for(n_qry, n_threads, hyb_range, &c);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* normals from radius neighbourhoods (Sec. 3; Sec. 4 uses a 1 cm radius):    */
+/* every point within r (inclusive, the point itself included), then the same */
+/* covariance / Jacobi / orientation / curvature as oracle_normals            */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  const float *xyz;
+  int64_t n;
+  double r2;
+  const double *vp;
+  double *normals, *curv, *evals;
+  int64_t *counts;
+} nrr_ctx;
+
+static void nrr_range(void *vctx, int64_t lo, int64_t hi, int tid) {
+  (void)tid;
+  nrr_ctx *c = (nrr_ctx *)vctx;
+  for (int64_t i = lo; i < hi; ++i) {
+    const float *p = c->xyz + 3 * i;
+    double mu[3] = {0, 0, 0};
+    int64_t m = 0;
+    for (int64_t j = 0; j < c->n; ++j)
+      if (dist2(p, c->xyz + 3 * j) <= c->r2) {
+        for (int a = 0; a < 3; ++a) mu[a] += (double)c->xyz[3 * j + a];
+        ++m;
+      }
+    if (c->counts) c->counts[i] = m;
+    double *nout = c->normals + 3 * i;
+    double ev[3] = {NAN, NAN, NAN};
+    nout[0] = nout[1] = nout[2] = NAN;
+    c->curv[i] = NAN;
+    if (m >= 3) {
+      for (int a = 0; a < 3; ++a) mu[a] /= (double)m;
+      double C[6] = {0, 0, 0, 0, 0, 0};
+      for (int64_t j = 0; j < c->n; ++j)
+        if (dist2(p, c->xyz + 3 * j) <= c->r2) {
+          const float *q = c->xyz + 3 * j;
+          double e0 = q[0] - mu[0], e1 = q[1] - mu[1], e2 = q[2] - mu[2];
+          C[0] += e0 * e0;
+          C[1] += e0 * e1;
+          C[2] += e0 * e2;
+          C[3] += e1 * e1;
+          C[4] += e1 * e2;
+          C[5] += e2 * e2;
+        }
+      for (int t = 0; t < 6; ++t) C[t] /= (double)m;
+      double vec[9];
+      oracle_sym3_eigen(C, ev, vec);
+      double tr = ev[0] + ev[1] + ev[2];
+      if (tr > 0) {
+        double nx = vec[0], ny = vec[3], nz = vec[6];
+        double s = nx * (c->vp[0] - p[0]) + ny * (c->vp[1] - p[1]) + nz * (c->vp[2] - p[2]);
+        if (s < 0) {
+          nx = -nx;
+          ny = -ny;
+          nz = -nz;
+        }
+        nout[0] = nx;
+        nout[1] = ny;
+        nout[2] = nz;
+        c->curv[i] = ev[0] / tr;
+      }
+    }
+    if (c->evals)
+      for (int a = 0; a < 3; ++a) c->evals[3 * i + a] = ev[a];
+  }
+}
+
+int oracle_normals_radius(const float *xyz, int64_t n, double r, const double *viewpoint,
+                          double *normals, double *curvature, double *evals, int64_t *counts,
+                          int n_threads) {
+  if (r < 0 || n < 0) return 1;
+  nrr_ctx c = {xyz, n, r * r, viewpoint, normals, curvature, evals, counts};
+  parallel_for(n, n_threads, nrr_range, &c);
+  return 0;
+}

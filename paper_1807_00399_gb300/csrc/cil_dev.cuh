@@ -372,4 +372,32 @@ struct KSum {
   }
 };
 
+// Host-side dispatch of a kernel template on the smallest compiled register
+// top-k capacity KM >= k (k in 1..32).
+#define CIL_FOR_K(k, CALL)          \
+  do {                              \
+    if ((k) <= 1) {                 \
+      constexpr int KM = 1;         \
+      CALL;                         \
+    } else if ((k) <= 4) {          \
+      constexpr int KM = 4;         \
+      CALL;                         \
+    } else if ((k) <= 8) {          \
+      constexpr int KM = 8;         \
+      CALL;                         \
+    } else if ((k) <= 10) {         \
+      constexpr int KM = 10;        \
+      CALL;                         \
+    } else if ((k) <= 16) {         \
+      constexpr int KM = 16;        \
+      CALL;                         \
+    } else if ((k) <= 24) {         \
+      constexpr int KM = 24;        \
+      CALL;                         \
+    } else {                        \
+      constexpr int KM = 32;        \
+      CALL;                         \
+    }                               \
+  } while (0)
+
 }  // namespace cil

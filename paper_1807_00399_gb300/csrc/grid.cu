@@ -443,24 +443,26 @@ __global__ void k_gather_sorted(const u64* __restrict__ keys, const int* __restr
 // ---------------------------------------------------------------------------
 // 5. level choice
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_choose_level(GridParams* prm, const float4* __restrict__ pts,
-                                                      int k_default, const int* cloud_k,
-                                                      float cell_size, float cell_scale,
-                                                      float icp_dmax, float icp_scale) {
+template <int KMAX>
+__global__ void __launch_bounds__(1024) k_choose_level(GridParams* prm, const float4* __restrict__ pts,
+                                                       int k_default, const int* cloud_k,
+                                                       float cell_size, float cell_scale,
+                                                       float icp_dmax, float icp_scale) {
   constexpr int S = 1024;
   __shared__ float est[S];
   GridParams& P = prm[blockIdx.x];
   const int n = P.n, s0 = P.start;
   int k = cloud_k ? cloud_k[blockIdx.x] : k_default;
-  k = max(1, min(k, 32));
+  k = max(1, min(k, KMAX));
   const int ns = min(S, n);
-  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+  {
+    const int s = threadIdx.x;  // one sample per thread
     float e = __int_as_float(0x7f800000);
     if (s < ns) {
       const int pos = s0 + (int)(((int64_t)s * n) / ns);
       const float4 q = pts[pos];
       const int W = 2 * k;
-      TopK<32> top;
+      TopK<KMAX> top;
       top.init(k);
       const int j0 = max(s0, pos - W), j1 = min(s0 + n - 1, pos + W);
       for (int j = j0; j <= j1; ++j) {
@@ -646,9 +648,11 @@ cil_status grid_build(const GridPlan& p, const Workspace& ws, const float* xyz,
     int* vs = which ? v1 : v0;
     float4* pts = ws.at<float4>(p.o_pts);
     k_gather_sorted<<<ceil_div(n, 256), 256, 0, s>>>(ks, vs, n, xyz, prm, pts);
-    k_choose_level<<<p.clouds, 256, 0, s>>>(prm, pts, opt.k_est, nullptr, opt.cell_size,
-                                            opt.cell_scale, p.icp_table ? opt.icp_dmax : 0.0f,
-                                            opt.icp_scale > 0.0f ? opt.icp_scale : 0.5f);
+    const int kk = opt.k_est < 1 ? 1 : (opt.k_est > 32 ? 32 : opt.k_est);
+    const float icp_d = p.icp_table ? opt.icp_dmax : 0.0f;
+    const float icp_s = opt.icp_scale > 0.0f ? opt.icp_scale : 0.5f;
+    CIL_FOR_K(kk, (k_choose_level<KM><<<p.clouds, 1024, 0, s>>>(prm, pts, kk, nullptr, opt.cell_size,
+                                                                opt.cell_scale, icp_d, icp_s)));
     k_cells_insert<<<ceil_div(n, 256), 256, 0, s>>>(ks, n, prm, 0, ws.at<CellEntry>(p.o_tab), p.mask);
     k_cells_count<<<ceil_div(n, 256), 256, 0, s>>>(ks, n, prm, 0, ws.at<CellEntry>(p.o_tab), p.mask);
     if (p.icp_table) {

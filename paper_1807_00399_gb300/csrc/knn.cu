@@ -288,33 +288,8 @@ __global__ void __launch_bounds__(256) k_normals(GridView g, int cloud_count, in
 
 // ---------------------------------------------------------------------------
 // host launchers: dispatch on the smallest compiled register capacity >= k
+// (CIL_FOR_K, cil_dev.cuh)
 // ---------------------------------------------------------------------------
-#define CIL_FOR_K(k, CALL)          \
-  do {                              \
-    if ((k) <= 1) {                 \
-      constexpr int KM = 1;         \
-      CALL;                         \
-    } else if ((k) <= 4) {          \
-      constexpr int KM = 4;         \
-      CALL;                         \
-    } else if ((k) <= 8) {          \
-      constexpr int KM = 8;         \
-      CALL;                         \
-    } else if ((k) <= 10) {         \
-      constexpr int KM = 10;        \
-      CALL;                         \
-    } else if ((k) <= 16) {         \
-      constexpr int KM = 16;        \
-      CALL;                         \
-    } else if ((k) <= 24) {         \
-      constexpr int KM = 24;        \
-      CALL;                         \
-    } else {                        \
-      constexpr int KM = 32;        \
-      CALL;                         \
-    }                               \
-  } while (0)
-
 cil_status launch_knn(const GridView& g, const float* qry, int64_t nq, const int* order, int k,
                       int* out_idx, float* out_d2, int block, cudaStream_t s) {
   if (nq <= 0) return CIL_OK;

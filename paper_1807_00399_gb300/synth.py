@@ -392,3 +392,51 @@ def lattice_points(shape=(4, 4, 4), spacing: float = 1.0, origin=(0.0, 0.0, 0.0)
     distance is an integer multiple of spacing^2, so ties are exact."""
     g = np.stack(np.meshgrid(*[np.arange(s) for s in shape], indexing="ij"), -1).reshape(-1, 3)
     return (g * spacing + np.asarray(origin)).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# the batch workload generated on the GPU (same distributions as
+# surface_pair / surface_batch, drawn with a seeded torch generator)
+# ---------------------------------------------------------------------------
+def surface_batch_torch(seed: int, sizes, noise: float = 0.002, max_angle_deg: float = 10.0,
+                        max_trans: float = 0.05, device="cuda"):
+    """Concatenated source and target clouds of len(sizes) wavy-surface pairs
+    (pair i has sizes[i] points on both sides), plus the source -> target
+    labels.  Returns (src float32 (sum,3), dst float32 (sum,3), T_gt float64
+    (B,4,4)), all on `device`."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    f64 = torch.float64
+    sizes = [int(n) for n in sizes]
+    tot = sum(sizes)
+    B = len(sizes)
+    pair_of = torch.repeat_interleave(torch.arange(B, device=device),
+                                      torch.tensor(sizes, device=device))
+
+    def surface(n):
+        xy = torch.rand(n, 2, generator=gen, device=device, dtype=f64) * 2 - 1
+        z = 0.1 * torch.sin(4 * xy[:, 0]) * torch.cos(4 * xy[:, 1])
+        p = torch.cat([xy, z[:, None]], 1)
+        return p + noise * torch.randn(n, 3, generator=gen, device=device, dtype=f64)
+
+    dst = surface(tot)
+    src0 = surface(tot)
+    axis = torch.randn(B, 3, generator=gen, device=device, dtype=f64)
+    axis = axis / axis.norm(dim=1, keepdim=True)
+    ang = torch.rand(B, generator=gen, device=device, dtype=f64) * math.radians(max_angle_deg)
+    # quaternion -> rotation matrix, as in rotation_from_axis_angle
+    w = torch.cos(ang / 2)
+    xyz = torch.sin(ang / 2)[:, None] * axis
+    x, y, z = xyz[:, 0], xyz[:, 1], xyz[:, 2]
+    R = torch.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                     2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                     2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], 1).reshape(B, 3, 3)
+    t = (torch.rand(B, 3, generator=gen, device=device, dtype=f64) * 2 - 1) * max_trans
+    src = torch.einsum("nij,nj->ni", R[pair_of], src0) + t[pair_of]
+    T = torch.zeros(B, 4, 4, dtype=f64, device=device)
+    Rt = R.transpose(1, 2)
+    T[:, :3, :3] = Rt
+    T[:, :3, 3] = -(Rt @ t[:, :, None])[:, :, 0]
+    T[:, 3, 3] = 1
+    return src.to(torch.float32).contiguous(), dst.to(torch.float32).contiguous(), T

@@ -146,3 +146,25 @@ def test_radius_empty_rows():
     qry = ref[:5] + 10.0
     off, idx, d2 = oracle.radius(ref, qry, 0.5)
     assert off.tolist() == [0] * 6 and idx.size == 0
+
+
+def test_hybrid_query_matches_library_bounded_search():
+    ref = _cloud(20, 4000)
+    qry = _cloud(21, 300)
+    k, r = 12, 0.12
+    idx, d2 = oracle.knn_hybrid(ref, qry, k, r)
+    rr = float(np.float32(r))
+    dd, ii = cKDTree(ref.astype(np.float64)).query(qry.astype(np.float64), k,
+                                                    distance_upper_bound=rr * (1 + 1e-12))
+    found = np.isfinite(dd)
+    assert np.array_equal(idx[found], ii[found])
+    assert np.all(idx[~found] == -1) and np.all(np.isinf(d2[~found]))
+    np.testing.assert_allclose(d2[found], dd[found] ** 2, rtol=1e-12)
+
+
+def test_hybrid_query_is_knn_truncated_by_radius():
+    pts = synth.lattice_points((5, 5, 5))
+    idx, d2 = oracle.knn_hybrid(pts, pts[62:63], 27, 1.0)
+    full, fd = oracle.knn(pts, pts[62:63], 27)
+    assert idx[0, :7].tolist() == full[0, :7].tolist()  # self + 6 face neighbours at d2 <= 1
+    assert np.all(idx[0, 7:] == -1)

@@ -140,3 +140,37 @@ def test_subset_route_equals_full():
     ns, cs, evs = oracle.normals_subset(pts, sel, 10, [0, 0, 10])
     np.testing.assert_allclose(ns, n[sel], atol=1e-14)
     np.testing.assert_allclose(cs, c[sel], atol=1e-15)
+
+
+def test_radius_normals_plane_and_star():
+    rng = np.random.default_rng(7)
+    xy = rng.uniform(-1, 1, size=(2000, 2))
+    pts = np.column_stack([xy, np.zeros(len(xy))]).astype(np.float32)
+    n, c, ev, cnt = oracle.normals_radius(pts, 0.1, [0, 0, 10])
+    ok = cnt >= 3
+    assert ok.mean() > 0.99
+    assert np.all(n[ok] == [0.0, 0.0, 1.0]) and np.all(c[ok] == 0.0)
+    assert np.isnan(n[~ok]).all()
+    # on the integer lattice a radius-1 ball is the 7-point star (covariance (2/7) I)
+    lat = synth.lattice_points((3, 3, 3))
+    n, c, ev, cnt = oracle.normals_radius(lat, 1.0, [0, 0, 10])
+    assert cnt[13] == 7 and abs(c[13] - 1.0 / 3.0) < 1e-15
+
+
+def test_radius_normals_equal_knn_normals_when_the_sets_coincide():
+    # when the radius ball holds exactly the k nearest points, both routes agree
+    pts = synth.surface_pair(8, n=3000).target
+    k = 10
+    idx, d2 = oracle.knn(pts, pts, k + 1)
+    # a radius strictly between the k-th and (k+1)-th distance of every point
+    # is not available globally, so compare per point with its own radius
+    sel = np.arange(0, 3000, 97)
+    nk, ck, _ = oracle.normals(pts, k, [0, 0, 10])
+    for i in sel:
+        r = float(np.sqrt(0.5 * (d2[i, k - 1] + d2[i, k])))
+        if not (np.float32(r) ** 2 > d2[i, k - 1] and np.float32(r) ** 2 < d2[i, k]):
+            continue
+        nr, cr, _, cnt = oracle.normals_radius(pts, r, [0, 0, 10])
+        assert cnt[i] == k
+        np.testing.assert_allclose(nr[i], nk[i], atol=1e-12)
+        assert abs(cr[i] - ck[i]) < 1e-15
