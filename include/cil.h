@@ -99,19 +99,27 @@ cil_status cil_knn_ex(const float *ref, int64_t n_ref, const float *qry, int64_t
                       int32_t *out_idx, float *out_d2, const cil_params *params, void *stream);
 
 /* ---------------------------------------------------------------------------
- * Radius search (Sec. 3, KDTree radius query): for every query all reference
- * points with squared distance <= r*r (inclusive), as CSR:
- *   out_offsets [n_qry+1] int64 (device): row q is [offsets[q], offsets[q+1])
- *   out_idx     [capacity] int32 (device), out_d2 [capacity] float (device,
- *               may be NULL); rows ascend by (d2, idx)
- *   out_nnz     host int64: total number of neighbours found
- * If the total exceeds `capacity`, nothing is written to out_idx/out_d2,
- * out_offsets holds the full CSR offsets, *out_nnz the required size, and the
- * call returns CIL_ERR_CAPACITY.  r >= 0.  Synchronises the stream.
+ * Hybrid query (Sec. 3, KDTree "hybrid" queries): for every query the k
+ * nearest reference points among those with squared distance <= r*r
+ * (inclusive).  Same layout, order and padding (-1 / +inf) as cil_knn; rows
+ * hold fewer than k valid entries when the ball holds fewer points.  r >= 0.
+ * Asynchronous.
  */
-cil_status cil_radius_search(const float *ref, int64_t n_ref, const float *qry, int64_t n_qry,
-                             float r, int64_t *out_offsets, int32_t *out_idx, float *out_d2,
-                             int64_t capacity, int64_t *out_nnz, void *stream);
+cil_status cil_knn_hybrid(const float *ref, int64_t n_ref, const float *qry, int64_t n_qry, int k,
+                          float r, int32_t *out_idx, float *out_d2, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * PCA normals over radius neighbourhoods (Sec. 3 normal estimation; Sec. 4
+ * compares 1 cm balls): for every point, all points within r (inclusive, the
+ * point itself included) form the neighbourhood; mean, centred covariance,
+ * smallest eigenvector, viewpoint orientation and curvature as in
+ * cil_estimate_normals.  out_counts [n] int32 (device, may be NULL) receives
+ * each neighbourhood's size; fewer than 3 neighbours give NaN.  r > 0.
+ * Asynchronous.
+ */
+cil_status cil_estimate_normals_radius(const float *xyz, int64_t n, float r, const float *viewpoint,
+                                       float *out_normals, float *out_curvature,
+                                       int32_t *out_counts, void *stream);
 
 /* ---------------------------------------------------------------------------
  * PCA surface normals and curvature (Sec. 3 normal/curvature estimation,

@@ -72,7 +72,7 @@ def _load():
     lib.oracle_normals_subset.argtypes = [P, I64, P, I64, I, P, P, P, P, I, I]
     lib.oracle_icp.argtypes = [P, I64, P, P, I64, P, I, D, P, P, P, P, P, P, I, I]
     lib.oracle_knn_hybrid.argtypes = [P, I64, P, I64, I, D, P, P, I]
-    lib.oracle_normals_radius.argtypes = [P, I64, D, P, P, P, P, P, I]
+    lib.oracle_normals_radius.argtypes = [P, I64, D, P, P, P, P, P, P, I64, I]
     for f in ("oracle_knn", "oracle_knn_kdtree", "oracle_radius", "oracle_sym3_eigen",
               "oracle_normals", "oracle_normals_subset", "oracle_icp", "oracle_knn_hybrid",
               "oracle_normals_radius"):
@@ -149,19 +149,23 @@ def knn_hybrid(ref, qry, k: int, r: float, threads: int = 0):
     return idx, d2
 
 
-def normals_radius(xyz, r: float, viewpoint, threads: int = 0):
+def normals_radius(xyz, r: float, viewpoint, sel=None, threads: int = 0):
     """PCA normals over radius neighbourhoods (every point within r, itself
-    included): (normals, curvature, evals, neighbour counts)."""
+    included): (normals, curvature, evals, neighbour counts), for every point
+    or only for the points `sel` (neighbourhoods still searched in all of xyz)."""
     lib = _load()
     xyz = _pts(xyz)
     n = xyz.shape[0]
     vp = np.ascontiguousarray(viewpoint, np.float64).reshape(3)
-    nrm = np.empty((n, 3), np.float64)
-    cur = np.empty(n, np.float64)
-    ev = np.empty((n, 3), np.float64)
-    cnt = np.empty(n, np.int64)
+    sel_a = None if sel is None else np.ascontiguousarray(sel, np.int64)
+    m = n if sel_a is None else sel_a.shape[0]
+    nrm = np.empty((m, 3), np.float64)
+    cur = np.empty(m, np.float64)
+    ev = np.empty((m, 3), np.float64)
+    cnt = np.empty(m, np.int64)
     rc = lib.oracle_normals_radius(_p(xyz), n, float(np.float32(r)), _p(vp), _p(nrm), _p(cur),
-                                   _p(ev), _p(cnt), int(threads))
+                                   _p(ev), _p(cnt), None if sel_a is None else _p(sel_a), m,
+                                   int(threads))
     if rc:
         raise RuntimeError("oracle normals_radius failed")
     return nrm, cur, ev, cnt

@@ -885,13 +885,14 @@ typedef struct {
   const double *vp;
   double *normals, *curv, *evals;
   int64_t *counts;
+  const int64_t *sel; /* NULL: every point; else the points to evaluate */
 } nrr_ctx;
 
 static void nrr_range(void *vctx, int64_t lo, int64_t hi, int tid) {
   (void)tid;
   nrr_ctx *c = (nrr_ctx *)vctx;
   for (int64_t i = lo; i < hi; ++i) {
-    const float *p = c->xyz + 3 * i;
+    const float *p = c->xyz + 3 * (c->sel ? c->sel[i] : i);
     double mu[3] = {0, 0, 0};
     int64_t m = 0;
     for (int64_t j = 0; j < c->n; ++j)
@@ -941,11 +942,13 @@ static void nrr_range(void *vctx, int64_t lo, int64_t hi, int tid) {
   }
 }
 
+/* sel (optional): evaluate only these points (outputs have n_sel rows); the
+ * neighbourhoods are always searched in the whole cloud */
 int oracle_normals_radius(const float *xyz, int64_t n, double r, const double *viewpoint,
                           double *normals, double *curvature, double *evals, int64_t *counts,
-                          int n_threads) {
-  if (r < 0 || n < 0) return 1;
-  nrr_ctx c = {xyz, n, r * r, viewpoint, normals, curvature, evals, counts};
-  parallel_for(n, n_threads, nrr_range, &c);
+                          const int64_t *sel, int64_t n_sel, int n_threads) {
+  if (r < 0 || n < 0 || (sel && n_sel < 0)) return 1;
+  nrr_ctx c = {xyz, n, r * r, viewpoint, normals, curvature, evals, counts, sel};
+  parallel_for(sel ? n_sel : n, n_threads, nrr_range, &c);
   return 0;
 }

@@ -81,6 +81,10 @@ def lib():
         L.cil_icp_batch_destroy.argtypes = [P]
         L.cil_icp_batch_destroy.restype = None
         L.cil_launch_count.restype = I64
+        L.cil_knn_hybrid.argtypes = [P, I64, P, I64, I, F, P, P, P]
+        L.cil_knn_hybrid.restype = I
+        L.cil_estimate_normals_radius.argtypes = [P, I64, F, P, P, P, P, P]
+        L.cil_estimate_normals_radius.restype = I
         L.cil_pointnet_num_params.restype = I
         L.cil_pointnet_create.argtypes = [I, I, P]
         L.cil_pointnet_destroy.argtypes = [P]
@@ -169,6 +173,37 @@ def knn(ref, qry, k: int, *, cell_size=0.0, cell_scale=0.0, block=0, with_d2=Tru
                           ctypes.byref(prm) if prm is not None else None, _stream(stream))
     _check(st, "cil_knn")
     return out_idx, out_d2
+
+
+def knn_hybrid(ref, qry, k: int, r: float, stream=None):
+    """k nearest neighbours within radius r (cil_knn_hybrid): (idx, d2), rows
+    padded with -1 / inf where the ball holds fewer than k points."""
+    torch = _torch()
+    ref = _points(ref, "ref")
+    qry = ref if qry is ref else _points(qry, "qry")
+    nq = qry.shape[0]
+    idx = torch.empty((nq, k), dtype=torch.int32, device=qry.device)
+    d2 = torch.empty((nq, k), dtype=torch.float32, device=qry.device)
+    st = lib().cil_knn_hybrid(_ptr(ref), ref.shape[0], _ptr(qry), nq, int(k), float(r), _ptr(idx),
+                              _ptr(d2), _stream(stream))
+    _check(st, "cil_knn_hybrid")
+    return idx, d2
+
+
+def estimate_normals_radius(xyz, r: float, viewpoint, stream=None):
+    """PCA normals over radius-r neighbourhoods (cil_estimate_normals_radius):
+    (normals, curvature, neighbour counts)."""
+    torch = _torch()
+    xyz = _points(xyz, "xyz")
+    n = xyz.shape[0]
+    nrm = torch.empty((n, 3), dtype=torch.float32, device=xyz.device)
+    cur = torch.empty(n, dtype=torch.float32, device=xyz.device)
+    cnt = torch.empty(n, dtype=torch.int32, device=xyz.device)
+    vp = (ctypes.c_float * 3)(*[float(v) for v in np.asarray(viewpoint, np.float64).reshape(3)])
+    st = lib().cil_estimate_normals_radius(_ptr(xyz), n, float(r), vp, _ptr(nrm), _ptr(cur),
+                                           _ptr(cnt), _stream(stream))
+    _check(st, "cil_estimate_normals_radius")
+    return nrm, cur, cnt
 
 
 def radius_search(ref, qry, r: float, capacity: int | None = None, stream=None):

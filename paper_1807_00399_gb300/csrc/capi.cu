@@ -263,6 +263,64 @@ cil_status cil_estimate_normals(const float* xyz, int64_t n, int k, const float*
   return cil_estimate_normals_ex(xyz, n, k, viewpoint, out_normals, out_curvature, nullptr, stream);
 }
 
+cil_status cil_knn_hybrid(const float* ref, int64_t n_ref, const float* qry, int64_t n_qry, int k,
+                          float r, int32_t* out_idx, float* out_d2, void* stream) {
+  if (k < 1 || k > CIL_MAX_K || bad_count(n_ref) || bad_count(n_qry) || !(r >= 0.0f) ||
+      !isfinite(r))
+    return CIL_ERR_INVALID_ARG;
+  if (n_qry == 0) return CIL_OK;
+  if (!qry || !out_idx || (n_ref > 0 && !ref)) return CIL_ERR_INVALID_ARG;
+  cil_status st = CIL_OK;
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool self = (qry == ref && n_qry == n_ref);
+  Workspace ws;
+  GridPlan gp;
+  grid_plan(gp, ws, n_ref, 1);
+  OrderPlan op;
+  size_t o_order = 0;
+  if (!self) {
+    order_plan(op, ws, n_qry);
+    o_order = ws.reserve(sizeof(int) * (size_t)n_qry);
+  }
+  if ((st = ws.allocate(ctx, s)) != CIL_OK) return st;
+  if ((st = grid_build(gp, ws, ref, nullptr, grid_options(nullptr, k), ctx, s)) != CIL_OK) return st;
+  const GridView g = grid_view(gp, ws);
+  int* order = nullptr;
+  if (!self) {
+    order = ws.at<int>(o_order);
+    if ((st = order_queries(op, ws, qry, nullptr, 1, g.prm, nullptr, order, s)) != CIL_OK) return st;
+  }
+  st = launch_knn_hybrid(g, qry, n_qry, order, k, r, out_idx, out_d2, s);
+  ws.release(s);
+  return st;
+}
+
+cil_status cil_estimate_normals_radius(const float* xyz, int64_t n, float r, const float* viewpoint,
+                                       float* out_normals, float* out_curvature,
+                                       int32_t* out_counts, void* stream) {
+  if (bad_count(n) || !viewpoint || !(r > 0.0f) || !isfinite(r)) return CIL_ERR_INVALID_ARG;
+  if (n == 0) return CIL_OK;
+  if (!xyz || !out_normals) return CIL_ERR_INVALID_ARG;
+  cil_status st = CIL_OK;
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace ws;
+  GridPlan gp;
+  grid_plan(gp, ws, n, 1);
+  if ((st = ws.allocate(ctx, s)) != CIL_OK) return st;
+  GridOptions opt;
+  opt.k_est = 10;
+  opt.cell_size = r;
+  if ((st = grid_build(gp, ws, xyz, nullptr, opt, ctx, s)) != CIL_OK) return st;
+  st = launch_normals_radius(grid_view(gp, ws), n, r, viewpoint, out_normals, out_curvature,
+                             out_counts, s);
+  ws.release(s);
+  return st;
+}
+
 cil_status cil_icp_point_to_plane(const float* src, int64_t n_src, const float* dst,
                                   const float* dst_normals, int64_t n_dst, const double* T_init,
                                   int max_iters, float max_corr_dist, double* T_out,

@@ -312,6 +312,40 @@ __device__ __forceinline__ void grid_knn(const GridView& g, int cloud, const flo
   if (visited_cells) *visited_cells = nvis;
 }
 
+// Exact k nearest neighbours of q among the points within squared distance r2
+// (inclusive): the search, the pruning and the stopping bound all use
+// min(current k-th distance, r2).
+template <int KMAX>
+__device__ __forceinline__ void grid_knn_within(const GridView& g, int cloud, const float q[3],
+                                                float r2, TopK<KMAX>& top) {
+  const GridParams& P = g.prm[cloud];
+  CellFrame f;
+  f.load(P, cloud);
+  const float inv_fine = P.inv_fine;
+  const int cx = f.cell_of(q[0], 0, inv_fine);
+  const int cy = f.cell_of(q[1], 1, inv_fine);
+  const int cz = f.cell_of(q[2], 2, inv_fine);
+  const int rmax = max(max(max(cx, f.hi[0] - cx), max(cy, f.hi[1] - cy)), max(cz, f.hi[2] - cz));
+  for (int r = 0; r <= rmax; ++r) {
+    CIL_SHELL_FOR(f, cx, cy, cz, r, x, y, z) {
+      const float lim = top.full() ? fminf(top.thr_d2(), r2) : r2;
+      const int c3[3] = {x, y, z};
+      if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > lim) continue;
+      int s, n;
+      if (!cell_lookup(g, cell_key(cloud, x, y, z), s, n)) continue;
+      for (int j = s; j < s + n; ++j) {
+        const float4 p = __ldg(g.pts + j);
+        const float d2 = sqdist(p.x, p.y, p.z, q[0], q[1], q[2]);
+        if (d2 <= r2) top.push(pack_key(d2, __float_as_int(p.w)));
+      }
+    }
+    const float lim = top.full() ? fminf(top.thr_d2(), r2) : r2;
+    const int e0[3] = {cx - r, cy - r, cz - r};
+    const int e1[3] = {cx + r, cy + r, cz + r};
+    if (lim < f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f)) break;
+  }
+}
+
 // Exact nearest neighbour of q within squared distance dmax2 (inclusive).
 // Returns the packed key, or kEmptyKey when no point lies within dmax2.
 __device__ __forceinline__ u64 grid_nn(const GridView& g, int cloud, const float q[3], float dmax2) {

@@ -13,6 +13,11 @@ cil_status launch_normals(const GridView& g, int clouds, int64_t n, int k, const
                           const float* vp_host, const float* xyz, float* out_n, float* out_c,
                           int block, cudaStream_t s);
 
+cil_status launch_knn_hybrid(const GridView& g, const float* qry, int64_t nq, const int* order,
+                             int k, float r, int* out_idx, float* out_d2, cudaStream_t s);
+cil_status launch_normals_radius(const GridView& g, int64_t n, float r, const float* vp_host,
+                                 float* out_n, float* out_c, int* out_cnt, cudaStream_t s);
+
 // ---------------------------------------------------------------------------
 // point-to-plane ICP over B pairs (B = 1 for a single registration)
 // ---------------------------------------------------------------------------

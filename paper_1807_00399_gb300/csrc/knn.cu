@@ -188,6 +188,26 @@ __device__ __forceinline__ bool sym3_smallest(const float C[6], float ev[3], flo
   return true;
 }
 
+// Normal, orientation and curvature from a covariance (shared by the k-NN and
+// the radius neighbourhoods).
+__device__ __forceinline__ void finish_normal(const float C[6], const float q[3], const float vp[3],
+                                              float out_n[3], float& out_c) {
+  const float nan = __int_as_float(0x7fc00000);
+  float ev[3], nv[3];
+  if (!sym3_smallest(C, ev, nv)) {
+    out_n[0] = out_n[1] = out_n[2] = nan;
+    out_c = nan;
+    return;
+  }
+  const float tr = ev[0] + ev[1] + ev[2];
+  const float s = nv[0] * (vp[0] - q[0]) + nv[1] * (vp[1] - q[1]) + nv[2] * (vp[2] - q[2]);
+  const float sg = s < 0.0f ? -1.0f : 1.0f;
+  out_n[0] = sg * nv[0];
+  out_n[1] = sg * nv[1];
+  out_n[2] = sg * nv[2];
+  out_c = tr > 0.0f ? fmaxf(ev[0], 0.0f) / tr : nan;
+}
+
 // PCA normal + curvature of one point from its neighbour keys.  `xyz` and the
 // key indices are relative to the same cloud.
 template <int KMAX>
@@ -234,19 +254,7 @@ __device__ __forceinline__ void normal_from_topk(const TopK<KMAX>& top, int k,
     }
   }
   const float C[6] = {cxx * im, cxy * im, cxz * im, cyy * im, cyz * im, czz * im};
-  float ev[3], nv[3];
-  if (!sym3_smallest(C, ev, nv)) {
-    out_n[0] = out_n[1] = out_n[2] = nan;
-    out_c = nan;
-    return;
-  }
-  const float tr = ev[0] + ev[1] + ev[2];
-  const float s = nv[0] * (vp[0] - q[0]) + nv[1] * (vp[1] - q[1]) + nv[2] * (vp[2] - q[2]);
-  const float sg = s < 0.0f ? -1.0f : 1.0f;
-  out_n[0] = sg * nv[0];
-  out_n[1] = sg * nv[1];
-  out_n[2] = sg * nv[2];
-  out_c = tr > 0.0f ? fmaxf(ev[0], 0.0f) / tr : nan;
+  finish_normal(C, q, vp, out_n, out_c);
 }
 
 template <int KMAX>
@@ -287,6 +295,128 @@ __global__ void __launch_bounds__(256) k_normals(GridView g, int cloud_count, in
 }
 
 // ---------------------------------------------------------------------------
+// hybrid query (k nearest within r) and radius-neighbourhood normals
+// (Sec. 3 hybrid queries and radius normals; Sec. 4 uses 1 cm balls)
+// ---------------------------------------------------------------------------
+template <int KMAX>
+__global__ void __launch_bounds__(256) k_knn_hybrid(GridView g, const float* __restrict__ qry,
+                                                    int64_t nq, const int* __restrict__ order, int k,
+                                                    float r2, int* __restrict__ out_idx,
+                                                    float* __restrict__ out_d2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq) return;
+  int64_t qi;
+  float q[3];
+  if (order) {
+    qi = order[i];
+    q[0] = qry[3 * qi];
+    q[1] = qry[3 * qi + 1];
+    q[2] = qry[3 * qi + 2];
+  } else {
+    const float4 p = g.pts[i];
+    qi = __float_as_int(p.w);
+    q[0] = p.x;
+    q[1] = p.y;
+    q[2] = p.z;
+  }
+  TopK<KMAX> top;
+  top.init(k);
+  grid_knn_within<KMAX>(g, 0, q, r2, top);
+  int* oi = out_idx + qi * k;
+  float* od = out_d2 ? out_d2 + qi * k : nullptr;
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    if (j < k) {
+      const u64 key = top.v[j];
+      const bool none = key == kEmptyKey;
+      oi[j] = none ? -1 : key_idx(key);
+      if (od) od[j] = none ? __int_as_float(0x7f800000) : key_d2(key);
+    }
+  }
+}
+
+// every point within r of each point (itself included): mean offset in a first
+// pass over the ball's cells, centred covariance in a second
+__global__ void __launch_bounds__(128) k_normals_radius(GridView g, int64_t n, float r, float vx,
+                                                        float vy, float vz,
+                                                        float* __restrict__ out_n,
+                                                        float* __restrict__ out_c,
+                                                        int* __restrict__ out_cnt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 pq = g.pts[i];
+  const int64_t qi = __float_as_int(pq.w);
+  const float q[3] = {pq.x, pq.y, pq.z};
+  const GridParams& P = g.prm[0];
+  CellFrame f;
+  f.load(P, 0);
+  const float r2 = r * r;
+  int lo[3], hi[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = f.cell_of(q[a] - r - f.eps, a, P.inv_fine);
+    hi[a] = f.cell_of(q[a] + r + f.eps, a, P.inv_fine);
+  }
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  int m = 0;
+  for (int z = lo[2]; z <= hi[2]; ++z)
+    for (int y = lo[1]; y <= hi[1]; ++y)
+      for (int x = lo[0]; x <= hi[0]; ++x) {
+        const int c3[3] = {x, y, z};
+        if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > r2) continue;
+        int s, cnt;
+        if (!cell_lookup(g, cell_key(0, x, y, z), s, cnt)) continue;
+        for (int j = s; j < s + cnt; ++j) {
+          const float4 p = __ldg(g.pts + j);
+          if (sqdist(p.x, p.y, p.z, q[0], q[1], q[2]) <= r2) {
+            sx += p.x - q[0];
+            sy += p.y - q[1];
+            sz += p.z - q[2];
+            ++m;
+          }
+        }
+      }
+  if (out_cnt) out_cnt[qi] = m;
+  const float nan = __int_as_float(0x7fc00000);
+  if (m < 3) {
+    out_n[3 * qi] = out_n[3 * qi + 1] = out_n[3 * qi + 2] = nan;
+    if (out_c) out_c[qi] = nan;
+    return;
+  }
+  const float im = 1.0f / (float)m;
+  const float mx = sx * im, my = sy * im, mz = sz * im;
+  float cxx = 0.f, cxy = 0.f, cxz = 0.f, cyy = 0.f, cyz = 0.f, czz = 0.f;
+  for (int z = lo[2]; z <= hi[2]; ++z)
+    for (int y = lo[1]; y <= hi[1]; ++y)
+      for (int x = lo[0]; x <= hi[0]; ++x) {
+        const int c3[3] = {x, y, z};
+        if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > r2) continue;
+        int s, cnt;
+        if (!cell_lookup(g, cell_key(0, x, y, z), s, cnt)) continue;
+        for (int j = s; j < s + cnt; ++j) {
+          const float4 p = __ldg(g.pts + j);
+          if (sqdist(p.x, p.y, p.z, q[0], q[1], q[2]) <= r2) {
+            const float ex = (p.x - q[0]) - mx, ey = (p.y - q[1]) - my, ez = (p.z - q[2]) - mz;
+            cxx = fmaf(ex, ex, cxx);
+            cxy = fmaf(ex, ey, cxy);
+            cxz = fmaf(ex, ez, cxz);
+            cyy = fmaf(ey, ey, cyy);
+            cyz = fmaf(ey, ez, cyz);
+            czz = fmaf(ez, ez, czz);
+          }
+        }
+      }
+  const float C[6] = {cxx * im, cxy * im, cxz * im, cyy * im, cyz * im, czz * im};
+  const float vp[3] = {vx, vy, vz};
+  float nv[3], c;
+  finish_normal(C, q, vp, nv, c);
+  out_n[3 * qi] = nv[0];
+  out_n[3 * qi + 1] = nv[1];
+  out_n[3 * qi + 2] = nv[2];
+  if (out_c) out_c[qi] = c;
+}
+
+// ---------------------------------------------------------------------------
 // host launchers: dispatch on the smallest compiled register capacity >= k
 // (CIL_FOR_K, cil_dev.cuh)
 // ---------------------------------------------------------------------------
@@ -313,6 +443,31 @@ cil_status launch_normals(const GridView& g, int clouds, int64_t n, int k, const
               vz = vp_host ? vp_host[2] : 0.0f;
   CIL_FOR_K(k, (k_normals<KM><<<grid, block, 0, s>>>(g, clouds, n, k, vp_dev, vx, vy, vz, xyz,
                                                      out_n, out_c)));
+  return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
+}
+
+}  // namespace cil
+
+namespace cil {
+
+cil_status launch_knn_hybrid(const GridView& g, const float* qry, int64_t nq, const int* order,
+                             int k, float r, int* out_idx, float* out_d2, cudaStream_t s) {
+  if (nq <= 0) return CIL_OK;
+  const int grid = ceil_div(nq, 128);
+  TimedRegion timer("k_knn_hybrid", s);
+  note_launches(1);
+  const float r2 = r * r;
+  CIL_FOR_K(k, (k_knn_hybrid<KM><<<grid, 128, 0, s>>>(g, qry, nq, order, k, r2, out_idx, out_d2)));
+  return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
+}
+
+cil_status launch_normals_radius(const GridView& g, int64_t n, float r, const float* vp_host,
+                                 float* out_n, float* out_c, int* out_cnt, cudaStream_t s) {
+  if (n <= 0) return CIL_OK;
+  TimedRegion timer("k_normals_radius", s);
+  note_launches(1);
+  k_normals_radius<<<ceil_div(n, 128), 128, 0, s>>>(g, n, r, vp_host[0], vp_host[1], vp_host[2],
+                                                    out_n, out_c, out_cnt);
   return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
 }
 

@@ -174,3 +174,12 @@ def test_radius_normals_equal_knn_normals_when_the_sets_coincide():
         assert cnt[i] == k
         np.testing.assert_allclose(nr[i], nk[i], atol=1e-12)
         assert abs(cr[i] - ck[i]) < 1e-15
+
+
+def test_radius_normals_subset_route_equals_full():
+    pts = synth.surface_pair(9, n=2000).target
+    sel = np.arange(0, 2000, 13)
+    n, c, ev, cnt = oracle.normals_radius(pts, 0.07, [0, 0, 10])
+    ns, cs, evs, cnts = oracle.normals_radius(pts, 0.07, [0, 0, 10], sel=sel)
+    np.testing.assert_array_equal(cnts, cnt[sel])
+    np.testing.assert_allclose(ns, n[sel], atol=0)
