@@ -73,9 +73,10 @@ def _load():
     lib.oracle_icp.argtypes = [P, I64, P, P, I64, P, I, D, P, P, P, P, P, P, I, I]
     lib.oracle_knn_hybrid.argtypes = [P, I64, P, I64, I, D, P, P, I]
     lib.oracle_normals_radius.argtypes = [P, I64, D, P, P, P, P, P, P, I64, I]
+    lib.oracle_voxel_downsample.argtypes = [P, I64, ctypes.c_float, P, P, P]
     for f in ("oracle_knn", "oracle_knn_kdtree", "oracle_radius", "oracle_sym3_eigen",
               "oracle_normals", "oracle_normals_subset", "oracle_icp", "oracle_knn_hybrid",
-              "oracle_normals_radius"):
+              "oracle_normals_radius", "oracle_voxel_downsample"):
         getattr(lib, f).restype = I
     _lib = lib
     return lib
@@ -169,6 +170,22 @@ def normals_radius(xyz, r: float, viewpoint, sel=None, threads: int = 0):
     if rc:
         raise RuntimeError("oracle normals_radius failed")
     return nrm, cur, ev, cnt
+
+
+def voxel_downsample(xyz, voxel: float):
+    """Mean of the points of every occupied voxel floor(p / voxel) (float32
+    division), ascending (ix, iy, iz): (points f64 (M,3), counts int64 (M,))."""
+    lib = _load()
+    xyz = _pts(xyz)
+    n = xyz.shape[0]
+    out = np.empty((max(n, 1), 3), np.float64)
+    cnt = np.empty(max(n, 1), np.int64)
+    m = ctypes.c_int64()
+    rc = lib.oracle_voxel_downsample(_p(xyz), n, float(np.float32(voxel)), _p(out), _p(cnt),
+                                     ctypes.byref(m))
+    if rc:
+        raise RuntimeError("oracle voxel_downsample failed")
+    return out[:m.value], cnt[:m.value]
 
 
 def sym3_eigen(C):

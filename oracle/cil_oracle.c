@@ -952,3 +952,52 @@ int oracle_normals_radius(const float *xyz, int64_t n, double r, const double *v
   parallel_for(sel ? n_sel : n, n_threads, nrr_range, &c);
   return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* voxel-grid downsampling (Sec. 3 GridAccumulator; Sec. 4 downsamples at     */
+/* 1 cm before ICP): point i falls in voxel floor(x / v) per axis (float      */
+/* division, as the float point type of the library computes it); every       */
+/* occupied voxel yields the mean of its points.  Output in ascending         */
+/* (ix, iy, iz) order.                                                         */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int64_t ix, iy, iz, idx;
+} vox_rec;
+
+static int cmp_vox(const void *a, const void *b) {
+  const vox_rec *x = (const vox_rec *)a, *y = (const vox_rec *)b;
+  if (x->ix != y->ix) return x->ix < y->ix ? -1 : 1;
+  if (x->iy != y->iy) return x->iy < y->iy ? -1 : 1;
+  if (x->iz != y->iz) return x->iz < y->iz ? -1 : 1;
+  return x->idx < y->idx ? -1 : (x->idx > y->idx);
+}
+
+int oracle_voxel_downsample(const float *xyz, int64_t n, float voxel, double *out_xyz,
+                            int64_t *out_counts, int64_t *out_n) {
+  if (n < 0 || !(voxel > 0)) return 1;
+  vox_rec *r = (vox_rec *)malloc(sizeof(vox_rec) * (size_t)(n > 0 ? n : 1));
+  if (!r) return 2;
+  for (int64_t i = 0; i < n; ++i) {
+    r[i].ix = (int64_t)floorf(xyz[3 * i] / voxel);
+    r[i].iy = (int64_t)floorf(xyz[3 * i + 1] / voxel);
+    r[i].iz = (int64_t)floorf(xyz[3 * i + 2] / voxel);
+    r[i].idx = i;
+  }
+  qsort(r, (size_t)n, sizeof(vox_rec), cmp_vox);
+  int64_t m = 0;
+  for (int64_t i = 0; i < n;) {
+    int64_t j = i;
+    double s[3] = {0, 0, 0};
+    while (j < n && r[j].ix == r[i].ix && r[j].iy == r[i].iy && r[j].iz == r[i].iz) {
+      for (int a = 0; a < 3; ++a) s[a] += (double)xyz[3 * r[j].idx + a];
+      ++j;
+    }
+    for (int a = 0; a < 3; ++a) out_xyz[3 * m + a] = s[a] / (double)(j - i);
+    out_counts[m] = j - i;
+    ++m;
+    i = j;
+  }
+  *out_n = m;
+  free(r);
+  return 0;
+}
