@@ -142,6 +142,19 @@ cil_status cil_estimate_normals_ex(const float *xyz, int64_t n, int k, const flo
                                    const cil_params *params, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Voxel-grid downsampling (Sec. 3 GridAccumulator; Sec. 4 downsamples to
+ * 1 cm voxels before ICP): point p falls in voxel floor(p / voxel) per axis
+ * (correctly rounded FP32 division, voxel indices clamped to +-2^20); each
+ * occupied voxel yields the mean of its points.
+ *   out_xyz     [n][3] float (device; capacity n: at most n voxels)
+ *   out_counts  [n] int32 (device, may be NULL): points per output voxel
+ *   out_n       host: number of output voxels
+ * Output voxels ascend by (ix, iy, iz).  Synchronises the stream.
+ */
+cil_status cil_voxel_downsample(const float *xyz, int64_t n, float voxel, float *out_xyz,
+                                int32_t *out_counts, int64_t *out_n, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Rigid point-to-plane ICP (Sec. 2 ICP base loop; Sec. 3 point-to-plane
  * estimator after Low 2004; Sec. 4 fixed iterations + rejection distance).
  * Each of `max_iters` rounds, at the current T:

@@ -85,6 +85,8 @@ def lib():
         L.cil_knn_hybrid.restype = I
         L.cil_estimate_normals_radius.argtypes = [P, I64, F, P, P, P, P, P]
         L.cil_estimate_normals_radius.restype = I
+        L.cil_voxel_downsample.argtypes = [P, I64, F, P, P, P, P]
+        L.cil_voxel_downsample.restype = I
         L.cil_pointnet_num_params.restype = I
         L.cil_pointnet_create.argtypes = [I, I, P]
         L.cil_pointnet_destroy.argtypes = [P]
@@ -204,6 +206,20 @@ def estimate_normals_radius(xyz, r: float, viewpoint, stream=None):
                                            _ptr(cnt), _stream(stream))
     _check(st, "cil_estimate_normals_radius")
     return nrm, cur, cnt
+
+
+def voxel_downsample(xyz, voxel: float, stream=None):
+    """Voxel-grid downsampling (cil_voxel_downsample): (means (M,3), counts (M,))."""
+    torch = _torch()
+    xyz = _points(xyz, "xyz")
+    n = xyz.shape[0]
+    out = torch.empty((max(n, 1), 3), dtype=torch.float32, device=xyz.device)
+    cnt = torch.empty(max(n, 1), dtype=torch.int32, device=xyz.device)
+    m = ctypes.c_int64(0)
+    st = lib().cil_voxel_downsample(_ptr(xyz), n, float(voxel), _ptr(out), _ptr(cnt),
+                                    ctypes.byref(m), _stream(stream))
+    _check(st, "cil_voxel_downsample")
+    return out[:m.value], cnt[:m.value]
 
 
 def radius_search(ref, qry, r: float, capacity: int | None = None, stream=None):

@@ -120,4 +120,15 @@ struct TimedRegion {
 };
 unsigned next_pow2_u32(uint64_t v);
 
+// stable LSD radix sort of (u64 key, int value) pairs on the low `bits` key
+// bits, in the buffers reserved by radix_sort_plan (keys0/vals0 hold the input);
+// returns which buffer pair (0 or 1) holds the result
+struct RadixPlan {
+  int64_t n = 0;
+  int blocks = 0;
+  size_t o_keys0, o_keys1, o_vals0, o_vals1, o_counts, o_scan;
+};
+void radix_sort_plan(RadixPlan& p, Workspace& ws, int64_t n);
+int radix_sort_pairs(const RadixPlan& p, const Workspace& ws, int bits, cudaStream_t s);
+
 }  // namespace cil

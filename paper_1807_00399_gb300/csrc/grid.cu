@@ -425,6 +425,24 @@ static int radix_sort(u64* k0, int* v0, u64* k1, int* v1, int64_t n, int passes,
   return cur;
 }
 
+void radix_sort_plan(RadixPlan& p, Workspace& ws, int64_t n) {
+  p.n = n;
+  p.blocks = ceil_div(n > 0 ? n : 1, kRsTile);
+  p.o_keys0 = ws.reserve(sizeof(u64) * (size_t)(n > 0 ? n : 1));
+  p.o_keys1 = ws.reserve(sizeof(u64) * (size_t)(n > 0 ? n : 1));
+  p.o_vals0 = ws.reserve(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  p.o_vals1 = ws.reserve(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  p.o_counts = ws.reserve(sizeof(int) * (size_t)kRadix * p.blocks);
+  p.o_scan = ws.reserve(sizeof(int) * scan_tmp_ints((int64_t)kRadix * p.blocks));
+}
+
+int radix_sort_pairs(const RadixPlan& p, const Workspace& ws, int bits, cudaStream_t s) {
+  if (p.n <= 0) return 0;
+  return radix_sort(ws.at<u64>(p.o_keys0), ws.at<int>(p.o_vals0), ws.at<u64>(p.o_keys1),
+                    ws.at<int>(p.o_vals1), p.n, (bits + kRadixBits - 1) / kRadixBits,
+                    ws.at<int>(p.o_counts), ws.at<int>(p.o_scan), p.blocks, s);
+}
+
 // ---------------------------------------------------------------------------
 // 4. sorted points
 // ---------------------------------------------------------------------------

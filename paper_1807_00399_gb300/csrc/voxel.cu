@@ -1,0 +1,112 @@
+// voxel.cu -- voxel-grid downsampling (Sec. 3 GridAccumulator; Sec. 4
+// downsamples to 1 cm voxels before ICP).
+//
+// Point i falls in voxel (floor(x/v), floor(y/v), floor(z/v)) with correctly
+// rounded FP32 division; the 63-bit key (21 bits per axis, offset by 2^20) is
+// stable-radix-sorted with the point index, voxel heads are marked and
+// scanned into output slots, and each voxel's mean is accumulated over its run
+// in index order with compensated FP32 sums (deterministic).  Output voxels
+// ascend by (ix, iy, iz).
+#include <math.h>
+
+#include "cil_host.h"
+#include "cil_kernels.h"
+
+namespace cil {
+
+constexpr int kVoxBias = 1 << 20;
+
+__global__ void k_voxel_keys(const float* __restrict__ xyz, int64_t n, float v,
+                             u64* __restrict__ keys, int* __restrict__ vals) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  u64 key = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float f = floorf(__fdiv_rn(xyz[3 * i + a], v));
+    f = fminf(fmaxf(f, -(float)kVoxBias), (float)(kVoxBias - 1));  // NaN -> lower bound
+    const u64 c = (u64)(long long)((int)f + kVoxBias);
+    key = (key << 21) | c;
+  }
+  keys[i] = key;
+  vals[i] = (int)i;
+}
+
+__global__ void k_voxel_heads(const u64* __restrict__ keys, int64_t n, int* __restrict__ head) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  if (i == n) {
+    head[n] = 0;
+    return;
+  }
+  head[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
+}
+
+// one thread per voxel run: compensated mean in sorted (= index) order
+__global__ void k_voxel_reduce(const u64* __restrict__ keys, const int* __restrict__ vals,
+                               const int* __restrict__ slot, int64_t n, const float* __restrict__ xyz,
+                               float* __restrict__ out_xyz, int* __restrict__ out_counts) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (i > 0 && keys[i] == keys[i - 1]) return;  // not a run head
+  KSum s[3];
+  s[0].zero();
+  s[1].zero();
+  s[2].zero();
+  int64_t j = i;
+  const u64 key = keys[i];
+  for (; j < n && keys[j] == key; ++j) {
+    const int64_t p = vals[j];
+    s[0].add(xyz[3 * p]);
+    s[1].add(xyz[3 * p + 1]);
+    s[2].add(xyz[3 * p + 2]);
+  }
+  const int m = (int)(j - i);
+  const int o = slot[i];
+  const double inv = 1.0 / (double)m;
+  for (int a = 0; a < 3; ++a) out_xyz[3 * (int64_t)o + a] = (float)(((double)s[a].s + (double)s[a].c) * inv);
+  if (out_counts) out_counts[o] = m;
+}
+
+}  // namespace cil
+
+using namespace cil;
+
+extern "C" cil_status cil_voxel_downsample(const float* xyz, int64_t n, float voxel, float* out_xyz,
+                                           int32_t* out_counts, int64_t* out_n, void* stream) {
+  if (n < 0 || n > 0x7fffffff || !(voxel > 0.0f) || !isfinite(voxel) || !out_n)
+    return CIL_ERR_INVALID_ARG;
+  *out_n = 0;
+  if (n == 0) return CIL_OK;
+  if (!xyz || !out_xyz) return CIL_ERR_INVALID_ARG;
+  cil_status st = CIL_OK;
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace ws;
+  RadixPlan rp;
+  radix_sort_plan(rp, ws, n);
+  const size_t o_head = ws.reserve(sizeof(int) * (size_t)(n + 1));
+  const size_t o_tmp = ws.reserve(sizeof(int) * scan_tmp_ints(n + 1));
+  if ((st = ws.allocate(ctx, s)) != CIL_OK) return st;
+  TimedRegion timer("voxel_downsample", s);
+  note_launches(3);
+  k_voxel_keys<<<ceil_div(n, 256), 256, 0, s>>>(xyz, n, voxel, ws.at<u64>(rp.o_keys0),
+                                                 ws.at<int>(rp.o_vals0));
+  const int which = radix_sort_pairs(rp, ws, 63, s);
+  const u64* keys = ws.at<u64>(which ? rp.o_keys1 : rp.o_keys0);
+  const int* vals = ws.at<int>(which ? rp.o_vals1 : rp.o_vals0);
+  int* head = ws.at<int>(o_head);
+  k_voxel_heads<<<ceil_div(n + 1, 256), 256, 0, s>>>(keys, n, head);
+  scan_exclusive(head, n + 1, ws.at<int>(o_tmp), s);
+  int m = 0;
+  if (cudaMemcpyAsync(&m, head + n, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return CIL_ERR_CUDA;
+  k_voxel_reduce<<<ceil_div(n, 256), 256, 0, s>>>(keys, vals, head, n, xyz, out_xyz, out_counts);
+  ws.release(s);
+  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    return CIL_ERR_CUDA;
+  *out_n = m;
+  return CIL_OK;
+}
