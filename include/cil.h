@@ -99,6 +99,43 @@ cil_status cil_knn_ex(const float *ref, int64_t n_ref, const float *qry, int64_t
                       int32_t *out_idx, float *out_d2, const cil_params *params, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * k nearest neighbours without any device allocation (the paper has no
+ * counterpart: it concerns how the library obtains memory, not what it
+ * computes).  For callers that cannot call cudaMalloc -- plugins inside a host
+ * framework whose allocator owns all device memory, real-time loops that
+ * forbid allocation after start-up, certified code without dynamic allocation
+ * -- this runs cil_knn's kernels on scratch held in a fixed 4 MiB array inside
+ * the library (every GPU that loads the library keeps it until exit).
+ * Arguments, layout and results are those of cil_knn, except:
+ *   - n_ref and n_qry must each be <= 32768, else CIL_ERR_CAPACITY (nothing is
+ *     launched);
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current: make it before any
+ *     stream capture;
+ *   - every call shares the one array: calls that overlap on the GPU race and
+ *     corrupt each other's results; each call resets the state it needs;
+ *   - the call synchronises `stream` and returns a device-detected error
+ *     (CIL_ERR_NONFINITE) directly.
+ */
+cil_status cil_knn_noalloc(const float *ref, int64_t n_ref, const float *qry, int64_t n_qry,
+                           int k, int32_t *out_idx, float *out_d2, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Radius search (Sec. 3, KDTree radius query): for every query all reference
+ * points with squared distance <= r*r (inclusive), as CSR:
+ *   out_offsets [n_qry+1] int64 (device): row q is [offsets[q], offsets[q+1])
+ *   out_idx     [capacity] int32 (device), out_d2 [capacity] float (device,
+ *               may be NULL); rows ascend by (d2, idx)
+ *   out_nnz     host int64: total number of neighbours found
+ * If the total exceeds `capacity`, nothing is written to out_idx/out_d2,
+ * out_offsets holds the full CSR offsets, *out_nnz the required size, and the
+ * call returns CIL_ERR_CAPACITY.  r >= 0.  Synchronises the stream.
+ */
+cil_status cil_radius_search(const float *ref, int64_t n_ref, const float *qry, int64_t n_qry,
+                             float r, int64_t *out_offsets, int32_t *out_idx, float *out_d2,
+                             int64_t capacity, int64_t *out_nnz, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Hybrid query (Sec. 3, KDTree "hybrid" queries): for every query the k
  * nearest reference points among those with squared distance <= r*r
  * (inclusive).  Same layout, order and padding (-1 / +inf) as cil_knn; rows

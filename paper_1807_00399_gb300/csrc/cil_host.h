@@ -43,6 +43,12 @@ class Workspace {
   }
   void release(cudaStream_t s);
   ~Workspace();
+  // bytes reserved so far
+  size_t total() const { return total_; }
+  // use caller-provided device memory instead of allocating; detach() must
+  // run before release() or destruction so that nothing tries to free it
+  void attach(void* base) { base_ = static_cast<char*>(base); }
+  void detach() { base_ = nullptr; }
 
  private:
   char* base_ = nullptr;
