@@ -104,7 +104,7 @@ cil_status cil_knn_ex(const float *ref, int64_t n_ref, const float *qry, int64_t
  * computes).  For callers that cannot call cudaMalloc -- plugins inside a host
  * framework whose allocator owns all device memory, real-time loops that
  * forbid allocation after start-up, certified code without dynamic allocation
- * -- this runs cil_knn's kernels on scratch held in a fixed 4 MiB array inside
+ * -- this runs cil_knn's kernels on scratch held in a fixed 8 MiB array inside
  * the library (every GPU that loads the library keeps it until exit).
  * Arguments, layout and results are those of cil_knn, except:
  *   - n_ref and n_qry must each be <= 32768, else CIL_ERR_CAPACITY (nothing is

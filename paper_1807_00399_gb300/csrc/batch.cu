@@ -45,7 +45,6 @@ static cil_status enqueue_batch(BatchHandle* h, const float* src, const float* d
   opt.k_est = h->prm.k;
   opt.cell_size = h->prm.tune.cell_size > 0.0f ? h->prm.tune.cell_size : 0.0f;
   opt.cell_scale = h->prm.tune.cell_scale > 0.0f ? h->prm.tune.cell_scale : 1.0f;
-  opt.icp_dmax = h->prm.max_corr_dist;
   cil_status st = grid_build(h->gp, h->ws, dst, dst_start, opt, h->ctx, s);
   if (st != CIL_OK) return st;
   const GridView g = grid_view(h->gp, h->ws);
@@ -95,7 +94,7 @@ cil_status cil_icp_batch_create(const int64_t* n_src, const int64_t* n_dst, int 
   h->n_dst.assign(n_dst, n_dst + B);
   h->tot_src = ts;
   h->tot_dst = td;
-  grid_plan(h->gp, h->ws, td, B, true);
+  grid_plan(h->gp, h->ws, td, B);
   icp_plan(h->ip, h->ws, n_src, B);
   h->o_src_start = h->ws.reserve(sizeof(int) * (B + 1));
   h->o_dst_start = h->ws.reserve(sizeof(int) * (B + 1));

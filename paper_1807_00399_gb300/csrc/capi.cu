@@ -335,14 +335,13 @@ cil_status cil_icp_point_to_plane(const float* src, int64_t n_src, const float* 
   cudaStream_t s = (cudaStream_t)stream;
   Workspace ws;
   GridPlan gp;
-  grid_plan(gp, ws, n_dst, 1, true);
+  grid_plan(gp, ws, n_dst, 1);
   IcpPlan ip;
   const int64_t counts[1] = {n_src};
   icp_plan(ip, ws, counts, 1);
   const size_t o_out = ws.reserve(sizeof(double) * 16 + sizeof(cil_icp_report));
   if ((st = ws.allocate(ctx, s)) != CIL_OK) return st;
   GridOptions gopt = grid_options(nullptr, 10);
-  gopt.icp_dmax = max_corr_dist;
   if ((st = grid_build(gp, ws, dst, nullptr, gopt, ctx, s)) != CIL_OK) return st;
   if ((st = icp_run(ip, ws, grid_view(gp, ws), src, nullptr, dst_normals, nullptr, T_init, max_iters,
                     nullptr, max_corr_dist, ctx, s)) != CIL_OK)
@@ -378,7 +377,7 @@ cil_status cil_register_pair(const float* src, int64_t n_src, const float* dst, 
   cudaStream_t s = (cudaStream_t)stream;
   Workspace ws;
   GridPlan gp;
-  grid_plan(gp, ws, n_dst, 1, true);
+  grid_plan(gp, ws, n_dst, 1);
   IcpPlan ip;
   const int64_t counts[1] = {n_src};
   icp_plan(ip, ws, counts, 1);
@@ -387,7 +386,6 @@ cil_status cil_register_pair(const float* src, int64_t n_src, const float* dst, 
   if ((st = ws.allocate(ctx, s)) != CIL_OK) return st;
   float* nrm = out_normals ? out_normals : ws.at<float>(o_nrm);
   GridOptions gopt = grid_options(params, k);
-  gopt.icp_dmax = max_corr_dist;
   if ((st = grid_build(gp, ws, dst, nullptr, gopt, ctx, s)) != CIL_OK) return st;
   const GridView g = grid_view(gp, ws);
   if ((st = launch_normals(g, 1, n_dst, k, nullptr, viewpoint, dst, nrm, nullptr, block_of(params),

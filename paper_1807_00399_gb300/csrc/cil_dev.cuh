@@ -108,10 +108,17 @@ __device__ __forceinline__ unsigned hash_key(u64 k) {
   return (unsigned)k;
 }
 
-__device__ __forceinline__ u64 cell_key(int cloud, int x, int y, int z) {
-  return ((u64)(unsigned)cloud << 30) | ((u64)(unsigned)z << 20) | ((u64)(unsigned)y << 10) |
-         (u64)(unsigned)x;
+// hash-table key of a cell: level (4 bits), cloud (11 bits), z, y, x (10 bits each)
+__device__ __forceinline__ u64 cell_key(int level, int cloud, int x, int y, int z) {
+  return ((u64)(unsigned)level << 41) | ((u64)(unsigned)cloud << 30) | ((u64)(unsigned)z << 20) |
+         ((u64)(unsigned)y << 10) | (u64)(unsigned)x;
 }
+
+// levels searched by k-NN queries: the cloud's level and up to three coarser
+// ones (x8 cell edge each), all hashed in the k-NN table
+constexpr int kEscalateStep = 3;
+constexpr int kRingCap = 3;  // rings searched at one level before escalating
+__device__ __forceinline__ int next_level(int lvl) { return min(lvl + kEscalateStep, kFineBits); }
 
 __device__ __forceinline__ bool table_lookup(const CellEntry* tab, unsigned mask, u64 K, int& start,
                                              int& count) {
@@ -276,73 +283,103 @@ struct TopK {
 };
 
 // Exact k nearest neighbours of q among the points of cloud `cloud`.
+// Rings of cells are searched at the cloud's level; a search that has not
+// proved its k-th distance after kRingCap rings (sparse regions, queries far
+// from the cloud) restarts at an 8x coarser level, up to the level whose one
+// cell spans the whole cloud, so every query visits at most a few hundred
+// cells per level.
 template <int KMAX>
 __device__ __forceinline__ void grid_knn(const GridView& g, int cloud, const float q[3], TopK<KMAX>& top,
-                         int* visited_cells = nullptr) {
+                                         int* visited_cells = nullptr) {
   const GridParams& P = g.prm[cloud];
-  CellFrame f;
-  f.load(P, cloud);
   const float inv_fine = P.inv_fine;
-  const int cx = f.cell_of(q[0], 0, inv_fine);
-  const int cy = f.cell_of(q[1], 1, inv_fine);
-  const int cz = f.cell_of(q[2], 2, inv_fine);
-  const int rmax = max(max(max(cx, f.hi[0] - cx), max(cy, f.hi[1] - cy)), max(cz, f.hi[2] - cz));
   int nvis = 0;
-  for (int r = 0; r <= rmax; ++r) {
-    CIL_SHELL_FOR(f, cx, cy, cz, r, x, y, z) {
+  for (int lvl = P.level;; lvl = next_level(lvl)) {
+    CellFrame f;
+    f.load_level(P, cloud, lvl, ldexpf(P.fine, lvl));
+    const int cx = f.cell_of(q[0], 0, inv_fine);
+    const int cy = f.cell_of(q[1], 1, inv_fine);
+    const int cz = f.cell_of(q[2], 2, inv_fine);
+    const int rmax = max(max(max(cx, f.hi[0] - cx), max(cy, f.hi[1] - cy)), max(cz, f.hi[2] - cz));
+    const int rcap = lvl >= kFineBits ? rmax : min(rmax, kRingCap);
+    top.init(top.k);
+    bool done = false;
+    for (int r = 0; r <= rcap; ++r) {
+      CIL_SHELL_FOR(f, cx, cy, cz, r, x, y, z) {
+        if (top.full()) {
+          const int c3[3] = {x, y, z};
+          if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > top.thr_d2()) continue;
+        }
+        int s, n;
+        if (!cell_lookup(g, cell_key(lvl, cloud, x, y, z), s, n)) continue;
+        ++nvis;
+        for (int j = s; j < s + n; ++j) {
+          const float4 p = __ldg(g.pts + j);
+          top.push(pack_key(sqdist(p.x, p.y, p.z, q[0], q[1], q[2]), __float_as_int(p.w)));
+        }
+      }
+      if (r == rmax) {
+        done = true;  // the explored cube holds the whole cloud
+        break;
+      }
       if (top.full()) {
-        const int c3[3] = {x, y, z};
-        if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > top.thr_d2()) continue;
-      }
-      int s, n;
-      if (!cell_lookup(g, cell_key(cloud, x, y, z), s, n)) continue;
-      ++nvis;
-      for (int j = s; j < s + n; ++j) {
-        const float4 p = __ldg(g.pts + j);
-        top.push(pack_key(sqdist(p.x, p.y, p.z, q[0], q[1], q[2]), __float_as_int(p.w)));
+        const int e0[3] = {cx - r, cy - r, cz - r};
+        const int e1[3] = {cx + r, cy + r, cz + r};
+        if (top.thr_d2() < f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f)) {
+          done = true;
+          break;
+        }
       }
     }
-    if (top.full()) {
-      const int e0[3] = {cx - r, cy - r, cz - r};
-      const int e1[3] = {cx + r, cy + r, cz + r};
-      const float b2 = f.unexplored_d2(q, e0, e1);
-      if (top.thr_d2() < b2 * (1.0f - 1e-6f)) break;
-    }
+    if (done || lvl >= kFineBits) break;
   }
   if (visited_cells) *visited_cells = nvis;
 }
 
 // Exact k nearest neighbours of q among the points within squared distance r2
 // (inclusive): the search, the pruning and the stopping bound all use
-// min(current k-th distance, r2).
+// min(current k-th distance, r2); levels escalate as in grid_knn.
 template <int KMAX>
 __device__ __forceinline__ void grid_knn_within(const GridView& g, int cloud, const float q[3],
                                                 float r2, TopK<KMAX>& top) {
   const GridParams& P = g.prm[cloud];
-  CellFrame f;
-  f.load(P, cloud);
   const float inv_fine = P.inv_fine;
-  const int cx = f.cell_of(q[0], 0, inv_fine);
-  const int cy = f.cell_of(q[1], 1, inv_fine);
-  const int cz = f.cell_of(q[2], 2, inv_fine);
-  const int rmax = max(max(max(cx, f.hi[0] - cx), max(cy, f.hi[1] - cy)), max(cz, f.hi[2] - cz));
-  for (int r = 0; r <= rmax; ++r) {
-    CIL_SHELL_FOR(f, cx, cy, cz, r, x, y, z) {
+  for (int lvl = P.level;; lvl = next_level(lvl)) {
+    CellFrame f;
+    f.load_level(P, cloud, lvl, ldexpf(P.fine, lvl));
+    const int cx = f.cell_of(q[0], 0, inv_fine);
+    const int cy = f.cell_of(q[1], 1, inv_fine);
+    const int cz = f.cell_of(q[2], 2, inv_fine);
+    const int rmax = max(max(max(cx, f.hi[0] - cx), max(cy, f.hi[1] - cy)), max(cz, f.hi[2] - cz));
+    const int rcap = lvl >= kFineBits ? rmax : min(rmax, kRingCap);
+    top.init(top.k);
+    bool done = false;
+    for (int r = 0; r <= rcap; ++r) {
+      CIL_SHELL_FOR(f, cx, cy, cz, r, x, y, z) {
+        const float lim = top.full() ? fminf(top.thr_d2(), r2) : r2;
+        const int c3[3] = {x, y, z};
+        if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > lim) continue;
+        int s, n;
+        if (!cell_lookup(g, cell_key(lvl, cloud, x, y, z), s, n)) continue;
+        for (int j = s; j < s + n; ++j) {
+          const float4 p = __ldg(g.pts + j);
+          const float d2 = sqdist(p.x, p.y, p.z, q[0], q[1], q[2]);
+          if (d2 <= r2) top.push(pack_key(d2, __float_as_int(p.w)));
+        }
+      }
+      if (r == rmax) {
+        done = true;
+        break;
+      }
       const float lim = top.full() ? fminf(top.thr_d2(), r2) : r2;
-      const int c3[3] = {x, y, z};
-      if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > lim) continue;
-      int s, n;
-      if (!cell_lookup(g, cell_key(cloud, x, y, z), s, n)) continue;
-      for (int j = s; j < s + n; ++j) {
-        const float4 p = __ldg(g.pts + j);
-        const float d2 = sqdist(p.x, p.y, p.z, q[0], q[1], q[2]);
-        if (d2 <= r2) top.push(pack_key(d2, __float_as_int(p.w)));
+      const int e0[3] = {cx - r, cy - r, cz - r};
+      const int e1[3] = {cx + r, cy + r, cz + r};
+      if (lim < f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f)) {
+        done = true;
+        break;
       }
     }
-    const float lim = top.full() ? fminf(top.thr_d2(), r2) : r2;
-    const int e0[3] = {cx - r, cy - r, cz - r};
-    const int e1[3] = {cx + r, cy + r, cz + r};
-    if (lim < f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f)) break;
+    if (done || lvl >= kFineBits) break;
   }
 }
 
@@ -370,7 +407,7 @@ __device__ __forceinline__ u64 grid_nn(const GridView& g, int cloud, const float
       const int c3[3] = {x, y, z};
       if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > lim) continue;
       int s, n;
-      if (!cell_lookup(g, cell_key(cloud, x, y, z), s, n)) continue;
+      if (!cell_lookup(g, cell_key(P.level, cloud, x, y, z), s, n)) continue;
       for (int j = s; j < s + n; ++j) {
         const float4 p = __ldg(g.pts + j);
         const float d2 = sqdist(p.x, p.y, p.z, q[0], q[1], q[2]);

@@ -48,7 +48,7 @@ struct IcpPlan {
 };
 
 constexpr int kIcpThreads = 256;
-constexpr int kIcpPPT = 4;
+constexpr int kIcpPPT = 2;
 constexpr int kIcpQ = 28;  // 21 (H upper) + 6 (g) + 1 (sum r^2)
 
 // Reserve workspace; `src_counts` host array of per-pair source sizes.

@@ -538,24 +538,31 @@ __global__ void __launch_bounds__(1024) k_choose_level(GridParams* prm, const fl
 // ---------------------------------------------------------------------------
 // 6. cell table
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int level_of(const GridParams& P, int which) {
-  return which ? P.level2 : P.level;
+// Levels hashed in a table: table 0 holds the cloud's level and its
+// escalation levels (+3, +6, +9, capped at 10, duplicates dropped); table 1
+// the correspondence level only.  slot < 0 when the table has no such slot.
+__device__ __forceinline__ int table_level(const GridParams& P, int which, int slot) {
+  if (which) return slot == 0 ? P.level2 : -1;
+  int lvl = P.level;
+  for (int j = 0; j < slot; ++j) {
+    const int nx = min(lvl + kEscalateStep, kFineBits);
+    if (nx == lvl) return -1;
+    lvl = nx;
+  }
+  return lvl;
 }
-
-__device__ __forceinline__ void cell_of_key(u64 key, const GridParams* prm, int which, int& c,
-                                            unsigned& prefix, int& x, int& y, int& z) {
-  c = (int)(key >> 30);
-  const unsigned m = (unsigned)(key & 0x3fffffffu);
-  const int L = level_of(prm[c], which);
-  prefix = m >> (3 * L);
-  x = (int)(compact3(m) >> L);
-  y = (int)(compact3(m >> 1) >> L);
-  z = (int)(compact3(m >> 2) >> L);
-}
+constexpr int kTableSlots = 4;
 
 __device__ __forceinline__ bool same_cell(u64 a, u64 b, int L) {
   return (a >> 30) == (b >> 30) && ((unsigned)(a & 0x3fffffffu) >> (3 * L)) ==
                                        ((unsigned)(b & 0x3fffffffu) >> (3 * L));
+}
+
+__device__ __forceinline__ u64 key_cell(u64 key, int L) {
+  const int c = (int)(key >> 30);
+  const unsigned m = (unsigned)(key & 0x3fffffffu);
+  return cell_key(L, c, (int)(compact3(m) >> L), (int)(compact3(m >> 1) >> L),
+                  (int)(compact3(m >> 2) >> L));
 }
 
 __global__ void k_cells_insert(const u64* __restrict__ keys, int64_t n, const GridParams* prm,
@@ -563,19 +570,21 @@ __global__ void k_cells_insert(const u64* __restrict__ keys, int64_t n, const Gr
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const u64 key = keys[i];
-  int c, x, y, z;
-  unsigned prefix;
-  cell_of_key(key, prm, which, c, prefix, x, y, z);
-  if (i > 0 && same_cell(keys[i - 1], key, level_of(prm[c], which))) return;
-  const u64 K = cell_key(c, x, y, z);
-  unsigned h = hash_key(K) & mask;
-  for (unsigned probe = 0; probe <= mask; ++probe) {
-    const u64 old = atomicCAS(&tab[h].key, kEmptyKey, K);
-    if (old == kEmptyKey || old == K) break;
-    h = (h + 1) & mask;
+  const GridParams& P = prm[(int)(key >> 30)];
+  for (int slot = 0; slot < kTableSlots; ++slot) {
+    const int L = table_level(P, which, slot);
+    if (L < 0) break;
+    if (i > 0 && same_cell(keys[i - 1], key, L)) continue;
+    const u64 K = key_cell(key, L);
+    unsigned h = hash_key(K) & mask;
+    for (unsigned probe = 0; probe <= mask; ++probe) {
+      const u64 old = atomicCAS(&tab[h].key, kEmptyKey, K);
+      if (old == kEmptyKey || old == K) break;
+      h = (h + 1) & mask;
+    }
+    tab[h].start = (int)i;
+    tab[h].count = 0;
   }
-  tab[h].start = (int)i;
-  tab[h].count = 0;
 }
 
 __global__ void k_cells_count(const u64* __restrict__ keys, int64_t n, const GridParams* prm,
@@ -583,18 +592,20 @@ __global__ void k_cells_count(const u64* __restrict__ keys, int64_t n, const Gri
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const u64 key = keys[i];
-  int c, x, y, z;
-  unsigned prefix;
-  cell_of_key(key, prm, which, c, prefix, x, y, z);
-  if (i + 1 < n && same_cell(keys[i + 1], key, level_of(prm[c], which))) return;
-  const u64 K = cell_key(c, x, y, z);
-  unsigned h = hash_key(K) & mask;
-  for (unsigned probe = 0; probe <= mask; ++probe) {
-    if (tab[h].key == K) {
-      tab[h].count = (int)i - tab[h].start + 1;
-      return;
+  const GridParams& P = prm[(int)(key >> 30)];
+  for (int slot = 0; slot < kTableSlots; ++slot) {
+    const int L = table_level(P, which, slot);
+    if (L < 0) break;
+    if (i + 1 < n && same_cell(keys[i + 1], key, L)) continue;
+    const u64 K = key_cell(key, L);
+    unsigned h = hash_key(K) & mask;
+    for (unsigned probe = 0; probe <= mask; ++probe) {
+      if (tab[h].key == K) {
+        tab[h].count = (int)i - tab[h].start + 1;
+        break;
+      }
+      h = (h + 1) & mask;
     }
-    h = (h + 1) & mask;
   }
 }
 
@@ -605,7 +616,11 @@ void grid_plan(GridPlan& p, Workspace& ws, int64_t n, int clouds, bool icp_table
   p.n = n;
   p.clouds = clouds;
   p.icp_table = icp_table;
-  const uint64_t slots = next_pow2_u32((uint64_t)(n > 0 ? 2 * n : 2));
+  // cells hashed in the k-NN table: at most min(points, cells of the level)
+  // for each of its <= 4 levels (spaced x8); whatever the cloud's level, that
+  // is <= n + n + 4096 + 8 per cloud.  Keep the load factor <= 1/2.
+  const uint64_t entries = 2 * (uint64_t)(n > 0 ? n : 1) + (uint64_t)clouds * (4096 + 8);
+  const uint64_t slots = next_pow2_u32(2 * entries);
   p.mask = (unsigned)(slots - 1);
   p.radix_blocks = ceil_div(n > 0 ? n : 1, kRsTile);
   p.o_prm = ws.reserve(sizeof(GridParams) * clouds);

@@ -56,46 +56,67 @@ struct IcpArgs {
   int* err;
 };
 
-// nearest target point within dmax2, also returning the point itself; uses
-// the correspondence level (cells >= d_max / 2) when its table was built
+// Nearest target point within dmax2, also returning the point itself.  The
+// search starts at the cloud's k-NN level with at most one ring around the
+// query's cell (a converged source point finds its neighbour there); a query
+// that is not resolved by then -- an outlier or a point still far from the
+// surface -- restarts at the 8x coarser levels, where the rejection distance
+// bounds the rings.  Exact either way: a level's result is taken only once
+// the unexplored region lies beyond min(best, dmax).
 __device__ __forceinline__ u64 nearest_within(const GridView& g, int cloud, const float q[3],
                                               float dmax2, float4& bp) {
   const GridParams& P = g.prm[cloud];
-  const bool lvl2 = g.tab2 != nullptr && P.level2 >= 0;
-  const CellEntry* tab = lvl2 ? g.tab2 : g.tab;
-  const unsigned mask = lvl2 ? g.mask2 : g.mask;
-  CellFrame f;
-  f.load_level(P, cloud, lvl2 ? P.level2 : P.level, lvl2 ? P.cell2 : P.cell);
-  const int cx = f.cell_of(q[0], 0, P.inv_fine);
-  const int cy = f.cell_of(q[1], 1, P.inv_fine);
-  const int cz = f.cell_of(q[2], 2, P.inv_fine);
-  const int rmax = max(max(max(cx, f.hi[0] - cx), max(cy, f.hi[1] - cy)), max(cz, f.hi[2] - cz));
+  const float inv_fine = P.inv_fine;
   u64 best = kEmptyKey;
-  float lim = dmax2;
-  for (int r = 0; r <= rmax; ++r) {
-    if (r > 0) {
-      const int e0[3] = {cx - r + 1, cy - r + 1, cz - r + 1};
-      const int e1[3] = {cx + r - 1, cy + r - 1, cz + r - 1};
-      if (f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim) break;
-    }
-    CIL_SHELL_FOR(f, cx, cy, cz, r, x, y, z) {
-      const int c3[3] = {x, y, z};
-      if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > lim) continue;
-      int s, n;
-      if (!table_lookup(tab, mask, cell_key(cloud, x, y, z), s, n)) continue;
-      for (int j = s; j < s + n; ++j) {
-        const float4 p = __ldg(g.pts + j);
-        const float d2 = sqdist(p.x, p.y, p.z, q[0], q[1], q[2]);
-        if (d2 <= dmax2) {
-          const u64 key = pack_key(d2, __float_as_int(p.w));
-          if (key < best) {
-            best = key;
-            bp = p;
-            lim = fminf(lim, d2);
+  for (int lvl = P.level;; lvl = next_level(lvl)) {
+    CellFrame f;
+    f.load_level(P, cloud, lvl, ldexpf(P.fine, lvl));
+    const int cx = f.cell_of(q[0], 0, inv_fine);
+    const int cy = f.cell_of(q[1], 1, inv_fine);
+    const int cz = f.cell_of(q[2], 2, inv_fine);
+    const int rmax = max(max(max(cx, f.hi[0] - cx), max(cy, f.hi[1] - cy)), max(cz, f.hi[2] - cz));
+    const int rcap = (lvl == P.level && lvl < kFineBits) ? min(rmax, 1) : rmax;
+    best = kEmptyKey;
+    float lim = dmax2;
+    bool done = false;
+    for (int r = 0; r <= rcap; ++r) {
+      if (r > 0) {
+        const int e0[3] = {cx - r + 1, cy - r + 1, cz - r + 1};
+        const int e1[3] = {cx + r - 1, cy + r - 1, cz + r - 1};
+        if (f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim) {
+          done = true;
+          break;
+        }
+      }
+      CIL_SHELL_FOR(f, cx, cy, cz, r, x, y, z) {
+        const int c3[3] = {x, y, z};
+        if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > lim) continue;
+        int s, n;
+        if (!cell_lookup(g, cell_key(lvl, cloud, x, y, z), s, n)) continue;
+        for (int j = s; j < s + n; ++j) {
+          const float4 p = __ldg(g.pts + j);
+          const float d2 = sqdist(p.x, p.y, p.z, q[0], q[1], q[2]);
+          if (d2 <= dmax2) {
+            const u64 key = pack_key(d2, __float_as_int(p.w));
+            if (key < best) {
+              best = key;
+              bp = p;
+              lim = fminf(lim, d2);
+            }
           }
         }
       }
+      if (r == rmax) {
+        done = true;
+        break;
+      }
     }
+    if (!done) {
+      const int e0[3] = {cx - rcap, cy - rcap, cz - rcap};
+      const int e1[3] = {cx + rcap, cy + rcap, cz + rcap};
+      done = f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim;
+    }
+    if (done || lvl >= kFineBits) break;
   }
   return best;
 }
@@ -299,9 +320,12 @@ __global__ void __launch_bounds__(kIcpThreads, 2) k_icp(IcpArgs a) {
 #pragma unroll
     for (int j = 0; j < 12; ++j) R[j] = s_Rt[j];
     const float dmax2 = s_dmax2;
-    KSum acc[kIcpQ];
+    // per-thread partials over its <= kIcpPPT points are plain FP32 (at most
+    // 3 roundings each); every combination across threads below is
+    // compensated (error-free TwoSum merges)
+    float part[kIcpQ];
 #pragma unroll
-    for (int q = 0; q < kIcpQ; ++q) acc[q].zero();
+    for (int q = 0; q < kIcpQ; ++q) part[q] = 0.0f;
     int cnt = 0;
     for (int pos = lo + tid; pos < hi; pos += kIcpThreads) {
       const int64_t si = __ldg(a.order + pos);
@@ -325,32 +349,37 @@ __global__ void __launch_bounds__(kIcpThreads, 2) k_icp(IcpArgs a) {
 #pragma unroll
       for (int u = 0; u < 6; ++u)
 #pragma unroll
-        for (int v = u; v < 6; ++v) acc[q++].add(__fmul_rn(J[u], J[v]));
+        for (int v = u; v < 6; ++v) {
+          part[q] = fmaf(J[u], J[v], part[q]);
+          ++q;
+        }
 #pragma unroll
-      for (int u = 0; u < 6; ++u) acc[21 + u].add(__fmul_rn(J[u], r));
-      acc[27].add(__fmul_rn(r, r));
+      for (int u = 0; u < 6; ++u) part[21 + u] = fmaf(J[u], r, part[21 + u]);
+      part[27] = fmaf(r, r, part[27]);
       ++cnt;
     }
-    // block reduction of the tile (fixed shuffle tree, then warps in order)
+    // block reduction of the tile (fixed shuffle tree, then warps in order),
+    // compensated: each merge is an error-free TwoSum of the partial sums;
+    // one quantity at a time keeps the live registers low
 #pragma unroll
     for (int q = 0; q < kIcpQ; ++q) {
+      KSum t;
+      t.s = part[q];
+      t.c = 0.0f;
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
-        const float s2 = __shfl_down_sync(0xffffffffu, acc[q].s, off);
-        const float c2 = __shfl_down_sync(0xffffffffu, acc[q].c, off);
-        acc[q].merge(s2, c2);
+        const float s2 = __shfl_down_sync(0xffffffffu, t.s, off);
+        const float c2 = __shfl_down_sync(0xffffffffu, t.c, off);
+        t.merge(s2, c2);
+      }
+      if (lane == 0) {
+        sm_s[warp][q] = t.s;
+        sm_c[warp][q] = t.c;
       }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, off);
-    if (lane == 0) {
-#pragma unroll
-      for (int q = 0; q < kIcpQ; ++q) {
-        sm_s[warp][q] = acc[q].s;
-        sm_c[warp][q] = acc[q].c;
-      }
-      sm_n[warp] = cnt;
-    }
+    if (lane == 0) sm_n[warp] = cnt;
     __syncthreads();
     if (tid < kIcpQ) {
       KSum t;

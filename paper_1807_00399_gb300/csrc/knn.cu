@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(128) k_normals_radius(GridView g, int64_t n, f
         const int c3[3] = {x, y, z};
         if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > r2) continue;
         int s, cnt;
-        if (!cell_lookup(g, cell_key(0, x, y, z), s, cnt)) continue;
+        if (!cell_lookup(g, cell_key(P.level, 0, x, y, z), s, cnt)) continue;
         for (int j = s; j < s + cnt; ++j) {
           const float4 p = __ldg(g.pts + j);
           if (sqdist(p.x, p.y, p.z, q[0], q[1], q[2]) <= r2) {
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(128) k_normals_radius(GridView g, int64_t n, f
         const int c3[3] = {x, y, z};
         if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > r2) continue;
         int s, cnt;
-        if (!cell_lookup(g, cell_key(0, x, y, z), s, cnt)) continue;
+        if (!cell_lookup(g, cell_key(P.level, 0, x, y, z), s, cnt)) continue;
         for (int j = s; j < s + cnt; ++j) {
           const float4 p = __ldg(g.pts + j);
           if (sqdist(p.x, p.y, p.z, q[0], q[1], q[2]) <= r2) {

@@ -25,7 +25,7 @@
 namespace cil {
 
 constexpr int64_t kNoAllocMaxPoints = 32768;          // per reference and per query set
-constexpr size_t kNoAllocScratchBytes = 4u << 20;     // 4 MiB
+constexpr size_t kNoAllocScratchBytes = 8u << 20;     // 8 MiB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 static __device__ int g_noalloc_err;

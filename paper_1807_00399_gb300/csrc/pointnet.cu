@@ -24,6 +24,7 @@
 
 #include "cil_host.h"
 #include "cil_kernels.h"
+#include "tc05.cuh"
 
 namespace cil {
 
@@ -267,6 +268,199 @@ __global__ void __launch_bounds__(kEncThreads, 1) k_pn_encode(const float* __res
       }
       __syncthreads();
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// encoder forward on the 5th-generation tensor cores (tcgen05 + TMEM)
+// ---------------------------------------------------------------------------
+// 128 threads; thread r owns point row r of a 128-point tile.  Operands live in
+// shared memory as K-major BF16 tiles with the 128-byte swizzle (64-element
+// rows); the two GEMMs accumulate in tensor memory (columns 0..127: layer 2,
+// 128..383: layer 3), issued by one thread and completed through an mbarrier.
+constexpr int kTcThreads = 128;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kMbarPolls = 1u << 26;  // bounded wait (~seconds)
+
+struct EncTcSmem {
+  uint8_t a1[kTileP * 128];      // [128 rows][64 k]
+  uint8_t w2[kH2 * 128];         // [128 n][64 k]
+  uint8_t a2[2][kTileP * 128];   // two 64-wide k blocks of [128 rows][64 k]
+  uint8_t w3[2][kH3 * 128];      // two 64-wide k blocks of [256 n][64 k]
+  float w1[kH1 * kIn];
+  float b1[kH1];
+  float b2[kH2];
+  float b3[kH3];
+  float red[4][32][33];          // per-warp transpose for the column max
+  u64 wmax[4][kH3];              // per-warp column maxima of one tile
+  uint64_t bar;
+  uint32_t tmem_base;
+  int abort;
+};
+
+static size_t enc_tc_smem() { return sizeof(EncTcSmem) + 1024; }
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_pn_encode_tc(
+    const float* __restrict__ X, int clouds, int P, const float* __restrict__ prm,
+    const __nv_bfloat16* __restrict__ w2b, const __nv_bfloat16* __restrict__ w3b,
+    u64* __restrict__ feat_key, int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // operand tiles need 1024-byte alignment (swizzle atom)
+  const uint32_t raw_s = tc::smem_u32(smem_raw);
+  EncTcSmem& S = *reinterpret_cast<EncTcSmem*>(smem_raw + (((raw_s + 1023u) & ~1023u) - raw_s));
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (warp == 0) {
+    tc::tmem_alloc(&S.tmem_base, kTmemCols);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&S.bar, 1);
+    tc::fence_mbar_init();
+    S.abort = 0;
+  }
+  // resident weights, swizzled: 16-byte chunks of 8 bf16
+  for (int e = tid; e < kH2 * 8; e += kTcThreads) {
+    const int n = e >> 3, c = e & 7;
+    *reinterpret_cast<uint4*>(S.w2 + tc::sw128_offset(n, 8 * c)) =
+        *reinterpret_cast<const uint4*>(w2b + n * kH1 + 8 * c);
+  }
+  for (int e = tid; e < kH3 * 16; e += kTcThreads) {
+    const int n = e >> 4, c = e & 15;
+    *reinterpret_cast<uint4*>(S.w3[c >> 3] + tc::sw128_offset(n, 8 * (c & 7))) =
+        *reinterpret_cast<const uint4*>(w3b + n * kH2 + 8 * c);
+  }
+  for (int e = tid; e < kH1 * kIn; e += kTcThreads) S.w1[e] = prm[oW1 + e];
+  for (int e = tid; e < kH1; e += kTcThreads) S.b1[e] = prm[oB1 + e];
+  for (int e = tid; e < kH2; e += kTcThreads) S.b2[e] = prm[oB2 + e];
+  for (int e = tid; e < kH3; e += kTcThreads) S.b3[e] = prm[oB3 + e];
+  tc::fence_async_smem();
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = S.tmem_base;
+  const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+  const uint32_t id2 = tc::idesc_bf16_f32(128, kH2);
+  const uint32_t id3 = tc::idesc_bf16_f32(128, kH3);
+  uint32_t phase = 0;
+
+  const int tiles_per_cloud = P / kTileP;
+  const int total = clouds * tiles_per_cloud;
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    const int cloud = t / tiles_per_cloud;
+    const int row0 = (t % tiles_per_cloud) * kTileP;
+    // ---- layer 1 (FP32 ALU): row tid, 64 channels -> bf16 A1 ----
+    {
+      const float* xp = X + ((int64_t)cloud * P + row0 + tid) * 3;
+      const float x = xp[0], y = xp[1], z = xp[2];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        unsigned w[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const int ch = 8 * c + 2 * h;
+          const float* wr = S.w1 + ch * 3;
+          const float z0 = fmaf(wr[0], x, fmaf(wr[1], y, fmaf(wr[2], z, S.b1[ch])));
+          const float z1 = fmaf(wr[3], x, fmaf(wr[4], y, fmaf(wr[5], z, S.b1[ch + 1])));
+          w[h] = pack_bf16x2(fmaxf(z0, 0.0f), fmaxf(z1, 0.0f));
+        }
+        *reinterpret_cast<uint4*>(S.a1 + tc::sw128_offset(tid, 8 * c)) =
+            make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+    tc::fence_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    // ---- layer 2: D[0:128) = A1 [128x64] * W2^T ----
+    if (tid == 0) {
+      tc::tc_fence_after();
+      const uint32_t a = tc::smem_u32(S.a1), b = tc::smem_u32(S.w2);
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks)
+        tc::mma_bf16(tmem, tc::smem_desc_sw128(a + 32 * ks), tc::smem_desc_sw128(b + 32 * ks), id2,
+                     ks > 0);
+      tc::mma_commit(&S.bar);
+    }
+    bool ok = tc::mbar_wait(&S.bar, phase, kMbarPolls);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicCAS(err, 0, (int)CIL_ERR_TIMEOUT);
+      break;
+    }
+    tc::tc_fence_after();
+    // ---- epilogue 2: bias + relu -> bf16 A2 (two 64-wide k blocks) ----
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j) {
+      float v[32];
+      tc::tmem_ld32(tmem + lane_base + 32 * j, v);
+      uint8_t* blk = S.a2[j >> 1];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        unsigned w[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const int col = 32 * j + 8 * c + 2 * h;
+          w[h] = pack_bf16x2(fmaxf(v[8 * c + 2 * h] + S.b2[col], 0.0f),
+                             fmaxf(v[8 * c + 2 * h + 1] + S.b2[col + 1], 0.0f));
+        }
+        *reinterpret_cast<uint4*>(blk + tc::sw128_offset(tid, (32 * j + 8 * c) & 63)) =
+            make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+    tc::fence_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    // ---- layer 3: D[128:384) = A2 [128x128] * W3^T ----
+    if (tid == 0) {
+      tc::tc_fence_after();
+#pragma unroll
+      for (int ks = 0; ks < 8; ++ks) {
+        const uint32_t a = tc::smem_u32(S.a2[ks >> 2]) + 32 * (ks & 3);
+        const uint32_t b = tc::smem_u32(S.w3[ks >> 2]) + 32 * (ks & 3);
+        tc::mma_bf16(tmem + kH2, tc::smem_desc_sw128(a), tc::smem_desc_sw128(b), id3, ks > 0);
+      }
+      tc::mma_commit(&S.bar);
+    }
+    ok = tc::mbar_wait(&S.bar, phase, kMbarPolls);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicCAS(err, 0, (int)CIL_ERR_TIMEOUT);
+      break;
+    }
+    tc::tc_fence_after();
+    // ---- epilogue 3: bias + relu, column (value, row) max of the tile ----
+#pragma unroll 1
+    for (int j = 0; j < 8; ++j) {
+      float v[32];
+      tc::tmem_ld32(tmem + lane_base + kH2 + 32 * j, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) S.red[warp][lane][i] = fmaxf(v[i] + S.b3[32 * j + i], 0.0f);
+      __syncwarp();
+      float best = S.red[warp][0][lane];
+      int br = 0;
+      for (int rr = 1; rr < 32; ++rr) {
+        const float x = S.red[warp][rr][lane];
+        if (x > best) {  // strict: ties keep the smaller row
+          best = x;
+          br = rr;
+        }
+      }
+      S.wmax[warp][32 * j + lane] = feat_pack(best, row0 + 32 * warp + br);
+      __syncwarp();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    for (int c = tid; c < kH3; c += kTcThreads) {
+      u64 m = S.wmax[0][c];
+#pragma unroll
+      for (int w = 1; w < 4; ++w) m = max(m, S.wmax[w][c]);
+      atomicMax(feat_key + (int64_t)cloud * kH3 + c, m);
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, kTmemCols);
   }
 }
 
@@ -632,8 +826,8 @@ static cil_status pn_forward_enqueue(cil_pointnet* h, const float* clouds, int B
   {
     TimedRegion timer("k_pn_encode", s);
     note_launches(2);
-    k_pn_encode<<<grid, kEncThreads, enc_smem(), s>>>(clouds, 2 * B, S.P, S.params, S.w2b, S.w3b,
-                                                       S.feat_key);
+    k_pn_encode_tc<<<grid, kTcThreads, enc_tc_smem(), s>>>(clouds, 2 * B, S.P, S.params, S.w2b,
+                                                           S.w3b, S.feat_key, h->ctx->err);
     k_pn_head<<<B, 256, 0, s>>>(S.params, S.w4t, S.feat_key, B, S.h, S.z4, S.o, T_out);
   }
   return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
@@ -650,6 +844,8 @@ cil_status cil_pointnet_create(int max_pairs, int n_points, cil_pointnet** out) 
   if (!ctx) return st;
   if (cudaFuncSetAttribute(k_pn_encode, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)enc_smem()) != cudaSuccess ||
+      cudaFuncSetAttribute(k_pn_encode_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)enc_tc_smem()) != cudaSuccess ||
       cudaFuncSetAttribute(k_pn_encode_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)enc_bwd_smem()) != cudaSuccess)
     return CIL_ERR_CUDA;
