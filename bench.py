@@ -31,6 +31,7 @@ no data-path collective; value = all ranks' queries / max rank time.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -410,8 +411,9 @@ def run_batched(args, rank: int, B: int = 256, runs: int = 5):
     src, dst, T_gt = synth.surface_batch_torch(1000 + args.seed + rank, sizes)
     h = cil.Batch(sizes, sizes, k=K_NN, iters=ICP_ITERS, max_corr_dist=0.1,
                   viewpoint=(0.0, 0.0, 10.0))
+    RS = ctypes.sizeof(cil.IcpReport)
     T = torch.empty((B, 16), dtype=torch.float64, device="cuda")
-    rep = torch.empty((B, 32), dtype=torch.uint8, device="cuda")
+    rep = torch.empty((B, RS), dtype=torch.uint8, device="cuda")
     h.run(src, dst, T_out=T, rep=rep)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -426,7 +428,7 @@ def run_batched(args, rank: int, B: int = 256, runs: int = 5):
     # sequential plain calls
     off = np.concatenate([[0], np.cumsum(sizes)])
     Ts = torch.empty((B, 16), dtype=torch.float64, device="cuda")
-    reps_s = torch.empty((B, 32), dtype=torch.uint8, device="cuda")
+    reps_s = torch.empty((B, RS), dtype=torch.uint8, device="cuda")
     nrm = torch.empty_like(dst)
 
     def seq():
@@ -447,6 +449,7 @@ def run_batched(args, rank: int, B: int = 256, runs: int = 5):
     rb = np.array([r["rmse"] for r in reps_b])
     rq = np.array([r["rmse"] for r in rs])
     h.close()
+    same_T = bool(torch.equal(T, Ts))
     Tb = T.cpu().numpy().reshape(B, 4, 4)
     Rg = T_gt.cpu().numpy()
     M = Tb[:, :3, :3] @ np.transpose(Rg[:, :3, :3], (0, 2, 1))
@@ -456,6 +459,7 @@ def run_batched(args, rank: int, B: int = 256, runs: int = 5):
             "ms_sequential_plain": ms_s, "pairs_per_s_plain": B / (ms_s / 1e3),
             "speedup": ms_s / ms_b,
             "max_abs_rmse_diff": float(np.nanmax(np.abs(rb - rq))),
+            "T_bitwise_equal_batched_vs_plain": same_T,
             "median_rmse": float(np.nanmedian(rb)),
             "success_rate_rmse_lt_0.005": float(np.mean(np.nan_to_num(rb, nan=1.0) < 0.005)),
             "median_rot_err_deg_vs_generator": float(np.median(rot_err))}

@@ -98,14 +98,17 @@ __device__ __forceinline__ int fine_coord(float v, float o, float inv_fine) {
   return (int)f;
 }
 
-// 64-bit mixer (MurmurHash3 finaliser)
+// Cell-key hash on 32-bit arithmetic: fold the key's high word into the low
+// one with a Fibonacci multiplier, then the "lowbias32" integer mixer
+// (xorshift-multiply rounds, C. Wellons' hash-prospector).
 __device__ __forceinline__ unsigned hash_key(u64 k) {
-  k ^= k >> 33;
-  k *= 0xff51afd7ed558ccdull;
-  k ^= k >> 33;
-  k *= 0xc4ceb9fe1a85ec53ull;
-  k ^= k >> 33;
-  return (unsigned)k;
+  unsigned h = (unsigned)k ^ ((unsigned)(k >> 32) * 0x9E3779B1u);
+  h ^= h >> 16;
+  h *= 0x7FEB352Du;
+  h ^= h >> 15;
+  h *= 0x846CA68Bu;
+  h ^= h >> 16;
+  return h;
 }
 
 // hash-table key of a cell: level (4 bits), cloud (11 bits), z, y, x (10 bits each)

@@ -32,7 +32,9 @@ struct IcpPairState {
   float Rt[12];     // T as float rows [R | t] for the association passes
   float dmax2;      // squared rejection distance
   int tile_begin, tile_end;
-  int tiles_done;   // tiles of the current round finished
+  int grp_begin;    // first tile group of the pair (groups of kIcpGroup tiles)
+  int n_grp;        // tile groups of the pair
+  int tiles_done;   // tile groups of the current round reduced
   int iter_done;    // rounds published (the next round may start)
   int status;       // CIL_OK or CIL_ERR_DEGENERATE
   int iters;        // rounds requested
@@ -43,13 +45,16 @@ struct IcpPlan {
   int64_t n_src = 0;
   int n_tiles = 0;
   int tile = 0;     // source points per tile
+  int n_groups = 0;  // tile groups over all pairs
   size_t o_state, o_order, o_tile_off, o_rt, o_part_s, o_part_c, o_part_n, o_work;
+  size_t o_grp_s, o_grp_c, o_grp_n, o_grp_done;
   OrderPlan order;
 };
 
 constexpr int kIcpThreads = 256;
 constexpr int kIcpPPT = 2;
 constexpr int kIcpQ = 28;  // 21 (H upper) + 6 (g) + 1 (sum r^2)
+constexpr int kIcpGroup = 32;  // tiles reduced together before the round's solve
 
 // Reserve workspace; `src_counts` host array of per-pair source sizes.
 void icp_plan(IcpPlan& p, Workspace& ws, const int64_t* src_counts, int pairs);

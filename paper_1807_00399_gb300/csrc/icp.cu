@@ -8,11 +8,13 @@
 //   p' = R p + t  (FP32),  q = exact nearest target point of p' within the
 //   rejection distance, n = normal of q, r = n.(p' - q), J = [p' x n, n],
 // and accumulates H = sum J J^T (21 terms), g = sum J r (6), sum r^2 with
-// compensated FP32 sums; the block writes the tile's partial sums.  The block
-// that completes the last tile of a pair's round reduces that pair's tile
-// partials in tile order (deterministic), solves H xi = -g in FP64 by
-// Cholesky, left-composes T <- [exp(w^), tau; 0 1] T in FP64 and publishes the
-// round.  The extra last round only evaluates the final RMSE.
+// compensated FP32 sums; the block writes the tile's partial sums.  Tiles
+// form groups of kIcpGroup: the block that completes a group's last tile
+// reduces the group in a fixed order, and the block that completes a pair's
+// last group reduces the group partials in order (deterministic), solves
+// H xi = -g in FP64 by Cholesky, left-composes T <- [exp(w^), tau; 0 1] T in
+// FP64 and publishes the round.  The extra last round only evaluates the
+// final RMSE.
 // A round only depends on earlier tiles, which running blocks hold, so the
 // schedule cannot deadlock; every wait still has an iteration limit and
 // reports CIL_ERR_TIMEOUT instead of hanging.
@@ -51,87 +53,124 @@ struct IcpArgs {
   float* part_s;
   float* part_c;
   int* part_n;
+  float* grp_s;
+  float* grp_c;
+  int* grp_n;
+  int* grp_done;
   unsigned* work;
   int* abort;
   int* err;
 };
 
-// Nearest target point within dmax2, also returning the point itself.  The
-// search starts at the cloud's k-NN level with at most one ring around the
-// query's cell (a converged source point finds its neighbour there); a query
-// that is not resolved by then -- an outlier or a point still far from the
-// surface -- restarts at the 8x coarser levels, where the rejection distance
-// bounds the rings.  Exact either way: a level's result is taken only once
-// the unexplored region lies beyond min(best, dmax).
+// Points of one cell that improve on (best, lim); lim = min(dmax2, best d^2).
+__device__ __forceinline__ void scan_cell(const GridView& g, int s, int n, const float q[3],
+                                          float dmax2, u64& best, int& bj, float& lim) {
+  for (int j = s; j < s + n; ++j) {
+    const float4 p = __ldg(g.pts + j);
+    const float d2 = sqdist(p.x, p.y, p.z, q[0], q[1], q[2]);
+    const u64 key = pack_key(d2, __float_as_int(p.w));
+    if (d2 <= dmax2 && key < best) {
+      best = key;
+      bj = j;
+      lim = fminf(lim, d2);
+    }
+  }
+}
+
+// Nearest target point within dmax2 (sorted position in bj, key returned, or
+// kEmptyKey).  At the cloud's own level the query's cell is scanned first;
+// then only the cells of its 3x3x3 block that meet the ball of the best
+// distance so far (a converged source point finds its neighbour there).  A
+// query whose ball leaves the block -- an outlier or a point still far from
+// the surface -- continues with a ring search at the 8x coarser levels, where
+// the rejection distance bounds the rings.  Exact: a level's search ends only
+// once the unexplored region lies beyond min(best, dmax).
 __device__ __forceinline__ u64 nearest_within(const GridView& g, int cloud, const float q[3],
-                                              float dmax2, float4& bp) {
+                                              float dmax2, int& bj) {
   const GridParams& P = g.prm[cloud];
   const float inv_fine = P.inv_fine;
   u64 best = kEmptyKey;
-  for (int lvl = P.level;; lvl = next_level(lvl)) {
+  float lim = dmax2;
+  bj = -1;
+  {
+    CellFrame f;
+    f.load(P, cloud);
+    const int c[3] = {f.cell_of(q[0], 0, inv_fine), f.cell_of(q[1], 1, inv_fine),
+                      f.cell_of(q[2], 2, inv_fine)};
+    int s, n;
+    if (cell_lookup(g, cell_key(f.level, cloud, c[0], c[1], c[2]), s, n))
+      scan_cell(g, s, n, q, dmax2, best, bj, lim);
+    if (f.level >= kFineBits) return best;  // one cell holds the whole cloud
+    // cells of the block meeting the ball of radius sqrt(lim) (padded)
+    const float rad = fmaf(sqrtf(lim), 1.0f + 1e-6f, f.eps);
+    int lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = max(f.cell_of(q[a] - rad, a, inv_fine), c[a] - 1);
+      hi[a] = min(f.cell_of(q[a] + rad, a, inv_fine), c[a] + 1);
+    }
+    for (int z = lo[2]; z <= hi[2]; ++z)
+      for (int y = lo[1]; y <= hi[1]; ++y)
+        for (int x = lo[0]; x <= hi[0]; ++x) {
+          if (x == c[0] && y == c[1] && z == c[2]) continue;
+          const int c3[3] = {x, y, z};
+          if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > lim) continue;
+          if (cell_lookup(g, cell_key(f.level, cloud, x, y, z), s, n))
+            scan_cell(g, s, n, q, dmax2, best, bj, lim);
+        }
+    const int e0[3] = {c[0] - 1, c[1] - 1, c[2] - 1};
+    const int e1[3] = {c[0] + 1, c[1] + 1, c[2] + 1};
+    if (f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim) return best;
+  }
+  for (int lvl = next_level(P.level);; lvl = next_level(lvl)) {
     CellFrame f;
     f.load_level(P, cloud, lvl, ldexpf(P.fine, lvl));
     const int cx = f.cell_of(q[0], 0, inv_fine);
     const int cy = f.cell_of(q[1], 1, inv_fine);
     const int cz = f.cell_of(q[2], 2, inv_fine);
     const int rmax = max(max(max(cx, f.hi[0] - cx), max(cy, f.hi[1] - cy)), max(cz, f.hi[2] - cz));
-    const int rcap = (lvl == P.level && lvl < kFineBits) ? min(rmax, 1) : rmax;
-    best = kEmptyKey;
-    float lim = dmax2;
-    bool done = false;
+    const int rcap = lvl >= kFineBits ? rmax : min(rmax, kRingCap);
     for (int r = 0; r <= rcap; ++r) {
       if (r > 0) {
         const int e0[3] = {cx - r + 1, cy - r + 1, cz - r + 1};
         const int e1[3] = {cx + r - 1, cy + r - 1, cz + r - 1};
-        if (f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim) {
-          done = true;
-          break;
-        }
+        if (f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim) return best;
       }
       CIL_SHELL_FOR(f, cx, cy, cz, r, x, y, z) {
         const int c3[3] = {x, y, z};
         if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > lim) continue;
         int s, n;
-        if (!cell_lookup(g, cell_key(lvl, cloud, x, y, z), s, n)) continue;
-        for (int j = s; j < s + n; ++j) {
-          const float4 p = __ldg(g.pts + j);
-          const float d2 = sqdist(p.x, p.y, p.z, q[0], q[1], q[2]);
-          if (d2 <= dmax2) {
-            const u64 key = pack_key(d2, __float_as_int(p.w));
-            if (key < best) {
-              best = key;
-              bp = p;
-              lim = fminf(lim, d2);
-            }
-          }
-        }
-      }
-      if (r == rmax) {
-        done = true;
-        break;
+        if (cell_lookup(g, cell_key(lvl, cloud, x, y, z), s, n))
+          scan_cell(g, s, n, q, dmax2, best, bj, lim);
       }
     }
-    if (!done) {
-      const int e0[3] = {cx - rcap, cy - rcap, cz - rcap};
-      const int e1[3] = {cx + rcap, cy + rcap, cz + rcap};
-      done = f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim;
-    }
-    if (done || lvl >= kFineBits) break;
+    if (rcap == rmax) return best;  // every ring of this level searched
+    const int e0[3] = {cx - rcap, cy - rcap, cz - rcap};
+    const int e1[3] = {cx + rcap, cy + rcap, cz + rcap};
+    if (f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim) return best;
   }
-  return best;
 }
 
-// SO(3) exponential (Rodrigues), FP64
+// FP64 runs at 1/64 of the FP32 rate on this part, so the two solvers below
+// are written for few FP64 instructions: one reciprocal square root per
+// Cholesky column instead of a square root and a division per entry, and one
+// sincos of the half angle for the rotation.
+
+// SO(3) exponential (Rodrigues), FP64.  With t = |w|, s = sin(t/2), c = cos(t/2):
+// sin(t)/t = 2 s c / t and (1 - cos t)/t^2 = 2 s^2 / t^2 (no cancellation).
 __device__ void so3_exp_d(const double w[3], double R[9]) {
   const double t2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-  const double t = sqrt(t2);
   double a, b;  // sin(t)/t and (1 - cos(t))/t^2
-  if (t < 1e-8) {
+  if (t2 < 1e-16) {
     a = 1.0 - t2 / 6.0;
     b = 0.5 - t2 / 24.0;
   } else {
-    a = sin(t) / t;
-    b = (1.0 - cos(t)) / t2;
+    const double it = rsqrt(t2);  // 1/t
+    double s, c;
+    sincos(0.5 * (t2 * it), &s, &c);
+    const double si = s * it;
+    a = 2.0 * si * c;
+    b = 2.0 * si * si;
   }
   // R = I + a [w]x + b [w]x^2, with [w]x^2 = w w^T - t2 I
   R[0] = 1.0 + b * (w[0] * w[0] - t2);
@@ -145,34 +184,35 @@ __device__ void so3_exp_d(const double w[3], double R[9]) {
   R[8] = 1.0 + b * (w[2] * w[2] - t2);
 }
 
-// H x = -g by Cholesky in FP64; false if a pivot <= 1e-12 trace(H)
+// H x = -g by Cholesky H = L L^T in FP64; false if a pivot <= 1e-12 trace(H).
+// Only the reciprocals of L's diagonal are kept (r_j = 1 / L_jj).
 __device__ bool chol_solve6(const double H[36], const double g[6], double x[6]) {
-  double L[36];
+  double L[36], r[6];
   double tr = 0.0;
   for (int a = 0; a < 6; ++a) tr += H[7 * a];
   if (!(tr > 0.0)) return false;
+  const double piv_min = 1e-12 * tr;
   for (int j = 0; j < 6; ++j) {
     double d = H[7 * j];
-    for (int m = 0; m < j; ++m) d -= L[6 * j + m] * L[6 * j + m];
-    if (!(d > 1e-12 * tr)) return false;
-    const double l = sqrt(d);
-    L[7 * j] = l;
+    for (int m = 0; m < j; ++m) d = fma(-L[6 * j + m], L[6 * j + m], d);
+    if (!(d > piv_min)) return false;
+    r[j] = rsqrt(d);
     for (int i = j + 1; i < 6; ++i) {
       double v = H[6 * i + j];
-      for (int m = 0; m < j; ++m) v -= L[6 * i + m] * L[6 * j + m];
-      L[6 * i + j] = v / l;
+      for (int m = 0; m < j; ++m) v = fma(-L[6 * i + m], L[6 * j + m], v);
+      L[6 * i + j] = v * r[j];
     }
   }
   double y[6];
   for (int i = 0; i < 6; ++i) {
     double v = -g[i];
-    for (int m = 0; m < i; ++m) v -= L[6 * i + m] * y[m];
-    y[i] = v / L[7 * i];
+    for (int m = 0; m < i; ++m) v = fma(-L[6 * i + m], y[m], v);
+    y[i] = v * r[i];
   }
   for (int i = 5; i >= 0; --i) {
     double v = y[i];
-    for (int m = i + 1; m < 6; ++m) v -= L[6 * m + i] * x[m];
-    x[i] = v / L[7 * i];
+    for (int m = i + 1; m < 6; ++m) v = fma(-L[6 * m + i], x[m], v);
+    x[i] = v * r[i];
   }
   return true;
 }
@@ -186,9 +226,12 @@ __global__ void k_icp_setup(IcpPairState* st, int pairs, const int* src_start, i
                             int* tile_off, const double* T_init, Mat4 T_host, int use_host_T,
                             const float* dmax_dev, float dmax, int iters, float* rt_out) {
   // single block: tile prefix over pairs
-  __shared__ int carry;
-  __shared__ int tmp[1024];
-  if (threadIdx.x == 0) carry = 0;
+  __shared__ int carry, gcarry;
+  __shared__ int tmp[1024], gtmp[1024];
+  if (threadIdx.x == 0) {
+    carry = 0;
+    gcarry = 0;
+  }
   __syncthreads();
   for (int base = 0; base < pairs; base += blockDim.x) {
     const int b = base + threadIdx.x;
@@ -198,16 +241,21 @@ __global__ void k_icp_setup(IcpPairState* st, int pairs, const int* src_start, i
       nt = (int)((n + kTileSrc - 1) / kTileSrc);
     }
     // serial exclusive prefix of this chunk of pairs (pairs are few)
+    const int ng = (nt + kIcpGroup - 1) / kIcpGroup;
     tmp[threadIdx.x] = nt;
+    gtmp[threadIdx.x] = ng;
     __syncthreads();
     if (threadIdx.x == 0) {
-      int run = carry;
+      int run = carry, grun = gcarry;
       for (int j = 0; j < (int)blockDim.x && base + j < pairs; ++j) {
-        const int v = tmp[j];
+        const int v = tmp[j], w = gtmp[j];
         tmp[j] = run;
+        gtmp[j] = grun;
         run += v;
+        grun += w;
       }
       carry = run;
+      gcarry = grun;
     }
     __syncthreads();
     if (b < pairs) {
@@ -228,6 +276,8 @@ __global__ void k_icp_setup(IcpPairState* st, int pairs, const int* src_start, i
       S.tile_begin = tmp[threadIdx.x];
       S.tile_end = tmp[threadIdx.x] + nt;
       tile_off[b] = tmp[threadIdx.x];
+      S.grp_begin = gtmp[threadIdx.x];
+      S.n_grp = ng;
       S.tiles_done = 0;
       S.iters = iters;
       S.rmse = __longlong_as_double(0x7ff8000000000000ll);
@@ -255,11 +305,12 @@ __device__ __forceinline__ int pair_of_tile(const int* tile_off, int pairs, int 
   return lo;
 }
 
-__global__ void __launch_bounds__(kIcpThreads, 2) k_icp(IcpArgs a) {
+__global__ void __launch_bounds__(kIcpThreads, 3) k_icp(IcpArgs a) {
   __shared__ unsigned s_t;
-  __shared__ int s_go, s_last, s_pair;
+  __shared__ int s_go, s_last, s_pair, s_gid, s_g0, s_gsize;
   __shared__ float s_Rt[12];
   __shared__ float s_dmax2;
+  __shared__ int s_corr[kTileSrc];
   __shared__ float sm_s[kIcpWarps][kIcpQ];
   __shared__ float sm_c[kIcpWarps][kIcpQ];
   __shared__ int sm_n[kIcpWarps];
@@ -292,7 +343,7 @@ __global__ void __launch_bounds__(kIcpThreads, 2) k_icp(IcpArgs a) {
               break;
             }
             __nanosleep(ns);
-            if (ns < 2048) ns <<= 1;
+            if (ns < 512) ns <<= 1;
           }
         }
         if (go) {
@@ -316,18 +367,41 @@ __global__ void __launch_bounds__(kIcpThreads, 2) k_icp(IcpArgs a) {
     const int hi = min(se, lo + kTileSrc);
     const int dst_start = a.g.prm[b].start;
 
+    const float dmax2 = s_dmax2;
+    // phase 1: correspondences (sorted target position or -1) of the tile's
+    // points, kept in shared memory so that the search and the accumulation
+    // below do not hold their registers at the same time
+#pragma unroll 1
+    for (int pass = 0; pass < kIcpPPT; ++pass) {
+      const int pos = lo + pass * kIcpThreads + tid;
+      int bj = -1;
+      if (pos < hi) {
+        const int64_t si = __ldg(a.order + pos);
+        const float x = __ldg(a.src + 3 * si), y = __ldg(a.src + 3 * si + 1),
+                    z = __ldg(a.src + 3 * si + 2);
+        float p[3];
+        p[0] = fmaf(s_Rt[0], x, fmaf(s_Rt[1], y, fmaf(s_Rt[2], z, s_Rt[3])));
+        p[1] = fmaf(s_Rt[4], x, fmaf(s_Rt[5], y, fmaf(s_Rt[6], z, s_Rt[7])));
+        p[2] = fmaf(s_Rt[8], x, fmaf(s_Rt[9], y, fmaf(s_Rt[10], z, s_Rt[11])));
+        nearest_within(a.g, b, p, dmax2, bj);
+      }
+      s_corr[pass * kIcpThreads + tid] = bj;
+    }
+    // phase 2: residual and Jacobian rows.  Per-thread partials over its
+    // <= kIcpPPT points are plain FP32 (at most 3 roundings each); every
+    // combination across threads below is compensated (error-free TwoSum)
     float R[12];
 #pragma unroll
     for (int j = 0; j < 12; ++j) R[j] = s_Rt[j];
-    const float dmax2 = s_dmax2;
-    // per-thread partials over its <= kIcpPPT points are plain FP32 (at most
-    // 3 roundings each); every combination across threads below is
-    // compensated (error-free TwoSum merges)
     float part[kIcpQ];
 #pragma unroll
     for (int q = 0; q < kIcpQ; ++q) part[q] = 0.0f;
     int cnt = 0;
-    for (int pos = lo + tid; pos < hi; pos += kIcpThreads) {
+#pragma unroll 1
+    for (int pass = 0; pass < kIcpPPT; ++pass) {
+      const int pos = lo + pass * kIcpThreads + tid;
+      const int bj = s_corr[pass * kIcpThreads + tid];
+      if (pos >= hi || bj < 0) continue;
       const int64_t si = __ldg(a.order + pos);
       const float x = __ldg(a.src + 3 * si), y = __ldg(a.src + 3 * si + 1),
                   z = __ldg(a.src + 3 * si + 2);
@@ -335,10 +409,8 @@ __global__ void __launch_bounds__(kIcpThreads, 2) k_icp(IcpArgs a) {
       p[0] = fmaf(R[0], x, fmaf(R[1], y, fmaf(R[2], z, R[3])));
       p[1] = fmaf(R[4], x, fmaf(R[5], y, fmaf(R[6], z, R[7])));
       p[2] = fmaf(R[8], x, fmaf(R[9], y, fmaf(R[10], z, R[11])));
-      float4 qp;
-      const u64 key = nearest_within(a.g, b, p, dmax2, qp);
-      if (key == kEmptyKey) continue;
-      const int64_t j = dst_start + (int64_t)key_idx(key);
+      const float4 qp = __ldg(a.g.pts + bj);
+      const int64_t j = dst_start + (int64_t)__float_as_int(qp.w);
       const float nx = __ldg(a.dst_n + 3 * j), ny = __ldg(a.dst_n + 3 * j + 1),
                   nz = __ldg(a.dst_n + 3 * j + 2);
       if (!(isfinite(nx) && isfinite(ny) && isfinite(nz))) continue;
@@ -396,34 +468,84 @@ __global__ void __launch_bounds__(kIcpThreads, 2) k_icp(IcpArgs a) {
     __syncthreads();
     if (tid == 0) {
       const int ntiles_b = __ldg(a.tile_off + b + 1) - tb;
-      const int old = atomicAdd(&a.st[b].tiles_done, 1);
-      s_last = (old == ntiles_b - 1);
+      const int gl = (tt - tb) / kIcpGroup;
+      const int gid = a.st[b].grp_begin + gl;
+      const int gsize = min(kIcpGroup, ntiles_b - gl * kIcpGroup);
+      const int old = atomicAdd(a.grp_done + gid, 1);
+      s_last = (old == gsize - 1);
+      s_gid = gid;
+      s_g0 = tb + gl * kIcpGroup;
+      s_gsize = gsize;
     }
     __syncthreads();
     if (!s_last) continue;
 
-    // ---- this block closes round `it` of pair b ----
+    // ---- this block reduces its tile group: tile u of the group in lane u,
+    // a fixed compensated shuffle tree ----
     __threadfence();
-    const int te = __ldg(a.tile_off + b + 1);
-    for (int q = warp; q < kIcpQ; q += kIcpWarps) {
-      KSum t;
-      t.zero();
-      for (int u = tb + lane; u < te; u += 32)
-        t.merge(__ldcg(a.part_s + (int64_t)u * kIcpQ + q), __ldcg(a.part_c + (int64_t)u * kIcpQ + q));
+    {
+      const int gid = s_gid, g0 = s_g0, gs = s_gsize;
+      for (int q = warp; q < kIcpQ; q += kIcpWarps) {
+        KSum t;
+        t.zero();
+        if (lane < gs) {
+          t.s = __ldcg(a.part_s + (int64_t)(g0 + lane) * kIcpQ + q);
+          t.c = __ldcg(a.part_c + (int64_t)(g0 + lane) * kIcpQ + q);
+        }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float s2 = __shfl_down_sync(0xffffffffu, t.s, off);
-        const float c2 = __shfl_down_sync(0xffffffffu, t.c, off);
-        t.merge(s2, c2);
+        for (int off = 16; off > 0; off >>= 1) {
+          const float s2 = __shfl_down_sync(0xffffffffu, t.s, off);
+          const float c2 = __shfl_down_sync(0xffffffffu, t.c, off);
+          t.merge(s2, c2);
+        }
+        if (lane == 0) {
+          a.grp_s[(int64_t)gid * kIcpQ + q] = t.s;
+          a.grp_c[(int64_t)gid * kIcpQ + q] = t.c;
+        }
       }
-      if (lane == 0) sm_tot[q] = (double)t.s + (double)t.c;
-    }
-    if (warp == kIcpWarps - 1) {
-      long long n = 0;
-      for (int u = tb + lane; u < te; u += 32) n += __ldcg(a.part_n + u);
+      if (warp == kIcpWarps - 1) {
+        int n = lane < gs ? __ldcg(a.part_n + g0 + lane) : 0;
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) n += __shfl_down_sync(0xffffffffu, n, off);
-      if (lane == 0) sm_cnt = n;
+        for (int off = 16; off > 0; off >>= 1) n += __shfl_down_sync(0xffffffffu, n, off);
+        if (lane == 0) a.grp_n[gid] = n;
+      }
+      // every tile of this group has been counted for this round; the next
+      // round's tiles start only after the round is published
+      if (tid == 0) a.grp_done[gid] = 0;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      const int old = atomicAdd(&a.st[b].tiles_done, 1);
+      s_last = (old == a.st[b].n_grp - 1);
+    }
+    __syncthreads();
+    if (!s_last) continue;
+
+    // ---- this block closes round `it` of pair b: group partials in order ----
+    __threadfence();
+    {
+      const int gb = a.st[b].grp_begin, ge = gb + a.st[b].n_grp;
+      for (int q = warp; q < kIcpQ; q += kIcpWarps) {
+        KSum t;
+        t.zero();
+        for (int u = gb + lane; u < ge; u += 32)
+          t.merge(__ldcg(a.grp_s + (int64_t)u * kIcpQ + q), __ldcg(a.grp_c + (int64_t)u * kIcpQ + q));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          const float s2 = __shfl_down_sync(0xffffffffu, t.s, off);
+          const float c2 = __shfl_down_sync(0xffffffffu, t.c, off);
+          t.merge(s2, c2);
+        }
+        if (lane == 0) sm_tot[q] = (double)t.s + (double)t.c;
+      }
+      if (warp == kIcpWarps - 1) {
+        long long n = 0;
+        for (int u = gb + lane; u < ge; u += 32) n += __ldcg(a.grp_n + u);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) n += __shfl_down_sync(0xffffffffu, n, off);
+        if (lane == 0) sm_cnt = n;
+      }
     }
     __syncthreads();
     if (tid == 0) {
@@ -493,10 +615,13 @@ void icp_plan(IcpPlan& p, Workspace& ws, const int64_t* src_counts, int pairs) {
   p.pairs = pairs;
   p.n_src = 0;
   p.n_tiles = 0;
+  p.n_groups = 0;
   p.tile = kTileSrc;
   for (int b = 0; b < pairs; ++b) {
     p.n_src += src_counts[b];
-    p.n_tiles += ceil_div(src_counts[b], kTileSrc);
+    const int64_t t = ceil_div(src_counts[b], kTileSrc);
+    p.n_tiles += t;
+    p.n_groups += ceil_div(t, kIcpGroup);
   }
   const int nt = p.n_tiles > 0 ? p.n_tiles : 1;
   p.o_state = ws.reserve(sizeof(IcpPairState) * pairs);
@@ -506,6 +631,11 @@ void icp_plan(IcpPlan& p, Workspace& ws, const int64_t* src_counts, int pairs) {
   p.o_part_s = ws.reserve(sizeof(float) * kIcpQ * nt);
   p.o_part_c = ws.reserve(sizeof(float) * kIcpQ * nt);
   p.o_part_n = ws.reserve(sizeof(int) * nt);
+  const int ng = p.n_groups > 0 ? p.n_groups : 1;
+  p.o_grp_s = ws.reserve(sizeof(float) * kIcpQ * ng);
+  p.o_grp_c = ws.reserve(sizeof(float) * kIcpQ * ng);
+  p.o_grp_n = ws.reserve(sizeof(int) * ng);
+  p.o_grp_done = ws.reserve(sizeof(int) * ng);
   p.o_work = ws.reserve(sizeof(unsigned) * 4);
   order_plan(p.order, ws, p.n_src);
 }
@@ -528,6 +658,9 @@ cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt, c
   k_icp_setup<<<1, 1024, 0, s>>>(st, p.pairs, src_start_dev, p.n_src, tile_off, T_init_dev, Th,
                                  T_init_host != nullptr, dmax_dev, dmax, iters, rt);
   if (cudaMemsetAsync(work, 0, sizeof(unsigned) * 4, s) != cudaSuccess) return CIL_ERR_CUDA;
+  if (cudaMemsetAsync(ws.at<int>(p.o_grp_done), 0,
+                      sizeof(int) * (size_t)(p.n_groups > 0 ? p.n_groups : 1), s) != cudaSuccess)
+    return CIL_ERR_CUDA;
   int* order = ws.at<int>(p.o_order);
   cil_status stt = order_queries(p.order, ws, src, src_start_dev, p.pairs, tgt.prm, rt, order, s);
   if (stt != CIL_OK) return stt;
@@ -547,6 +680,10 @@ cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt, c
   a.part_s = ws.at<float>(p.o_part_s);
   a.part_c = ws.at<float>(p.o_part_c);
   a.part_n = ws.at<int>(p.o_part_n);
+  a.grp_s = ws.at<float>(p.o_grp_s);
+  a.grp_c = ws.at<float>(p.o_grp_c);
+  a.grp_n = ws.at<int>(p.o_grp_n);
+  a.grp_done = ws.at<int>(p.o_grp_done);
   a.work = work;
   a.abort = reinterpret_cast<int*>(work + 1);
   a.err = ctx->err;
