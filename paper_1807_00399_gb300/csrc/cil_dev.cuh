@@ -158,6 +158,22 @@ __device__ __forceinline__ u64 pack_key(float d2, int idx) {
 __device__ __forceinline__ float key_d2(u64 k) { return __uint_as_float((unsigned)(k >> 32)); }
 __device__ __forceinline__ int key_idx(u64 k) { return (int)(unsigned)(k & 0xffffffffu); }
 
+// Visit the points [s, s + n) of the sorted array in chunks of W whose loads
+// are issued together (the loop is otherwise bound by load latency).
+template <int W = 4, class F>
+__device__ __forceinline__ void for_points(const float4* pts, int s, int n, F&& fn) {
+  const int e = s + n;
+  for (int j = s; j < e; j += W) {
+    float4 p[W];
+#pragma unroll
+    for (int u = 0; u < W; ++u)
+      if (j + u < e) p[u] = __ldg(pts + j + u);
+#pragma unroll
+    for (int u = 0; u < W; ++u)
+      if (j + u < e) fn(p[u], j + u);
+  }
+}
+
 // squared distance from q to the box [lo, hi] (per axis), 0 inside
 __device__ __forceinline__ float box_d2(const float q[3], const float lo[3], const float hi[3]) {
   float s = 0.0f;
@@ -316,10 +332,9 @@ __device__ __forceinline__ void grid_knn(const GridView& g, int cloud, const flo
         int s, n;
         if (!cell_lookup(g, cell_key(lvl, cloud, x, y, z), s, n)) continue;
         ++nvis;
-        for (int j = s; j < s + n; ++j) {
-          const float4 p = __ldg(g.pts + j);
+        for_points(g.pts, s, n, [&](const float4& p, int) {
           top.push(pack_key(sqdist(p.x, p.y, p.z, q[0], q[1], q[2]), __float_as_int(p.w)));
-        }
+        });
       }
       if (r == rmax) {
         done = true;  // the explored cube holds the whole cloud
@@ -364,11 +379,10 @@ __device__ __forceinline__ void grid_knn_within(const GridView& g, int cloud, co
         if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > lim) continue;
         int s, n;
         if (!cell_lookup(g, cell_key(lvl, cloud, x, y, z), s, n)) continue;
-        for (int j = s; j < s + n; ++j) {
-          const float4 p = __ldg(g.pts + j);
+        for_points(g.pts, s, n, [&](const float4& p, int) {
           const float d2 = sqdist(p.x, p.y, p.z, q[0], q[1], q[2]);
           if (d2 <= r2) top.push(pack_key(d2, __float_as_int(p.w)));
-        }
+        });
       }
       if (r == rmax) {
         done = true;
@@ -411,8 +425,7 @@ __device__ __forceinline__ u64 grid_nn(const GridView& g, int cloud, const float
       if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > lim) continue;
       int s, n;
       if (!cell_lookup(g, cell_key(P.level, cloud, x, y, z), s, n)) continue;
-      for (int j = s; j < s + n; ++j) {
-        const float4 p = __ldg(g.pts + j);
+      for_points(g.pts, s, n, [&](const float4& p, int) {
         const float d2 = sqdist(p.x, p.y, p.z, q[0], q[1], q[2]);
         if (d2 <= dmax2) {
           const u64 key = pack_key(d2, __float_as_int(p.w));
@@ -421,7 +434,7 @@ __device__ __forceinline__ u64 grid_nn(const GridView& g, int cloud, const float
             lim = fminf(lim, d2);
           }
         }
-      }
+      });
     }
   }
   return best;

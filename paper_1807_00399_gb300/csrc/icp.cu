@@ -62,11 +62,14 @@ struct IcpArgs {
   int* err;
 };
 
+constexpr int kDirCells = 64;     // coarse cells of the directory search at most
+constexpr int kDirectScan = 128;  // coarse cells up to this many points are scanned whole
+constexpr int kLookupCost = 4;
+
 // Points of one cell that improve on (best, lim); lim = min(dmax2, best d^2).
 __device__ __forceinline__ void scan_cell(const GridView& g, int s, int n, const float q[3],
                                           float dmax2, u64& best, int& bj, float& lim) {
-  for (int j = s; j < s + n; ++j) {
-    const float4 p = __ldg(g.pts + j);
+  for_points(g.pts, s, n, [&](const float4& p, int j) {
     const float d2 = sqdist(p.x, p.y, p.z, q[0], q[1], q[2]);
     const u64 key = pack_key(d2, __float_as_int(p.w));
     if (d2 <= dmax2 && key < best) {
@@ -74,6 +77,102 @@ __device__ __forceinline__ void scan_cell(const GridView& g, int s, int n, const
       bj = j;
       lim = fminf(lim, d2);
     }
+  });
+}
+
+// The ball of radius sqrt(lim) around q leaves the 3x3x3 block around the
+// base-level cell c (already searched).  The 8x coarser cells meeting the
+// ball act as a directory: empty ones are skipped whole, small ones scanned,
+// and in large ones that the ball meets in few base-level cells only those
+// cells are looked up (dense surfaces seen from off the surface stay cheap).
+// Returns false, having searched nothing, when the ball spans more than
+// kDirCells coarse cells (large rejection distances), and true once every
+// cell meeting the ball has been searched.
+__device__ __forceinline__ bool escalate_directory(const GridView& g, int cloud, const float q[3],
+                                                float dmax2, const int c[3], u64& best, int& bj,
+                                                float& lim) {
+  const GridParams& P = g.prm[cloud];
+  const float inv_fine = P.inv_fine;
+  CellFrame f;
+  f.load(P, cloud);
+  int s, n;
+  const int Lc = next_level(f.level);
+  CellFrame fc;
+  fc.load_level(P, cloud, Lc, ldexpf(P.fine, Lc));
+  const float rad2 = fmaf(sqrtf(lim), 1.0f + 1e-6f, f.eps);
+  int clo[3], chi[3], blo[3], bhi[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    clo[a] = fc.cell_of(q[a] - rad2, a, inv_fine);
+    chi[a] = fc.cell_of(q[a] + rad2, a, inv_fine);
+    blo[a] = f.cell_of(q[a] - rad2, a, inv_fine);
+    bhi[a] = f.cell_of(q[a] + rad2, a, inv_fine);
+  }
+  if ((chi[0] - clo[0] + 1) * (chi[1] - clo[1] + 1) * (chi[2] - clo[2] + 1) <= kDirCells) {
+    const int sh = Lc - f.level;
+    for (int Z = clo[2]; Z <= chi[2]; ++Z)
+      for (int Y = clo[1]; Y <= chi[1]; ++Y)
+        for (int X = clo[0]; X <= chi[0]; ++X) {
+          const int C3[3] = {X, Y, Z};
+          if (fc.range_d2(q, C3, C3) * (1.0f - 1e-6f) > lim) continue;
+          if (!cell_lookup(g, cell_key(Lc, cloud, X, Y, Z), s, n)) continue;
+          const int zl = max(Z << sh, blo[2]), zh = min(((Z + 1) << sh) - 1, bhi[2]);
+          const int yl = max(Y << sh, blo[1]), yh = min(((Y + 1) << sh) - 1, bhi[1]);
+          const int xl = max(X << sh, blo[0]), xh = min(((X + 1) << sh) - 1, bhi[0]);
+          // a base-level lookup costs about kLookupCost streamed point tests
+          if (n <= kDirectScan || n < kLookupCost * (xh - xl + 1) * (yh - yl + 1) * (zh - zl + 1)) {
+            scan_cell(g, s, n, q, dmax2, best, bj, lim);
+            continue;
+          }
+          for (int z = zl; z <= zh; ++z)
+            for (int y = yl; y <= yh; ++y)
+              for (int x = xl; x <= xh; ++x) {
+                if (abs(x - c[0]) <= 1 && abs(y - c[1]) <= 1 && abs(z - c[2]) <= 1)
+                  continue;  // searched by the caller
+                const int c3[3] = {x, y, z};
+                if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > lim) continue;
+                int s2, n2;
+                if (cell_lookup(g, cell_key(f.level, cloud, x, y, z), s2, n2))
+                  scan_cell(g, s2, n2, q, dmax2, best, bj, lim);
+              }
+        }
+    return true;  // every cell meeting the ball was searched
+  }
+  return false;
+}
+
+// Ring search from the first coarser level upward (kRingCap rings per level)
+// for balls too large for the directory search.
+__device__ __forceinline__ void escalate_rings(const GridView& g, int cloud, const float q[3],
+                                            float dmax2, u64& best, int& bj, float& lim) {
+  const GridParams& P = g.prm[cloud];
+  const float inv_fine = P.inv_fine;
+  for (int lvl = next_level(P.level);; lvl = next_level(lvl)) {
+    CellFrame f;
+    f.load_level(P, cloud, lvl, ldexpf(P.fine, lvl));
+    const int cx = f.cell_of(q[0], 0, inv_fine);
+    const int cy = f.cell_of(q[1], 1, inv_fine);
+    const int cz = f.cell_of(q[2], 2, inv_fine);
+    const int rmax = max(max(max(cx, f.hi[0] - cx), max(cy, f.hi[1] - cy)), max(cz, f.hi[2] - cz));
+    const int rcap = lvl >= kFineBits ? rmax : min(rmax, kRingCap);
+    for (int r = 0; r <= rcap; ++r) {
+      if (r > 0) {
+        const int e0[3] = {cx - r + 1, cy - r + 1, cz - r + 1};
+        const int e1[3] = {cx + r - 1, cy + r - 1, cz + r - 1};
+        if (f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim) return;
+      }
+      CIL_SHELL_FOR(f, cx, cy, cz, r, x, y, z) {
+        const int c3[3] = {x, y, z};
+        if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > lim) continue;
+        int s, n;
+        if (cell_lookup(g, cell_key(lvl, cloud, x, y, z), s, n))
+          scan_cell(g, s, n, q, dmax2, best, bj, lim);
+      }
+    }
+    if (rcap == rmax) return;  // every ring of this level searched
+    const int e0[3] = {cx - rcap, cy - rcap, cz - rcap};
+    const int e1[3] = {cx + rcap, cy + rcap, cz + rcap};
+    if (f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim) return;
   }
 }
 
@@ -121,34 +220,12 @@ __device__ __forceinline__ u64 nearest_within(const GridView& g, int cloud, cons
     const int e0[3] = {c[0] - 1, c[1] - 1, c[2] - 1};
     const int e1[3] = {c[0] + 1, c[1] + 1, c[2] + 1};
     if (f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim) return best;
+
+    if (escalate_directory(g, cloud, q, dmax2, c, best, bj, lim)) return best;
   }
-  for (int lvl = next_level(P.level);; lvl = next_level(lvl)) {
-    CellFrame f;
-    f.load_level(P, cloud, lvl, ldexpf(P.fine, lvl));
-    const int cx = f.cell_of(q[0], 0, inv_fine);
-    const int cy = f.cell_of(q[1], 1, inv_fine);
-    const int cz = f.cell_of(q[2], 2, inv_fine);
-    const int rmax = max(max(max(cx, f.hi[0] - cx), max(cy, f.hi[1] - cy)), max(cz, f.hi[2] - cz));
-    const int rcap = lvl >= kFineBits ? rmax : min(rmax, kRingCap);
-    for (int r = 0; r <= rcap; ++r) {
-      if (r > 0) {
-        const int e0[3] = {cx - r + 1, cy - r + 1, cz - r + 1};
-        const int e1[3] = {cx + r - 1, cy + r - 1, cz + r - 1};
-        if (f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim) return best;
-      }
-      CIL_SHELL_FOR(f, cx, cy, cz, r, x, y, z) {
-        const int c3[3] = {x, y, z};
-        if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > lim) continue;
-        int s, n;
-        if (cell_lookup(g, cell_key(lvl, cloud, x, y, z), s, n))
-          scan_cell(g, s, n, q, dmax2, best, bj, lim);
-      }
-    }
-    if (rcap == rmax) return best;  // every ring of this level searched
-    const int e0[3] = {cx - rcap, cy - rcap, cz - rcap};
-    const int e1[3] = {cx + rcap, cy + rcap, cz + rcap};
-    if (f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim) return best;
-  }
+  // a ball spanning many coarse cells (large rejection distance)
+  escalate_rings(g, cloud, q, dmax2, best, bj, lim);
+  return best;
 }
 
 // FP64 runs at 1/64 of the FP32 rate on this part, so the two solvers below
@@ -305,7 +382,7 @@ __device__ __forceinline__ int pair_of_tile(const int* tile_off, int pairs, int 
   return lo;
 }
 
-__global__ void __launch_bounds__(kIcpThreads, 3) k_icp(IcpArgs a) {
+__global__ void __launch_bounds__(kIcpThreads, 2) k_icp(IcpArgs a) {
   __shared__ unsigned s_t;
   __shared__ int s_go, s_last, s_pair, s_gid, s_g0, s_gsize;
   __shared__ float s_Rt[12];

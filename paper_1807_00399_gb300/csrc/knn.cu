@@ -366,15 +366,14 @@ __global__ void __launch_bounds__(128) k_normals_radius(GridView g, int64_t n, f
         if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > r2) continue;
         int s, cnt;
         if (!cell_lookup(g, cell_key(P.level, 0, x, y, z), s, cnt)) continue;
-        for (int j = s; j < s + cnt; ++j) {
-          const float4 p = __ldg(g.pts + j);
+        for_points(g.pts, s, cnt, [&](const float4& p, int) {
           if (sqdist(p.x, p.y, p.z, q[0], q[1], q[2]) <= r2) {
             sx += p.x - q[0];
             sy += p.y - q[1];
             sz += p.z - q[2];
             ++m;
           }
-        }
+        });
       }
   if (out_cnt) out_cnt[qi] = m;
   const float nan = __int_as_float(0x7fc00000);
@@ -393,8 +392,7 @@ __global__ void __launch_bounds__(128) k_normals_radius(GridView g, int64_t n, f
         if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > r2) continue;
         int s, cnt;
         if (!cell_lookup(g, cell_key(P.level, 0, x, y, z), s, cnt)) continue;
-        for (int j = s; j < s + cnt; ++j) {
-          const float4 p = __ldg(g.pts + j);
+        for_points(g.pts, s, cnt, [&](const float4& p, int) {
           if (sqdist(p.x, p.y, p.z, q[0], q[1], q[2]) <= r2) {
             const float ex = (p.x - q[0]) - mx, ey = (p.y - q[1]) - my, ez = (p.z - q[2]) - mz;
             cxx = fmaf(ex, ex, cxx);
@@ -404,7 +402,7 @@ __global__ void __launch_bounds__(128) k_normals_radius(GridView g, int64_t n, f
             cyz = fmaf(ey, ez, cyz);
             czz = fmaf(ez, ez, czz);
           }
-        }
+        });
       }
   const float C[6] = {cxx * im, cxy * im, cxz * im, cyy * im, cyz * im, czz * im};
   const float vp[3] = {vx, vy, vz};

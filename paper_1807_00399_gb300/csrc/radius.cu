@@ -47,8 +47,7 @@ __global__ void __launch_bounds__(128) k_radius(GridView g, const float* __restr
         if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > r2) continue;
         int s, n;
         if (!cell_lookup(g, cell_key(P.level, 0, x, y, z), s, n)) continue;
-        for (int j = s; j < s + n; ++j) {
-          const float4 p = __ldg(g.pts + j);
+        for_points(g.pts, s, n, [&](const float4& p, int) {
           const float d2 = sqdist(p.x, p.y, p.z, q[0], q[1], q[2]);
           if (d2 <= r2) {
             if (kFill) {
@@ -59,7 +58,7 @@ __global__ void __launch_bounds__(128) k_radius(GridView g, const float* __restr
               ++cnt;
             }
           }
-        }
+        });
       }
   if (!kFill) off[qi] = cnt;
 }
