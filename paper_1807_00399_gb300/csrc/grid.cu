@@ -538,20 +538,19 @@ __global__ void __launch_bounds__(1024) k_choose_level(GridParams* prm, const fl
 // ---------------------------------------------------------------------------
 // 6. cell table
 // ---------------------------------------------------------------------------
-// Levels hashed in a table: table 0 holds the cloud's level and its
-// escalation levels (+3, +6, +9, capped at 10, duplicates dropped); table 1
-// the correspondence level only.  slot < 0 when the table has no such slot.
+// Levels hashed in a table: table 0 holds the cloud's level L, the
+// directory level of the correspondence search (L + 2) and the k-NN
+// escalation levels (L + 3, + 6, + 9), each capped at 10, duplicates
+// dropped; table 1 the correspondence level only.  -1 when the table has no
+// such slot.
 __device__ __forceinline__ int table_level(const GridParams& P, int which, int slot) {
   if (which) return slot == 0 ? P.level2 : -1;
-  int lvl = P.level;
-  for (int j = 0; j < slot; ++j) {
-    const int nx = min(lvl + kEscalateStep, kFineBits);
-    if (nx == lvl) return -1;
-    lvl = nx;
-  }
+  const int add[5] = {0, 2, 3, 6, 9};
+  const int lvl = min(P.level + add[slot], kFineBits);
+  if (slot > 0 && lvl == min(P.level + add[slot - 1], kFineBits)) return -1;
   return lvl;
 }
-constexpr int kTableSlots = 4;
+constexpr int kTableSlots = 5;
 
 __device__ __forceinline__ bool same_cell(u64 a, u64 b, int L) {
   return (a >> 30) == (b >> 30) && ((unsigned)(a & 0x3fffffffu) >> (3 * L)) ==
@@ -616,10 +615,10 @@ void grid_plan(GridPlan& p, Workspace& ws, int64_t n, int clouds, bool icp_table
   p.n = n;
   p.clouds = clouds;
   p.icp_table = icp_table;
-  // cells hashed in the k-NN table: at most min(points, cells of the level)
-  // for each of its <= 4 levels (spaced x8); whatever the cloud's level, that
-  // is <= n + n + 4096 + 8 per cloud.  Keep the load factor <= 1/2.
-  const uint64_t entries = 2 * (uint64_t)(n > 0 ? n : 1) + (uint64_t)clouds * (4096 + 8);
+  // cells hashed in the table: at most min(points, cells of the level) for
+  // each of its <= 5 levels (L, L+2, L+3, L+6, L+9); whatever the cloud's
+  // level, that is <= 3n + 16^3 + 2^3 per cloud.  Keep the load factor <= 1/2.
+  const uint64_t entries = 3 * (uint64_t)(n > 0 ? n : 1) + (uint64_t)clouds * (4096 + 8);
   const uint64_t slots = next_pow2_u32(2 * entries);
   p.mask = (unsigned)(slots - 1);
   p.radix_blocks = ceil_div(n > 0 ? n : 1, kRsTile);

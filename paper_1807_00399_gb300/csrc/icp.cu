@@ -62,7 +62,8 @@ struct IcpArgs {
   int* err;
 };
 
-constexpr int kDirCells = 64;     // coarse cells of the directory search at most
+constexpr int kDirLevels = 2;     // directory level = base level + 2 (in the cell table)
+constexpr int kDirCells = 125;    // directory cells meeting the ball at most
 constexpr int kDirectScan = 128;  // coarse cells up to this many points are scanned whole
 constexpr int kLookupCost = 4;
 
@@ -81,8 +82,9 @@ __device__ __forceinline__ void scan_cell(const GridView& g, int s, int n, const
 }
 
 // The ball of radius sqrt(lim) around q leaves the 3x3x3 block around the
-// base-level cell c (already searched).  The 8x coarser cells meeting the
-// ball act as a directory: empty ones are skipped whole, small ones scanned,
+// base-level cell c (already searched).  The cells of the directory level
+// (4x the base edge, hashed in the table for this) meeting the ball act as a
+// directory: empty ones are skipped whole, small ones scanned,
 // and in large ones that the ball meets in few base-level cells only those
 // cells are looked up (dense surfaces seen from off the surface stay cheap).
 // Returns false, having searched nothing, when the ball spans more than
@@ -96,7 +98,7 @@ __device__ __forceinline__ bool escalate_directory(const GridView& g, int cloud,
   CellFrame f;
   f.load(P, cloud);
   int s, n;
-  const int Lc = next_level(f.level);
+  const int Lc = min(f.level + kDirLevels, kFineBits);
   CellFrame fc;
   fc.load_level(P, cloud, Lc, ldexpf(P.fine, Lc));
   const float rad2 = fmaf(sqrtf(lim), 1.0f + 1e-6f, f.eps);
