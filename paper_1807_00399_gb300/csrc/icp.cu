@@ -301,6 +301,48 @@ __device__ __forceinline__ void rt_from_T(const double T[16], float Rt[12]) {
     for (int b = 0; b < 4; ++b) Rt[4 * a + b] = (float)T[4 * a + b];
 }
 
+// Round close of one pair (one thread): the final round records the RMSE and
+// inlier count; any other solves H xi = -g and left-composes the update.
+// Out of line so that its FP64 temporaries do not count against the
+// registers of the search.
+__device__ __noinline__ void close_round(IcpPairState& S, const double* tot, long long n,
+                                         bool final_round) {
+  if (final_round) {
+    S.n_inl = n;
+    S.rmse = n > 0 ? sqrt(tot[27] / (double)n) : __longlong_as_double(0x7ff8000000000000ll);
+    return;
+  }
+  double H[36], g[6], xi[6];
+  int q = 0;
+  for (int u = 0; u < 6; ++u)
+    for (int v = u; v < 6; ++v) {
+      H[6 * u + v] = tot[q];
+      H[6 * v + u] = tot[q];
+      ++q;
+    }
+  for (int u = 0; u < 6; ++u) g[u] = tot[21 + u];
+  if (n < 6 || !chol_solve6(H, g, xi)) {
+    S.status = CIL_ERR_DEGENERATE;
+    return;
+  }
+  double T[16], dR[9], Tn[16];
+  for (int j = 0; j < 16; ++j) T[j] = __ldcg(&S.T[j]);
+  so3_exp_d(xi, dR);
+  for (int u = 0; u < 3; ++u) {
+    for (int v = 0; v < 4; ++v)
+      Tn[4 * u + v] = dR[3 * u] * T[v] + dR[3 * u + 1] * T[4 + v] + dR[3 * u + 2] * T[8 + v];
+    Tn[4 * u + 3] += xi[3 + u];
+  }
+  Tn[12] = 0.0;
+  Tn[13] = 0.0;
+  Tn[14] = 0.0;
+  Tn[15] = 1.0;
+  for (int j = 0; j < 16; ++j) S.T[j] = Tn[j];
+  float Rt[12];
+  rt_from_T(Tn, Rt);
+  for (int j = 0; j < 12; ++j) S.Rt[j] = Rt[j];
+}
+
 __global__ void k_icp_setup(IcpPairState* st, int pairs, const int* src_start, int64_t n_src_single,
                             int* tile_off, const double* T_init, Mat4 T_host, int use_host_T,
                             const float* dmax_dev, float dmax, int iters, float* rt_out) {
@@ -629,41 +671,7 @@ __global__ void __launch_bounds__(kIcpThreads, 2) k_icp(IcpArgs a) {
     __syncthreads();
     if (tid == 0) {
       IcpPairState& S = a.st[b];
-      const long long n = sm_cnt;
-      if (it == a.rounds - 1) {
-        S.n_inl = n;
-        S.rmse = n > 0 ? sqrt(sm_tot[27] / (double)n) : __longlong_as_double(0x7ff8000000000000ll);
-      } else {
-        double H[36], g[6], xi[6];
-        int q = 0;
-        for (int u = 0; u < 6; ++u)
-          for (int v = u; v < 6; ++v) {
-            H[6 * u + v] = sm_tot[q];
-            H[6 * v + u] = sm_tot[q];
-            ++q;
-          }
-        for (int u = 0; u < 6; ++u) g[u] = sm_tot[21 + u];
-        if (n < 6 || !chol_solve6(H, g, xi)) {
-          S.status = CIL_ERR_DEGENERATE;
-        } else {
-          double T[16], dR[9], Tn[16];
-          for (int j = 0; j < 16; ++j) T[j] = __ldcg(&S.T[j]);
-          so3_exp_d(xi, dR);
-          for (int u = 0; u < 3; ++u) {
-            for (int v = 0; v < 4; ++v)
-              Tn[4 * u + v] = dR[3 * u] * T[v] + dR[3 * u + 1] * T[4 + v] + dR[3 * u + 2] * T[8 + v];
-            Tn[4 * u + 3] += xi[3 + u];
-          }
-          Tn[12] = 0.0;
-          Tn[13] = 0.0;
-          Tn[14] = 0.0;
-          Tn[15] = 1.0;
-          for (int j = 0; j < 16; ++j) S.T[j] = Tn[j];
-          float Rt[12];
-          rt_from_T(Tn, Rt);
-          for (int j = 0; j < 12; ++j) S.Rt[j] = Rt[j];
-        }
-      }
+      close_round(S, sm_tot, sm_cnt, it == a.rounds - 1);
       S.tiles_done = 0;
       __threadfence();
       st_release_i32(&S.iter_done, it + 1);
