@@ -248,7 +248,7 @@ def run_ours(args):
     dst = torch.from_numpy(pair.target).to(dev)
     nrm = torch.empty_like(dst)
     T = torch.empty(16, dtype=torch.float64, device=dev)
-    rep = torch.empty(32, dtype=torch.uint8, device=dev)
+    rep = torch.empty(ctypes.sizeof(cil.IcpReport), dtype=torch.uint8, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     vp = pair.viewpoint
 
@@ -262,7 +262,6 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     # ---- device-resident timed region ----
-    import ctypes
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     L.cil_timing_reset()
@@ -300,7 +299,7 @@ def run_ours(args):
     src_h = torch.from_numpy(pair.source).pin_memory()
     dst_h = torch.from_numpy(pair.target).pin_memory()
     T_h = torch.empty(16, dtype=torch.float64).pin_memory()
-    rep_h_buf = torch.empty(32, dtype=torch.uint8).pin_memory()
+    rep_h_buf = torch.empty(ctypes.sizeof(cil.IcpReport), dtype=torch.uint8).pin_memory()
     src_d = torch.empty_like(src)
     dst_d = torch.empty_like(dst)
     e2e_steps = max(1, min(args.steps, 200))
@@ -351,6 +350,9 @@ def run_ours(args):
     batched = None
     if not args.no_batch:
         batched = run_batched(args, rank)
+    learned_res = None
+    if not args.no_learned:
+        learned_res = run_learned(args, rank)
 
     # ---- CPU baseline (oracle, rank 0, N = 1 only) ----
     cpu = None
@@ -381,11 +383,12 @@ def run_ours(args):
             "icp_status": rep_h["status"],
             "e2e": {"value": e2e_value, "unit": "queries/s",
                     "h2d_bytes_per_step": int(src.numel() * 4 + dst.numel() * 4),
-                    "d2h_bytes_per_step": 16 * 8 + 32},
+                    "d2h_bytes_per_step": int(T_h.numel() * 8 + rep_h_buf.numel())},
             "roofline": roofline,
             "kernels_ms_per_launch": per_launch_ms,
             "cpu_baseline": cpu,
             "batched": batched,
+            "learned": learned_res,
             "gpu_launches": int(n1 - n0),
             "clocks": clocks,
         }
@@ -465,6 +468,25 @@ def run_batched(args, rank: int, B: int = 256, runs: int = 5):
             "median_rot_err_deg_vs_generator": float(np.median(rot_err))}
 
 
+def run_learned(args, rank: int, B: int = 256):
+    """Learned warm start + batched ICP against batched ICP from identity on
+    256 held-out pairs (10,000-point wavy surfaces, rotations up to 90 deg,
+    translations up to 0.5; 4,096-point subsamples into the network): success
+    rate (final RMSE < 0.005) and pairs/s.  Weights: the committed checkpoint,
+    trained by this library's kernels on 200k generated pairs."""
+    import paper_1807_00399_gb300 as cil
+    from paper_1807_00399_gb300 import learned, synth
+
+    net = cil.PointNet(B, 4096)
+    meta = learned.load_checkpoint(net, learned.CHECKPOINT)
+    pairs, s_sub, d_sub = synth.warm_start_pairs(777 + args.seed + rank, B, n=10_000)
+    res = learned.evaluate(net, pairs, s_sub, d_sub, iters=ICP_ITERS, max_corr_dist=0.1)
+    net.close()
+    res["checkpoint"] = {"steps": meta["step"], "pairs_seen": meta["extra"].get("pairs_seen"),
+                         "train_wall_s": meta["extra"].get("wall_s")}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -475,6 +497,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 256-pair batched-vs-sequential measurement")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned warm-start measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

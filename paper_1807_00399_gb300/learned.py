@@ -28,6 +28,31 @@ import numpy as np
 
 SUCCESS_RMSE = 0.005
 
+# Parameter layout of the network (the order of cil_pointnet_set_params):
+# shared MLP 3 -> 64 -> 128 -> 256 on each cloud, max-pool, head 512 -> 256 -> 9.
+LAYOUT = (("W1", (64, 3)), ("b1", (64,)), ("W2", (128, 64)), ("b2", (128,)),
+          ("W3", (256, 128)), ("b3", (256,)), ("W4", (256, 512)), ("b4", (256,)),
+          ("W5", (9, 256)), ("b5", (9,)))
+CHECKPOINT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "warmstart")
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """He-uniform weights and zero biases; the last layer starts near zero with
+    a bias that makes the initial prediction the identity (6-D rotation
+    (e1, e2), zero translation).  Flat float32 in LAYOUT order."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for name, shape in LAYOUT:
+        if name.startswith("W"):
+            lim = math.sqrt(6.0 / shape[1])
+            w = rng.uniform(-lim, lim, shape)
+            out.append((w * 1e-2 if name == "W5" else w).ravel())
+        elif name == "b5":
+            out.append(np.array([1.0, 0, 0, 0, 1.0, 0, 0, 0, 0]))
+        else:
+            out.append(np.zeros(shape))
+    return np.concatenate(out).astype(np.float32)
+
 
 def _rotations(u, angle):
     """Rotation matrices from unit axes u (B,3) and angles (B,) (Rodrigues,
@@ -141,8 +166,8 @@ def evaluate(net, pairs, src_sub, dst_sub, iters: int = 30, max_corr_dist: float
     T_init = torch.empty((B, 16), dtype=torch.float64, device="cuda")
     T_l = torch.empty((B, 16), dtype=torch.float64, device="cuda")
     T_i = torch.empty((B, 16), dtype=torch.float64, device="cuda")
-    rep_l = torch.empty((B, 32), dtype=torch.uint8, device="cuda")
-    rep_i = torch.empty((B, 32), dtype=torch.uint8, device="cuda")
+    rep_l = torch.empty((B, 24), dtype=torch.uint8, device="cuda")  # cil_icp_report
+    rep_i = torch.empty((B, 24), dtype=torch.uint8, device="cuda")
     # warm-up (graph capture) outside the timing
     net.forward(clouds, T_out=T_init)
     h.run(src, dst, T_init=T_init, T_out=T_l, rep=rep_l)
@@ -186,3 +211,77 @@ def evaluate(net, pairs, src_sub, dst_sub, iters: int = 30, max_corr_dist: float
         "successful_pairs_per_s_learned": float(ok_l.sum()) / (ms_learned / 1e3),
         "successful_pairs_per_s_identity": float(ok_i.sum()) / (ms_identity / 1e3),
     }
+
+
+def check_labels(n_pairs: int = 64, seed: int = 99, iters: int = 30) -> dict:
+    """Cross-check of the generator labels by plain ICP: pairs drawn like the
+    training pairs (full 10,000-point clouds), registered from their label;
+    ICP should barely move a correct label."""
+    import torch
+
+    from . import Batch, synth
+    pairs, _, _ = synth.warm_start_pairs(seed, n_pairs, n=10_000)
+    B = len(pairs)
+    src = torch.from_numpy(np.concatenate([p.source for p in pairs])).cuda()
+    dst = torch.from_numpy(np.concatenate([p.target for p in pairs])).cuda()
+    T_gt = np.stack([p.T_gt for p in pairs]).reshape(B, 16)
+    h = Batch([len(p.source) for p in pairs], [len(p.target) for p in pairs], k=10, iters=iters,
+              max_corr_dist=0.1, viewpoint=(0.0, 0.0, 10.0))
+    T, _ = h.run(src, dst, T_init=torch.from_numpy(T_gt).cuda())
+    torch.cuda.synchronize()
+    h.close()
+    Tn = T.cpu().numpy().reshape(B, 4, 4)
+    d_rot = rot_err_deg(Tn, T_gt)
+    d_t = np.linalg.norm(Tn[:, :3, 3] - T_gt.reshape(B, 4, 4)[:, :3, 3], axis=1)
+    return {"pairs": B, "icp_from_label_rot_change_deg_median": float(np.median(d_rot)),
+            "icp_from_label_rot_change_deg_max": float(d_rot.max()),
+            "icp_from_label_trans_change_median": float(np.median(d_t))}
+
+
+def main(argv=None):
+    """python -m paper_1807_00399_gb300.learned train|eval ..."""
+    import argparse
+
+    import torch
+
+    from . import PointNet, synth
+    ap = argparse.ArgumentParser(prog="python -m paper_1807_00399_gb300.learned")
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    tr = sub.add_parser("train", help="train from the seeded initialisation, write a checkpoint")
+    tr.add_argument("--pairs", type=int, default=200_000, help="training pairs (steps = pairs / batch)")
+    tr.add_argument("--batch", type=int, default=256)
+    tr.add_argument("--lr", type=float, default=1e-3)
+    tr.add_argument("--seed", type=int, default=0)
+    tr.add_argument("--out", default=CHECKPOINT)
+    ev = sub.add_parser("eval", help="held-out evaluation of a checkpoint")
+    ev.add_argument("--ckpt", default=CHECKPOINT)
+    ev.add_argument("--pairs", type=int, default=256)
+    ev.add_argument("--seed", type=int, default=777)
+    a = ap.parse_args(argv)
+    if a.cmd == "train":
+        steps = -(-a.pairs // a.batch)
+        net = PointNet(a.batch, 4096, params=init_params(a.seed))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hist, _ = train(net, steps, B=a.batch, lr=a.lr, seed=a.seed, log_every=max(1, steps // 20))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        extra = {"pairs_seen": steps * a.batch, "batch": a.batch, "lr": a.lr, "wall_s": wall,
+                 "loss_history": hist, "label_check": check_labels()}
+        os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
+        save_checkpoint(net, a.out, steps, a.seed, extra)
+        net.close()
+        print(json.dumps({"steps": steps, "wall_s": wall, "first_loss": hist[0][1],
+                          "last_loss": hist[-1][1], "label_check": extra["label_check"]}))
+    else:
+        net = PointNet(a.pairs, 4096)
+        meta = load_checkpoint(net, a.ckpt)
+        pairs, s_sub, d_sub = synth.warm_start_pairs(a.seed, a.pairs, n=10_000)
+        res = evaluate(net, pairs, s_sub, d_sub)
+        net.close()
+        res["checkpoint_steps"] = meta["step"]
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()
