@@ -1,0 +1,83 @@
+"""One invocation of the hot path on a named synthetic workload, for
+profilers (ncu) and quick timing.
+
+    python -m paper_1807_00399_gb300.profile_run --workload depth --op register --iters 30
+    python -m paper_1807_00399_gb300.profile_run --workload lidar --op radius
+
+Workloads: surface (10,000-point wavy surface pair), depth (640x480 depth
+frames, ~3.07e5 points), lidar (64 x 2048 sweep, ~1.2e5 returns), batch (256
+surface pairs with sizes log-uniform in [2e3, 2e5]).  Ops: register (grid,
+k-NN normals and point-to-plane ICP), knn (self k-NN), normals, radius
+(radius search), batch (the batched graph run; workload batch only).  Each op
+runs --repeat times after one warm-up call; the per-kernel times recorded by
+the library are printed as one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import sys
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(prog="python -m paper_1807_00399_gb300.profile_run")
+    ap.add_argument("--workload", choices=["surface", "depth", "lidar", "batch"], default="depth")
+    ap.add_argument("--op", choices=["register", "knn", "normals", "radius", "batch"],
+                    default="register")
+    ap.add_argument("--iters", type=int, default=30, help="ICP iterations")
+    ap.add_argument("--k", type=int, default=0, help="neighbours (default: 16 lidar, else 10)")
+    ap.add_argument("--radius", type=float, default=0.5)
+    ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--seed", type=int, default=0)
+    a = ap.parse_args(argv)
+
+    import torch
+
+    import paper_1807_00399_gb300 as cil
+    from paper_1807_00399_gb300 import synth
+
+    k = a.k or (16 if a.workload == "lidar" else 10)
+    if a.workload == "batch":
+        sizes = synth.batch_sizes(a.seed, 256)
+        src, dst, _ = synth.surface_batch_torch(1000 + a.seed, sizes)
+        h = cil.Batch(sizes, sizes, k=k, iters=a.iters, max_corr_dist=0.1, viewpoint=(0.0, 0.0, 10.0))
+        fn = lambda: h.run(src, dst)  # noqa: E731
+    else:
+        if a.workload == "surface":
+            p, dmax = synth.surface_pair(a.seed, n=10_000), 0.1
+        elif a.workload == "depth":
+            p, dmax = synth.depth_frame_pair(a.seed), 0.05
+        else:
+            p, dmax = synth.lidar_sweep_pair(a.seed), 1.0
+        src = torch.from_numpy(p.source).cuda()
+        dst = torch.from_numpy(p.target).cuda()
+        nrm = torch.empty_like(dst)
+        vp = p.viewpoint
+        fn = {
+            "register": lambda: cil.register_pair(src, dst, k, vp, a.iters, dmax, out_normals=nrm),
+            "knn": lambda: cil.knn(dst, dst, k),
+            "normals": lambda: cil.estimate_normals(dst, k, vp),
+            "radius": lambda: cil.radius_search(dst, dst, a.radius),
+        }[a.op]
+    L = cil.lib()
+    fn()
+    torch.cuda.synchronize()
+    L.cil_timing_reset()
+    L.cil_timing_enable(1)
+    for _ in range(a.repeat):
+        fn()
+    torch.cuda.synchronize()
+    L.cil_timing_enable(0)
+    out = {"workload": a.workload, "op": a.op, "k": k, "iters": a.iters, "repeat": a.repeat}
+    for name in ("grid_build", "order_queries", "k_knn", "k_normals", "k_icp", "k_radius"):
+        t, c = ctypes.c_double(), ctypes.c_int64()
+        L.cil_timing_read(name.encode(), ctypes.byref(t), ctypes.byref(c))
+        if c.value:
+            out[name + "_ms"] = t.value / c.value
+    print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
