@@ -652,7 +652,7 @@ cil_status grid_build(const GridPlan& p, const Workspace& ws, const float* xyz,
   TimedRegion timer("grid_build", s);
   GridParams* prm = ws.at<GridParams>(p.o_prm);
   const int64_t n = p.n;
-  note_launches(n > 0 ? 9 : 2);
+  note_launches(n > 0 ? 8 : 2);  // init, bbox, finalize, keys, gather, level, insert, count
   k_init_params<<<ceil_div(p.clouds, 128), 128, 0, s>>>(prm, p.clouds, cloud_start_dev, n);
   if (n > 0) {
     const int64_t threads = (n + 7) / 8;
