@@ -52,7 +52,7 @@ struct IcpPlan {
 };
 
 constexpr int kIcpThreads = 256;
-constexpr int kIcpPPT = 2;
+constexpr int kIcpPPT = 1;
 constexpr int kIcpQ = 28;  // 21 (H upper) + 6 (g) + 1 (sum r^2)
 constexpr int kIcpGroup = 32;  // tiles reduced together before the round's solve
 
