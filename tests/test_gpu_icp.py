@@ -130,3 +130,55 @@ def test_register_pair_equals_separate_calls(surface):
     T2, r2 = cil.icp_point_to_plane(s, d, n_sep, iters=20, max_corr_dist=0.1)
     assert np.array_equal(T.cpu().numpy().reshape(4, 4), T2)
     assert r == r2
+
+
+def _offset_surface_case(seed: int):
+    """A dense wavy patch (~1.4 mm spacing) and a source resampled from it
+    with per-point offsets along z of 0..2 cm plus points far above it: the
+    source's nearest neighbours are found by every stage of the search (own
+    block, directory cells of the 4x level, ring search for large rejection
+    distances)."""
+    rng = np.random.default_rng(seed)
+
+    def wave(n):
+        xy = rng.uniform(-0.1, 0.1, (n, 2))
+        z = 0.005 * np.sin(40 * xy[:, 0]) * np.cos(40 * xy[:, 1])
+        return np.column_stack([xy, z]) + rng.normal(0, 1e-4, (n, 3))
+
+    tgt = wave(20_000).astype(np.float32)
+    src = wave(6_000)
+    src[:, 2] += rng.uniform(0.0, 0.02, len(src))
+    far = np.column_stack([rng.uniform(-0.15, 0.15, (600, 2)), rng.uniform(0.03, 0.1, 600)])
+    src = np.concatenate([src, far]).astype(np.float32)
+    on, _, _ = oracle.normals(tgt, 10, (0.0, 0.0, 1.0))
+    return src, tgt, on.astype(np.float32)
+
+
+@pytest.mark.parametrize("dmax", [0.005, 0.02, 10.0])
+def test_association_every_search_stage(dmax):
+    src, tgt, nrm = _offset_surface_case(11)
+    # iters = 0: only the final association pass -- its inlier count and RMSE
+    # depend on every correspondence
+    Tg, rg = _gpu_icp(src, tgt, nrm, iters=0, max_corr_dist=dmax)
+    o = oracle.icp(src, tgt, nrm, iters=0, max_corr_dist=dmax)
+    assert abs(rg["n_inliers"] - o["n_inliers"]) <= 2
+    assert abs(rg["rmse"] - o["rmse"]) <= 1e-5 * o["rmse"]
+    # a few rounds from there
+    Tg, rg = _gpu_icp(src, tgt, nrm, iters=4, max_corr_dist=dmax)
+    o = oracle.icp(src, tgt, nrm, iters=4, max_corr_dist=dmax)
+    _assert_same(Tg, o["T"], tgt)
+    assert abs(rg["n_inliers"] - o["n_inliers"]) <= 2
+
+
+def test_association_large_rejection_distance(surface):
+    """A rejection distance of half the cloud: the directory of 4x cells is
+    too large and unresolved queries take the ring search."""
+    p, nrm = surface
+    src = np.concatenate([p.source, p.source[:500] + np.float32([0.0, 0.0, 0.6])])
+    Tg, rg = _gpu_icp(src, p.target, nrm, iters=0, max_corr_dist=1.0)
+    o = oracle.icp(src, p.target, nrm, iters=0, max_corr_dist=1.0)
+    assert rg["n_inliers"] == o["n_inliers"] == len(src)
+    assert abs(rg["rmse"] - o["rmse"]) <= 1e-5 * o["rmse"]
+    Tg, rg = _gpu_icp(src, p.target, nrm, iters=3, max_corr_dist=1.0)
+    o = oracle.icp(src, p.target, nrm, iters=3, max_corr_dist=1.0)
+    _assert_same(Tg, o["T"], p.target)
