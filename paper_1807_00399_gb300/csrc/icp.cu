@@ -416,6 +416,25 @@ __global__ void k_icp_setup(IcpPairState* st, int pairs, const int* src_start, i
   if (threadIdx.x == 0) tile_off[pairs] = carry;
 }
 
+// Operands of sum q of the normal equations in a row (J0..J5, r):
+// q = 0..20 the upper triangle of J J^T row by row, 21..26 J r, 27 r r.
+__device__ __forceinline__ void q_operands(int q, int& ia, int& ib) {
+  if (q >= 21) {
+    ia = q == 27 ? 6 : q - 21;
+    ib = 6;
+    return;
+  }
+  int u = 0, base = 0;
+  while (q >= base + 6 - u) {
+    base += 6 - u;
+    ++u;
+  }
+  ia = u;
+  ib = u + (q - base);
+}
+
+constexpr int kRowChunks = 8;  // chunks of a tile's rows summed in parallel
+
 __device__ __forceinline__ int pair_of_tile(const int* tile_off, int pairs, int tt) {
   int lo = 0, hi = pairs;
   while (hi - lo > 1) {
@@ -432,9 +451,9 @@ __global__ void __launch_bounds__(kIcpThreads, 2) k_icp(IcpArgs a) {
   __shared__ float s_Rt[12];
   __shared__ float s_dmax2;
   __shared__ int s_corr[kTileSrc];
-  __shared__ float sm_s[kIcpWarps][kIcpQ];
-  __shared__ float sm_c[kIcpWarps][kIcpQ];
-  __shared__ int sm_n[kIcpWarps];
+  __shared__ float s_row[7][kTileSrc + 8];  // J (6) and r per tile point; +8 spreads banks
+  __shared__ float s_ps[kIcpQ][kRowChunks], s_pc[kIcpQ][kRowChunks];
+  __shared__ int s_cnt;
   __shared__ double sm_tot[kIcpQ];
   __shared__ long long sm_cnt;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -508,82 +527,66 @@ __global__ void __launch_bounds__(kIcpThreads, 2) k_icp(IcpArgs a) {
       }
       s_corr[pass * kIcpThreads + tid] = bj;
     }
-    // phase 2: residual and Jacobian rows.  Per-thread partials over its
-    // <= kIcpPPT points are plain FP32 (at most 3 roundings each); every
-    // combination across threads below is compensated (error-free TwoSum)
-    float R[12];
-#pragma unroll
-    for (int j = 0; j < 12; ++j) R[j] = s_Rt[j];
-    float part[kIcpQ];
-#pragma unroll
-    for (int q = 0; q < kIcpQ; ++q) part[q] = 0.0f;
+    // phase 2: the residual and Jacobian row of each point of the tile into
+    // shared memory (zeros where there is no correspondence)
+    if (tid == 0) s_cnt = 0;
     int cnt = 0;
 #pragma unroll 1
     for (int pass = 0; pass < kIcpPPT; ++pass) {
-      const int pos = lo + pass * kIcpThreads + tid;
-      const int bj = s_corr[pass * kIcpThreads + tid];
-      if (pos >= hi || bj < 0) continue;
-      const int64_t si = __ldg(a.order + pos);
-      const float x = __ldg(a.src + 3 * si), y = __ldg(a.src + 3 * si + 1),
-                  z = __ldg(a.src + 3 * si + 2);
-      float p[3];
-      p[0] = fmaf(R[0], x, fmaf(R[1], y, fmaf(R[2], z, R[3])));
-      p[1] = fmaf(R[4], x, fmaf(R[5], y, fmaf(R[6], z, R[7])));
-      p[2] = fmaf(R[8], x, fmaf(R[9], y, fmaf(R[10], z, R[11])));
-      const float4 qp = __ldg(a.g.pts + bj);
-      const int64_t j = dst_start + (int64_t)__float_as_int(qp.w);
-      const float nx = __ldg(a.dst_n + 3 * j), ny = __ldg(a.dst_n + 3 * j + 1),
-                  nz = __ldg(a.dst_n + 3 * j + 2);
-      if (!(isfinite(nx) && isfinite(ny) && isfinite(nz))) continue;
-      const float r = nx * (p[0] - qp.x) + ny * (p[1] - qp.y) + nz * (p[2] - qp.z);
-      const float J[6] = {p[1] * nz - p[2] * ny, p[2] * nx - p[0] * nz, p[0] * ny - p[1] * nx,
-                          nx, ny, nz};
-      int q = 0;
-#pragma unroll
-      for (int u = 0; u < 6; ++u)
-#pragma unroll
-        for (int v = u; v < 6; ++v) {
-          part[q] = fmaf(J[u], J[v], part[q]);
-          ++q;
+      const int u = pass * kIcpThreads + tid;
+      const int pos = lo + u;
+      const int bj = s_corr[u];
+      float row[7] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+      if (pos < hi && bj >= 0) {
+        const int64_t si = __ldg(a.order + pos);
+        const float x = __ldg(a.src + 3 * si), y = __ldg(a.src + 3 * si + 1),
+                    z = __ldg(a.src + 3 * si + 2);
+        float p[3];
+        p[0] = fmaf(s_Rt[0], x, fmaf(s_Rt[1], y, fmaf(s_Rt[2], z, s_Rt[3])));
+        p[1] = fmaf(s_Rt[4], x, fmaf(s_Rt[5], y, fmaf(s_Rt[6], z, s_Rt[7])));
+        p[2] = fmaf(s_Rt[8], x, fmaf(s_Rt[9], y, fmaf(s_Rt[10], z, s_Rt[11])));
+        const float4 qp = __ldg(a.g.pts + bj);
+        const int64_t j = dst_start + (int64_t)__float_as_int(qp.w);
+        const float nx = __ldg(a.dst_n + 3 * j), ny = __ldg(a.dst_n + 3 * j + 1),
+                    nz = __ldg(a.dst_n + 3 * j + 2);
+        if (isfinite(nx) && isfinite(ny) && isfinite(nz)) {
+          row[0] = p[1] * nz - p[2] * ny;
+          row[1] = p[2] * nx - p[0] * nz;
+          row[2] = p[0] * ny - p[1] * nx;
+          row[3] = nx;
+          row[4] = ny;
+          row[5] = nz;
+          row[6] = nx * (p[0] - qp.x) + ny * (p[1] - qp.y) + nz * (p[2] - qp.z);
+          ++cnt;
         }
+      }
 #pragma unroll
-      for (int u = 0; u < 6; ++u) part[21 + u] = fmaf(J[u], r, part[21 + u]);
-      part[27] = fmaf(r, r, part[27]);
-      ++cnt;
+      for (int k = 0; k < 7; ++k) s_row[k][u] = row[k];
     }
-    // block reduction of the tile (fixed shuffle tree, then warps in order),
-    // compensated: each merge is an error-free TwoSum of the partial sums;
-    // one quantity at a time keeps the live registers low
-#pragma unroll
-    for (int q = 0; q < kIcpQ; ++q) {
+    __syncthreads();
+    if (cnt) atomicAdd(&s_cnt, cnt);
+    // the tile's 21 + 6 + 1 sums: item (q, ch) adds the products of rows
+    // ch, ch + kRowChunks, ... in that order (compensated), then the chunks
+    // are merged in order -- a fixed order, so the result is deterministic
+    for (int w = tid; w < kIcpQ * kRowChunks; w += kIcpThreads) {
+      const int q = w / kRowChunks, ch = w - q * kRowChunks;
+      int ia, ib;
+      q_operands(q, ia, ib);
       KSum t;
-      t.s = part[q];
-      t.c = 0.0f;
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float s2 = __shfl_down_sync(0xffffffffu, t.s, off);
-        const float c2 = __shfl_down_sync(0xffffffffu, t.c, off);
-        t.merge(s2, c2);
-      }
-      if (lane == 0) {
-        sm_s[warp][q] = t.s;
-        sm_c[warp][q] = t.c;
-      }
+      t.zero();
+      for (int i = ch; i < kTileSrc; i += kRowChunks) t.add(__fmul_rn(s_row[ia][i], s_row[ib][i]));
+      s_ps[q][ch] = t.s;
+      s_pc[q][ch] = t.c;
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, off);
-    if (lane == 0) sm_n[warp] = cnt;
     __syncthreads();
     if (tid < kIcpQ) {
       KSum t;
       t.zero();
-      for (int w = 0; w < kIcpWarps; ++w) t.merge(sm_s[w][tid], sm_c[w][tid]);
+      for (int ch = 0; ch < kRowChunks; ++ch) t.merge(s_ps[tid][ch], s_pc[tid][ch]);
       a.part_s[(int64_t)tt * kIcpQ + tid] = t.s;
       a.part_c[(int64_t)tt * kIcpQ + tid] = t.c;
     } else if (tid == 32) {
-      int n = 0;
-      for (int w = 0; w < kIcpWarps; ++w) n += sm_n[w];
-      a.part_n[tt] = n;
+      a.part_n[tt] = s_cnt;
     }
     __threadfence();
     __syncthreads();
