@@ -279,22 +279,26 @@ struct TopK {
     for (int j = 0; j < KMAX; ++j) v[j] = kEmptyKey;
     thr = kEmptyKey;
   }
-  // branch-free insertion (selects, no predicated stores) so the array stays
-  // in registers; slots j >= k never change
+  // branch-free insertion into the ascending list (selects, no predicated
+  // stores, so the array stays in registers).  The whole KMAX-slot list stays
+  // sorted, so its first k slots are the k smallest keys seen; thr = v[k-1].
   __device__ __forceinline__ void push(u64 key) {
     if (key < thr) {
 #pragma unroll
       for (int j = KMAX - 1; j > 0; --j) {
         const u64 prev = v[j - 1];
         const u64 cur = v[j];
-        const u64 nv = (key < prev) ? prev : ((key < cur) ? key : cur);
-        v[j] = (j < k) ? nv : cur;
+        v[j] = (key < prev) ? prev : ((key < cur) ? key : cur);
       }
       v[0] = (key < v[0]) ? key : v[0];
-      u64 t = v[0];
+      if (k == KMAX) {
+        thr = v[KMAX - 1];
+      } else {
+        u64 t = v[0];
 #pragma unroll
-      for (int j = 1; j < KMAX; ++j) t = (j < k) ? v[j] : t;
-      thr = t;
+        for (int j = 1; j < KMAX; ++j) t = (j < k) ? v[j] : t;
+        thr = t;
+      }
     }
   }
   __device__ __forceinline__ bool full() const { return thr != kEmptyKey; }
