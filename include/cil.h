@@ -242,8 +242,8 @@ cil_status cil_register_pair(const float *src, int64_t n_src, const float *dst, 
  * in the paper, which registers one pair at a time, Sec. 4).  Per pair: the
  * same target grid + k-NN normals + point-to-plane ICP as cil_register_pair,
  * all pairs in one CUDA graph launch: one grid build over the concatenated
- * targets (one cell level per pair), one normals kernel, one persistent ICP
- * kernel whose per-pair rounds are scheduled independently.
+ * targets (one cell level per pair), one normals kernel, and per ICP round
+ * three kernels over all pairs' source tiles.
  *   cil_icp_batch_create  n_src, n_dst: host int64[B] point counts; allocates
  *                         the handle's device workspace (synchronous)
  *   cil_icp_batch_run     src_cat [sum n_src][3], dst_cat [sum n_dst][3]:

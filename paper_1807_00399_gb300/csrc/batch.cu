@@ -4,8 +4,8 @@
 // enqueues, for all B pairs at once:
 //   grid build over the concatenated targets (cloud id above the Morton bits,
 //   one search level per cloud), k-NN PCA normals of every target point, and
-//   the persistent ICP kernel over every pair (per-pair rounds scheduled as a
-//   dataflow, see icp.cu) with the final RMSE pass.
+//   the ICP rounds of every pair (three launches per round over all pairs'
+//   tiles, see icp.cu) with the final RMSE pass.
 // The sequence is captured once per set of buffer pointers into a CUDA graph
 // and replayed with a single cudaGraphLaunch on the caller's stream.
 #include <stdlib.h>

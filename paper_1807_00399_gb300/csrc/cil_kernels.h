@@ -35,7 +35,6 @@ struct IcpPairState {
   int grp_begin;    // first tile group of the pair (groups of kIcpGroup tiles)
   int n_grp;        // tile groups of the pair
   int tiles_done;   // tile groups of the current round reduced
-  int iter_done;    // rounds published (the next round may start)
   int status;       // CIL_OK or CIL_ERR_DEGENERATE
   int iters;        // rounds requested
 };
@@ -46,13 +45,13 @@ struct IcpPlan {
   int n_tiles = 0;
   int tile = 0;     // source points per tile
   int n_groups = 0;  // tile groups over all pairs
-  size_t o_state, o_order, o_tile_off, o_rt, o_part_s, o_part_c, o_part_n, o_work;
+  size_t o_state, o_order, o_tile_off, o_rt, o_part_s, o_part_c, o_part_n;
   size_t o_grp_s, o_grp_c, o_grp_n, o_grp_done;
+  size_t o_corr, o_queue, o_qc;
   OrderPlan order;
 };
 
-constexpr int kIcpThreads = 256;
-constexpr int kIcpPPT = 1;
+constexpr int kIcpThreads = 256;  // source points per tile (one per thread)
 constexpr int kIcpQ = 28;  // 21 (H upper) + 6 (g) + 1 (sum r^2)
 constexpr int kIcpGroup = 32;  // tiles reduced together before the round's solve
 
@@ -61,8 +60,8 @@ void icp_plan(IcpPlan& p, Workspace& ws, const int64_t* src_counts, int pairs);
 
 // Enqueue: order the sources, initialise per-pair state from T_init (device
 // double[16 * pairs], or host double[16] for one pair, or both null =
-// identity) and run all rounds plus the final RMSE pass in one persistent
-// launch.  `src_start_dev`: device int[pairs+1] (null for one pair).
+// identity) and run all rounds plus the final RMSE pass (three launches per
+// round).  `src_start_dev`: device int[pairs+1] (null for one pair).
 cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt,
                    const float* src, const int* src_start_dev, const float* dst_normals,
                    const double* T_init_dev, const double* T_init_host, int iters,

@@ -1,23 +1,26 @@
 // icp.cu -- rigid point-to-plane ICP (Sec. 2 ICP loop; Sec. 3 point-to-plane
 // estimator after Low 2004; Sec. 4 fixed rounds and a rejection distance).
 //
-// One persistent launch runs every round of every pair.  Work items are tiles
-// of kIcpThreads * kIcpPPT source points, numbered round-major; blocks grab
-// them from an atomic counter.  A tile of round r of pair b first waits until
-// pair b has published round r - 1 (a bounded spin), then:
-//   p' = R p + t  (FP32),  q = exact nearest target point of p' within the
-//   rejection distance, n = normal of q, r = n.(p' - q), J = [p' x n, n],
-// and accumulates H = sum J J^T (21 terms), g = sum J r (6), sum r^2 with
-// compensated FP32 sums; the block writes the tile's partial sums.  Tiles
-// form groups of kIcpGroup: the block that completes a group's last tile
-// reduces the group in a fixed order, and the block that completes a pair's
-// last group reduces the group partials in order (deterministic), solves
-// H xi = -g in FP64 by Cholesky, left-composes T <- [exp(w^), tau; 0 1] T in
-// FP64 and publishes the round.  The extra last round only evaluates the
-// final RMSE.
-// A round only depends on earlier tiles, which running blocks hold, so the
-// schedule cannot deadlock; every wait still has an iteration limit and
-// reports CIL_ERR_TIMEOUT instead of hanging.
+// Every round of every pair runs as three launches over tiles of kIcpThreads
+// source points (all pairs' tiles together in batched mode):
+//   k_icp_search      p' = R p + t (FP32) and the first stage of the exact
+//                     nearest-neighbour search within the rejection distance
+//                     (the query's cell, then the cells of its 3x3x3 block
+//                     meeting the ball of the best distance so far); queries
+//                     whose ball leaves the block go to a queue;
+//   k_icp_finish      each queued query is finished by one whole warp: the
+//                     cells of the directory level meeting its ball are looked
+//                     up by the lanes in parallel and their points scanned
+//                     with the lanes splitting them;
+//   k_icp_accumulate  for each correspondence n = normal of q, r = n.(p' - q),
+//                     J = [p' x n, n]; the tile's sums H = sum J J^T (21),
+//                     g = sum J r (6), sum r^2 in a fixed compensated order;
+//                     tiles form groups of kIcpGroup whose last block reduces
+//                     the group, and the block finishing a pair's last group
+//                     reduces the group partials in order, solves H xi = -g in
+//                     FP64 (Cholesky) and left-composes T <- [exp(w^), tau; 0 1] T.
+// The extra last round only evaluates the final RMSE.  No kernel waits on
+// another: rounds are ordered by the stream, so nothing can hang.
 #include <math.h>
 
 #include "cil_host.h"
@@ -25,18 +28,8 @@
 
 namespace cil {
 
-constexpr int kTileSrc = kIcpThreads * kIcpPPT;
+constexpr int kTileSrc = kIcpThreads;
 constexpr int kIcpWarps = kIcpThreads / 32;
-constexpr long long kSpinLimit = 1ll << 22;
-
-__device__ __forceinline__ int ld_acquire_i32(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_i32(int* p, int v) {
-  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 struct IcpArgs {
   GridView g;
@@ -50,6 +43,10 @@ struct IcpArgs {
   int n_tiles;
   int rounds;           // iterations + 1
   IcpPairState* st;
+  int* corr;            // per sorted source position: sorted target position or -1
+  int2* queue;          // (sorted source position, pair) of queries for k_icp_finish
+  unsigned* qcount;     // [2] queue length of the rounds of each parity
+  unsigned* qhead;      // [2] queue items taken
   float* part_s;
   float* part_c;
   int* part_n;
@@ -57,15 +54,12 @@ struct IcpArgs {
   float* grp_c;
   int* grp_n;
   int* grp_done;
-  unsigned* work;
-  int* abort;
-  int* err;
 };
 
 constexpr int kDirLevels = 2;     // directory level = base level + 2 (in the cell table)
 constexpr int kDirCells = 125;    // directory cells meeting the ball at most
-constexpr int kDirectScan = 128;  // coarse cells up to this many points are scanned whole
-constexpr int kLookupCost = 4;
+constexpr int kDirectScan = 128;  // directory cells up to this many points are scanned whole
+constexpr int kLookupCost = 4;    // a base-level lookup costs about this many point tests
 
 // Points of one cell that improve on (best, lim); lim = min(dmax2, best d^2).
 __device__ __forceinline__ void scan_cell(const GridView& g, int s, int n, const float q[3],
@@ -81,16 +75,87 @@ __device__ __forceinline__ void scan_cell(const GridView& g, int s, int n, const
   });
 }
 
-// The ball of radius sqrt(lim) around q leaves the 3x3x3 block around the
-// base-level cell c (already searched).  The cells of the directory level
-// (4x the base edge, hashed in the table for this) meeting the ball act as a
-// directory: empty ones are skipped whole, small ones scanned,
-// and in large ones that the ball meets in few base-level cells only those
-// cells are looked up (dense surfaces seen from off the surface stay cheap).
-// Returns false, having searched nothing, when the ball spans more than
-// kDirCells coarse cells (large rejection distances), and true once every
-// cell meeting the ball has been searched.
-__device__ __forceinline__ bool escalate_directory(const GridView& g, int cloud, const float q[3],
+// Ring search from the first coarser level upward (kRingCap rings per level)
+// for balls too large for the directory search.
+__device__ __forceinline__ void escalate_rings(const GridView& g, int cloud, const float q[3],
+                                            float dmax2, u64& best, int& bj, float& lim) {
+  const GridParams& P = g.prm[cloud];
+  const float inv_fine = P.inv_fine;
+  for (int lvl = next_level(P.level);; lvl = next_level(lvl)) {
+    CellFrame f;
+    f.load_level(P, cloud, lvl, ldexpf(P.fine, lvl));
+    const int cx = f.cell_of(q[0], 0, inv_fine);
+    const int cy = f.cell_of(q[1], 1, inv_fine);
+    const int cz = f.cell_of(q[2], 2, inv_fine);
+    const int rmax = max(max(max(cx, f.hi[0] - cx), max(cy, f.hi[1] - cy)), max(cz, f.hi[2] - cz));
+    const int rcap = lvl >= kFineBits ? rmax : min(rmax, kRingCap);
+    for (int r = 0; r <= rcap; ++r) {
+      if (r > 0) {
+        const int e0[3] = {cx - r + 1, cy - r + 1, cz - r + 1};
+        const int e1[3] = {cx + r - 1, cy + r - 1, cz + r - 1};
+        if (f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim) return;
+      }
+      CIL_SHELL_FOR(f, cx, cy, cz, r, x, y, z) {
+        const int c3[3] = {x, y, z};
+        if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > lim) continue;
+        int s, n;
+        if (cell_lookup(g, cell_key(lvl, cloud, x, y, z), s, n))
+          scan_cell(g, s, n, q, dmax2, best, bj, lim);
+      }
+    }
+    if (rcap == rmax) return;  // every ring of this level searched
+    const int e0[3] = {cx - rcap, cy - rcap, cz - rcap};
+    const int e1[3] = {cx + rcap, cy + rcap, cz + rcap};
+    if (f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim) return;
+  }
+}
+
+// First stage of the correspondence search of one query (per thread).  At
+// the cloud's own level the query's cell is scanned first, then only the
+// cells of its 3x3x3 block that meet the ball of the best distance so far (a
+// converged source point finds its neighbour there).  Returns true when that
+// is exact (the ball stays inside the block).  best / bj / lim: packed key,
+// sorted position (-1: none) and min(dmax2, best d^2) of the best point.
+__device__ __forceinline__ bool base_search(const GridView& g, int cloud, const float q[3],
+                                            float dmax2, u64& best, int& bj, float& lim) {
+  const GridParams& P = g.prm[cloud];
+  const float inv_fine = P.inv_fine;
+  best = kEmptyKey;
+  bj = -1;
+  lim = dmax2;
+  CellFrame f;
+  f.load(P, cloud);
+  const int c[3] = {f.cell_of(q[0], 0, inv_fine), f.cell_of(q[1], 1, inv_fine),
+                    f.cell_of(q[2], 2, inv_fine)};
+  int s, n;
+  if (cell_lookup(g, cell_key(f.level, cloud, c[0], c[1], c[2]), s, n))
+    scan_cell(g, s, n, q, dmax2, best, bj, lim);
+  if (f.level >= kFineBits) return true;  // one cell holds the whole cloud
+  // cells of the block meeting the ball of radius sqrt(lim) (padded)
+  const float rad = fmaf(sqrtf(lim), 1.0f + 1e-6f, f.eps);
+  int lo[3], hi[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = max(f.cell_of(q[a] - rad, a, inv_fine), c[a] - 1);
+    hi[a] = min(f.cell_of(q[a] + rad, a, inv_fine), c[a] + 1);
+  }
+  for (int z = lo[2]; z <= hi[2]; ++z)
+    for (int y = lo[1]; y <= hi[1]; ++y)
+      for (int x = lo[0]; x <= hi[0]; ++x) {
+        if (x == c[0] && y == c[1] && z == c[2]) continue;
+        const int c3[3] = {x, y, z};
+        if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > lim) continue;
+        if (cell_lookup(g, cell_key(f.level, cloud, x, y, z), s, n))
+          scan_cell(g, s, n, q, dmax2, best, bj, lim);
+      }
+  const int e0[3] = {c[0] - 1, c[1] - 1, c[2] - 1};
+  const int e1[3] = {c[0] + 1, c[1] + 1, c[2] + 1};
+  return f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim;
+}
+
+// The per-lane form of warp_directory (same cells, same result), for queues
+// long enough to give every lane its own query.
+__device__ __forceinline__ bool lane_directory(const GridView& g, int cloud, const float q[3],
                                                 float dmax2, const int c[3], u64& best, int& bj,
                                                 float& lim) {
   const GridParams& P = g.prm[cloud];
@@ -143,91 +208,153 @@ __device__ __forceinline__ bool escalate_directory(const GridView& g, int cloud,
   return false;
 }
 
-// Ring search from the first coarser level upward (kRingCap rings per level)
-// for balls too large for the directory search.
-__device__ __forceinline__ void escalate_rings(const GridView& g, int cloud, const float q[3],
-                                            float dmax2, u64& best, int& bj, float& lim) {
-  const GridParams& P = g.prm[cloud];
-  const float inv_fine = P.inv_fine;
-  for (int lvl = next_level(P.level);; lvl = next_level(lvl)) {
-    CellFrame f;
-    f.load_level(P, cloud, lvl, ldexpf(P.fine, lvl));
-    const int cx = f.cell_of(q[0], 0, inv_fine);
-    const int cy = f.cell_of(q[1], 1, inv_fine);
-    const int cz = f.cell_of(q[2], 2, inv_fine);
-    const int rmax = max(max(max(cx, f.hi[0] - cx), max(cy, f.hi[1] - cy)), max(cz, f.hi[2] - cz));
-    const int rcap = lvl >= kFineBits ? rmax : min(rmax, kRingCap);
-    for (int r = 0; r <= rcap; ++r) {
-      if (r > 0) {
-        const int e0[3] = {cx - r + 1, cy - r + 1, cz - r + 1};
-        const int e1[3] = {cx + r - 1, cy + r - 1, cz + r - 1};
-        if (f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim) return;
-      }
-      CIL_SHELL_FOR(f, cx, cy, cz, r, x, y, z) {
-        const int c3[3] = {x, y, z};
-        if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > lim) continue;
-        int s, n;
-        if (cell_lookup(g, cell_key(lvl, cloud, x, y, z), s, n))
-          scan_cell(g, s, n, q, dmax2, best, bj, lim);
-      }
-    }
-    if (rcap == rmax) return;  // every ring of this level searched
-    const int e0[3] = {cx - rcap, cy - rcap, cz - rcap};
-    const int e1[3] = {cx + rcap, cy + rcap, cz + rcap};
-    if (f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim) return;
+// Warp-wide minimum of the lanes' (key, position) candidates merged into the
+// warp-uniform (best, bj, lim).
+__device__ __forceinline__ void warp_merge(u64 mine, int mj, u64& best, int& bj, float& lim) {
+  u64 w = mine;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const u64 o = ((u64)__shfl_xor_sync(0xffffffffu, (unsigned)(w >> 32), off) << 32) |
+                  __shfl_xor_sync(0xffffffffu, (unsigned)w, off);
+    w = o < w ? o : w;
+  }
+  if (w < best) {
+    const unsigned who = __ballot_sync(0xffffffffu, mine == w);
+    bj = __shfl_sync(0xffffffffu, mj, __ffs(who) - 1);
+    best = w;
+    lim = fminf(lim, key_d2(w));
   }
 }
 
-// Nearest target point within dmax2 (sorted position in bj, key returned, or
-// kEmptyKey).  At the cloud's own level the query's cell is scanned first;
-// then only the cells of its 3x3x3 block that meet the ball of the best
-// distance so far (a converged source point finds its neighbour there).  A
-// query whose ball leaves the block -- an outlier or a point still far from
-// the surface -- continues with a ring search at the 8x coarser levels, where
-// the rejection distance bounds the rings.  Exact: a level's search ends only
-// once the unexplored region lies beyond min(best, dmax).
-__device__ __forceinline__ u64 nearest_within(const GridView& g, int cloud, const float q[3],
-                                              float dmax2, int& bj) {
+// Second stage for one query whose ball of radius sqrt(lim) leaves the 3x3x3
+// block around its base-level cell c, done by the whole warp (all arguments
+// warp-uniform; best / bj / lim hold the first stage's result and receive
+// the final one).  The cells of the directory level (4x the base edge,
+// hashed in the table for this) that meet the ball are looked up by the lanes
+// in parallel.  Empty ones are skipped whole.  Cells of at most kDirectScan
+// points, or with few points per base cell that the ball meets, are scanned
+// whole, their points concatenated and split over the lanes.  In the other
+// (large) ones only the base-level cells meeting the ball are looked up, one
+// per lane.  Returns false, having searched nothing, when the ball spans
+// more than kDirCells directory cells.  Exact: every cell meeting the ball
+// is searched (the stage's result is the minimum over a superset of the
+// ball's points).
+__device__ bool warp_directory(const GridView& g, int cloud, const float q[3], float dmax2,
+                               const int c[3], u64& best, int& bj, float& lim, int lane,
+                               int* sh_start, int* sh_incl) {
+  const unsigned FULL = 0xffffffffu;
   const GridParams& P = g.prm[cloud];
   const float inv_fine = P.inv_fine;
-  u64 best = kEmptyKey;
-  float lim = dmax2;
-  bj = -1;
-  {
-    CellFrame f;
-    f.load(P, cloud);
-    const int c[3] = {f.cell_of(q[0], 0, inv_fine), f.cell_of(q[1], 1, inv_fine),
-                      f.cell_of(q[2], 2, inv_fine)};
-    int s, n;
-    if (cell_lookup(g, cell_key(f.level, cloud, c[0], c[1], c[2]), s, n))
-      scan_cell(g, s, n, q, dmax2, best, bj, lim);
-    if (f.level >= kFineBits) return best;  // one cell holds the whole cloud
-    // cells of the block meeting the ball of radius sqrt(lim) (padded)
-    const float rad = fmaf(sqrtf(lim), 1.0f + 1e-6f, f.eps);
-    int lo[3], hi[3];
+  CellFrame f;
+  f.load(P, cloud);
+  const int Lc = min(f.level + kDirLevels, kFineBits);
+  CellFrame fc;
+  fc.load_level(P, cloud, Lc, ldexpf(P.fine, Lc));
+  const float rad = fmaf(sqrtf(lim), 1.0f + 1e-6f, f.eps);
+  int clo[3], chi[3], blo[3], bhi[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      lo[a] = max(f.cell_of(q[a] - rad, a, inv_fine), c[a] - 1);
-      hi[a] = min(f.cell_of(q[a] + rad, a, inv_fine), c[a] + 1);
-    }
-    for (int z = lo[2]; z <= hi[2]; ++z)
-      for (int y = lo[1]; y <= hi[1]; ++y)
-        for (int x = lo[0]; x <= hi[0]; ++x) {
-          if (x == c[0] && y == c[1] && z == c[2]) continue;
-          const int c3[3] = {x, y, z};
-          if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > lim) continue;
-          if (cell_lookup(g, cell_key(f.level, cloud, x, y, z), s, n))
-            scan_cell(g, s, n, q, dmax2, best, bj, lim);
-        }
-    const int e0[3] = {c[0] - 1, c[1] - 1, c[2] - 1};
-    const int e1[3] = {c[0] + 1, c[1] + 1, c[2] + 1};
-    if (f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim) return best;
-
-    if (escalate_directory(g, cloud, q, dmax2, c, best, bj, lim)) return best;
+  for (int a = 0; a < 3; ++a) {
+    clo[a] = fc.cell_of(q[a] - rad, a, inv_fine);
+    chi[a] = fc.cell_of(q[a] + rad, a, inv_fine);
+    blo[a] = f.cell_of(q[a] - rad, a, inv_fine);
+    bhi[a] = f.cell_of(q[a] + rad, a, inv_fine);
   }
-  // a ball spanning many coarse cells (large rejection distance)
-  escalate_rings(g, cloud, q, dmax2, best, bj, lim);
-  return best;
+  const int dx = chi[0] - clo[0] + 1, dy = chi[1] - clo[1] + 1, dz = chi[2] - clo[2] + 1;
+  const int ncell = dx * dy * dz;
+  if (ncell > kDirCells) return false;
+  const int sh = Lc - f.level;
+  for (int base = 0; base < ncell; base += 32) {
+    const int t = base + lane;
+    int X = 0, Y = 0, Z = 0, s = 0, n = 0;
+    bool direct = false, large = false;
+    if (t < ncell) {
+      X = clo[0] + t % dx;
+      Y = clo[1] + (t / dx) % dy;
+      Z = clo[2] + t / (dx * dy);
+      const int C3[3] = {X, Y, Z};
+      if (fc.range_d2(q, C3, C3) * (1.0f - 1e-6f) <= lim &&
+          cell_lookup(g, cell_key(Lc, cloud, X, Y, Z), s, n) && n > 0) {
+        const int nb = (min(((X + 1) << sh) - 1, bhi[0]) - max(X << sh, blo[0]) + 1) *
+                       (min(((Y + 1) << sh) - 1, bhi[1]) - max(Y << sh, blo[1]) + 1) *
+                       (min(((Z + 1) << sh) - 1, bhi[2]) - max(Z << sh, blo[2]) + 1);
+        direct = n <= kDirectScan || n < kLookupCost * nb;
+        large = !direct;
+      }
+    }
+    // directly scanned cells: their points concatenated in lane order, split
+    // over the lanes
+    const int cnt = direct ? n : 0;
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(FULL, incl, off);
+      if (lane >= off) incl += v;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    sh_start[lane] = s - (incl - cnt);  // point u of the run maps to sh_start[owner] + u
+    sh_incl[lane] = incl;
+    __syncwarp();
+    u64 mine = kEmptyKey;
+    int mj = -1;
+    for (int u0 = 0; u0 < total; u0 += 64) {
+      int j2[2];
+      float4 p2[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int u = u0 + 32 * h + lane;
+        j2[h] = -1;
+        if (u < total) {
+          int lo = 0, hi = 31;  // first lane whose inclusive count exceeds u
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (sh_incl[mid] > u) hi = mid;
+            else lo = mid + 1;
+          }
+          j2[h] = sh_start[lo] + u;
+          p2[h] = __ldg(g.pts + j2[h]);
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (j2[h] < 0) continue;
+        const float d2 = sqdist(p2[h].x, p2[h].y, p2[h].z, q[0], q[1], q[2]);
+        const u64 key = pack_key(d2, __float_as_int(p2[h].w));
+        if (d2 <= dmax2 && key < mine) {
+          mine = key;
+          mj = j2[h];
+        }
+      }
+    }
+    __syncwarp();
+    warp_merge(mine, mj, best, bj, lim);
+    // large cells, one after another: their base-level cells meeting the
+    // ball, one per lane (the query's own block was searched in stage one)
+    unsigned m = __ballot_sync(FULL, large);
+    while (m) {
+      const int src = __ffs(m) - 1;
+      m &= m - 1;
+      const int CX = __shfl_sync(FULL, X, src), CY = __shfl_sync(FULL, Y, src),
+                CZ = __shfl_sync(FULL, Z, src);
+      const int xl = max(CX << sh, blo[0]), xh = min(((CX + 1) << sh) - 1, bhi[0]);
+      const int yl = max(CY << sh, blo[1]), yh = min(((CY + 1) << sh) - 1, bhi[1]);
+      const int zl = max(CZ << sh, blo[2]), zh = min(((CZ + 1) << sh) - 1, bhi[2]);
+      const int nx = xh - xl + 1, ny = yh - yl + 1, nz = zh - zl + 1;
+      u64 mb = kEmptyKey;
+      int mbj = -1;
+      float mlim = lim;
+      for (int u = lane; u < nx * ny * nz; u += 32) {
+        const int x = xl + u % nx, y = yl + (u / nx) % ny, z = zl + u / (nx * ny);
+        if (abs(x - c[0]) <= 1 && abs(y - c[1]) <= 1 && abs(z - c[2]) <= 1) continue;
+        const int c3[3] = {x, y, z};
+        if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > mlim) continue;
+        int s2, n2;
+        if (cell_lookup(g, cell_key(f.level, cloud, x, y, z), s2, n2))
+          scan_cell(g, s2, n2, q, dmax2, mb, mbj, mlim);
+      }
+      warp_merge(mb, mbj, best, bj, lim);
+    }
+  }
+  return true;
 }
 
 // FP64 runs at 1/64 of the FP32 rate on this part, so the two solvers below
@@ -403,13 +530,8 @@ __global__ void k_icp_setup(IcpPairState* st, int pairs, const int* src_start, i
       S.iters = iters;
       S.rmse = __longlong_as_double(0x7ff8000000000000ll);
       S.n_inl = 0;
-      if (nt == 0) {  // no source points: nothing to estimate
-        S.status = iters > 0 ? (int)CIL_ERR_DEGENERATE : (int)CIL_OK;
-        S.iter_done = iters + 1;
-      } else {
-        S.status = CIL_OK;
-        S.iter_done = 0;
-      }
+      // no source points: nothing to estimate (the pair has no tiles)
+      S.status = (nt == 0 && iters > 0) ? (int)CIL_ERR_DEGENERATE : (int)CIL_OK;
     }
     __syncthreads();
   }
@@ -445,241 +567,313 @@ __device__ __forceinline__ int pair_of_tile(const int* tile_off, int pairs, int 
   return lo;
 }
 
-__global__ void __launch_bounds__(kIcpThreads, 2) k_icp(IcpArgs a) {
-  __shared__ unsigned s_t;
-  __shared__ int s_go, s_last, s_pair, s_gid, s_g0, s_gsize;
+
+__device__ __forceinline__ int pair_of(const int* off, int pairs, int v) {
+  int lo = 0, hi = pairs;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= v) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// p' = R p + t of the source point at sorted position pos (FP32; the same
+// operations in every kernel, so every kernel sees the same p')
+__device__ __forceinline__ void transformed_source(const IcpArgs& a, const float* Rt, int pos,
+                                                   float p[3]) {
+  const int64_t si = __ldg(a.order + pos);
+  const float x = __ldg(a.src + 3 * si), y = __ldg(a.src + 3 * si + 1),
+              z = __ldg(a.src + 3 * si + 2);
+  p[0] = fmaf(Rt[0], x, fmaf(Rt[1], y, fmaf(Rt[2], z, Rt[3])));
+  p[1] = fmaf(Rt[4], x, fmaf(Rt[5], y, fmaf(Rt[6], z, Rt[7])));
+  p[2] = fmaf(Rt[8], x, fmaf(Rt[9], y, fmaf(Rt[10], z, Rt[11])));
+}
+
+// Stage one of round `round` for the tile blockIdx.x.
+__global__ void __launch_bounds__(kIcpThreads) k_icp_search(IcpArgs a, int round) {
   __shared__ float s_Rt[12];
   __shared__ float s_dmax2;
-  __shared__ int s_corr[kTileSrc];
+  __shared__ int s_pair;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int tt = blockIdx.x;
+  if (tid == 0) {
+    const int b = pair_of(a.tile_off, a.pairs, tt);
+    s_pair = b;
+    s_dmax2 = a.st[b].dmax2;
+  }
+  if (tid < 12) s_Rt[tid] = a.st[pair_of(a.tile_off, a.pairs, tt)].Rt[tid];
+  __syncthreads();
+  const int b = s_pair;
+  const int tb = __ldg(a.tile_off + b);
+  const int sb = a.src_start ? __ldg(a.src_start + b) : 0;
+  const int se = a.src_start ? __ldg(a.src_start + b + 1) : a.n_src1;
+  const int pos = sb + (tt - tb) * kTileSrc + tid;
+  bool queued = false;
+  if (pos < se) {
+    float p[3];
+    transformed_source(a, s_Rt, pos, p);
+    u64 best;
+    int bj;
+    float lim;
+    queued = !base_search(a.g, b, p, s_dmax2, best, bj, lim);
+    a.corr[pos] = bj;  // final, or stage one's best for k_icp_finish
+  }
+  // warp-aggregated append to the queue
+  const unsigned m = __ballot_sync(0xffffffffu, queued);
+  if (m) {
+    unsigned base = 0;
+    if (lane == __ffs(m) - 1) base = atomicAdd(a.qcount + (round & 1), (unsigned)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+    if (queued) a.queue[base + __popc(m & ((1u << lane) - 1u))] = make_int2(pos, b);
+  }
+}
+
+// Stage one's result for the queued query at sorted source position pos of
+// pair b: p', the best point so far and the query's base-level cell.
+__device__ __forceinline__ void queued_query(const IcpArgs& a, int pos, int b, float q[3],
+                                             float& dmax2, u64& best, int& bj, float& lim,
+                                             int c[3]) {
+  float Rt[12];
+#pragma unroll
+  for (int j = 0; j < 12; ++j) Rt[j] = a.st[b].Rt[j];
+  dmax2 = a.st[b].dmax2;
+  transformed_source(a, Rt, pos, q);
+  bj = a.corr[pos];
+  best = kEmptyKey;
+  lim = dmax2;
+  if (bj >= 0) {
+    const float4 qp = __ldg(a.g.pts + bj);
+    lim = sqdist(qp.x, qp.y, qp.z, q[0], q[1], q[2]);
+    best = pack_key(lim, __float_as_int(qp.w));
+  }
+  const GridParams& P = a.g.prm[b];
+  CellFrame f;
+  f.load(P, b);
+  c[0] = f.cell_of(q[0], 0, P.inv_fine);
+  c[1] = f.cell_of(q[1], 1, P.inv_fine);
+  c[2] = f.cell_of(q[2], 2, P.inv_fine);
+}
+
+// Stage two of round `round`.  A short queue (converged rounds: outliers
+// and points far from the surface) is worked by whole warps, one query at a
+// time, which minimises the time until the last query is done.  A queue with
+// more than kLaneQueue queries per warp (the first rounds, large batches)
+// gives each lane its own query, which maximises throughput.
+constexpr int kLaneQueue = 16;
+__global__ void __launch_bounds__(kIcpThreads) k_icp_finish(IcpArgs a, int round) {
+  __shared__ int sh_start[kIcpWarps][32], sh_incl[kIcpWarps][32];
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned total = a.qcount[round & 1];
+  unsigned* head = a.qhead + (round & 1);
+  if (total > (unsigned)kLaneQueue * gridDim.x * kIcpWarps) {
+    for (;;) {
+      unsigned base = 0;
+      if (lane == 0) base = atomicAdd(head, 32u);
+      base = __shfl_sync(FULL, base, 0);
+      if (base >= total) break;
+      const unsigned item = base + lane;
+      if (item < total) {
+        const int2 e = a.queue[item];
+        float q[3], dmax2, lim;
+        u64 best;
+        int bj, c[3];
+        queued_query(a, e.x, e.y, q, dmax2, best, bj, lim, c);
+        if (!lane_directory(a.g, e.y, q, dmax2, c, best, bj, lim))
+          escalate_rings(a.g, e.y, q, dmax2, best, bj, lim);
+        a.corr[e.x] = bj;
+      }
+    }
+    return;
+  }
+  for (;;) {
+    unsigned item = 0;
+    if (lane == 0) item = atomicAdd(head, 1u);
+    item = __shfl_sync(FULL, item, 0);
+    if (item >= total) break;
+    const int2 e = a.queue[item];
+    float q[3], dmax2, lim;
+    u64 best;
+    int bj, c[3];
+    queued_query(a, e.x, e.y, q, dmax2, best, bj, lim, c);
+    if (!warp_directory(a.g, e.y, q, dmax2, c, best, bj, lim, lane, sh_start[warp],
+                        sh_incl[warp])) {
+      // a ball spanning many directory cells (large rejection distance)
+      if (lane == 0) escalate_rings(a.g, e.y, q, dmax2, best, bj, lim);
+    }
+    if (lane == 0) a.corr[e.x] = bj;
+    __syncwarp();
+  }
+}
+
+// Stage three of round `round` for the tile blockIdx.x: rows, tile sums,
+// group reduction and, in the last block of a pair, the round's solve.
+__global__ void __launch_bounds__(kIcpThreads) k_icp_accumulate(IcpArgs a, int round) {
+  __shared__ float s_Rt[12];
+  __shared__ int s_pair, s_last, s_gid, s_g0, s_gsize, s_cnt;
   __shared__ float s_row[7][kTileSrc + 8];  // J (6) and r per tile point; +8 spreads banks
   __shared__ float s_ps[kIcpQ][kRowChunks], s_pc[kIcpQ][kRowChunks];
-  __shared__ int s_cnt;
   __shared__ double sm_tot[kIcpQ];
   __shared__ long long sm_cnt;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const unsigned total = (unsigned)a.n_tiles * (unsigned)a.rounds;
-
-  for (;;) {
-    if (tid == 0) {
-      const unsigned t = atomicAdd(a.work, 1u);
-      int go = (t < total) && (ld_acquire_i32(a.abort) == 0);
-      int b = 0;
-      if (go) {
-        const int it = (int)(t / (unsigned)a.n_tiles);
-        const int tt = (int)(t % (unsigned)a.n_tiles);
-        b = pair_of_tile(a.tile_off, a.pairs, tt);
-        if (it > 0) {
-          long long spins = 0;
-          unsigned ns = 32;
-          while (ld_acquire_i32(&a.st[b].iter_done) < it) {
-            if (ld_acquire_i32(a.abort)) {
-              go = 0;
-              break;
-            }
-            if (++spins > kSpinLimit) {
-              atomicExch(a.abort, 1);
-              atomicCAS(a.err, 0, (int)CIL_ERR_TIMEOUT);
-              go = 0;
-              break;
-            }
-            __nanosleep(ns);
-            if (ns < 512) ns <<= 1;
-          }
-        }
-        if (go) {
-          for (int j = 0; j < 12; ++j) s_Rt[j] = __ldcg(&a.st[b].Rt[j]);
-          s_dmax2 = __ldcg(&a.st[b].dmax2);
-        }
-      }
-      s_t = t;
-      s_go = go;
-      s_pair = b;
+  const int tt = blockIdx.x;
+  if (tid == 0) {
+    s_pair = pair_of(a.tile_off, a.pairs, tt);
+    s_cnt = 0;
+    if (tt == 0) {
+      // the next round's queue counters (last used two rounds ago, whose
+      // launches have completed)
+      a.qcount[(round + 1) & 1] = 0;
+      a.qhead[(round + 1) & 1] = 0;
     }
-    __syncthreads();
-    if (!s_go) break;
-    const int it = (int)(s_t / (unsigned)a.n_tiles);
-    const int tt = (int)(s_t % (unsigned)a.n_tiles);
-    const int b = s_pair;
-    const int tb = __ldg(a.tile_off + b);
-    const int sb = a.src_start ? __ldg(a.src_start + b) : 0;
-    const int se = a.src_start ? __ldg(a.src_start + b + 1) : a.n_src1;
-    const int lo = sb + (tt - tb) * kTileSrc;
-    const int hi = min(se, lo + kTileSrc);
-    const int dst_start = a.g.prm[b].start;
-
-    const float dmax2 = s_dmax2;
-    // phase 1: correspondences (sorted target position or -1) of the tile's
-    // points, kept in shared memory so that the search and the accumulation
-    // below do not hold their registers at the same time
-#pragma unroll 1
-    for (int pass = 0; pass < kIcpPPT; ++pass) {
-      const int pos = lo + pass * kIcpThreads + tid;
-      int bj = -1;
-      if (pos < hi) {
-        const int64_t si = __ldg(a.order + pos);
-        const float x = __ldg(a.src + 3 * si), y = __ldg(a.src + 3 * si + 1),
-                    z = __ldg(a.src + 3 * si + 2);
-        float p[3];
-        p[0] = fmaf(s_Rt[0], x, fmaf(s_Rt[1], y, fmaf(s_Rt[2], z, s_Rt[3])));
-        p[1] = fmaf(s_Rt[4], x, fmaf(s_Rt[5], y, fmaf(s_Rt[6], z, s_Rt[7])));
-        p[2] = fmaf(s_Rt[8], x, fmaf(s_Rt[9], y, fmaf(s_Rt[10], z, s_Rt[11])));
-        nearest_within(a.g, b, p, dmax2, bj);
-      }
-      s_corr[pass * kIcpThreads + tid] = bj;
+  }
+  __syncthreads();
+  const int b = s_pair;
+  if (tid < 12) s_Rt[tid] = a.st[b].Rt[tid];
+  __syncthreads();
+  const int tb = __ldg(a.tile_off + b);
+  const int sb = a.src_start ? __ldg(a.src_start + b) : 0;
+  const int se = a.src_start ? __ldg(a.src_start + b + 1) : a.n_src1;
+  const int dst_start = a.g.prm[b].start;
+  const int pos = sb + (tt - tb) * kTileSrc + tid;
+  // the residual and Jacobian row of the thread's point (zeros where there
+  // is no correspondence)
+  float row[7] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  int cnt = 0;
+  const int bj = pos < se ? a.corr[pos] : -1;
+  if (bj >= 0) {
+    float p[3];
+    transformed_source(a, s_Rt, pos, p);
+    const float4 qp = __ldg(a.g.pts + bj);
+    const int64_t j = dst_start + (int64_t)__float_as_int(qp.w);
+    const float nx = __ldg(a.dst_n + 3 * j), ny = __ldg(a.dst_n + 3 * j + 1),
+                nz = __ldg(a.dst_n + 3 * j + 2);
+    if (isfinite(nx) && isfinite(ny) && isfinite(nz)) {
+      row[0] = p[1] * nz - p[2] * ny;
+      row[1] = p[2] * nx - p[0] * nz;
+      row[2] = p[0] * ny - p[1] * nx;
+      row[3] = nx;
+      row[4] = ny;
+      row[5] = nz;
+      row[6] = nx * (p[0] - qp.x) + ny * (p[1] - qp.y) + nz * (p[2] - qp.z);
+      cnt = 1;
     }
-    // phase 2: the residual and Jacobian row of each point of the tile into
-    // shared memory (zeros where there is no correspondence)
-    if (tid == 0) s_cnt = 0;
-    int cnt = 0;
-#pragma unroll 1
-    for (int pass = 0; pass < kIcpPPT; ++pass) {
-      const int u = pass * kIcpThreads + tid;
-      const int pos = lo + u;
-      const int bj = s_corr[u];
-      float row[7] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-      if (pos < hi && bj >= 0) {
-        const int64_t si = __ldg(a.order + pos);
-        const float x = __ldg(a.src + 3 * si), y = __ldg(a.src + 3 * si + 1),
-                    z = __ldg(a.src + 3 * si + 2);
-        float p[3];
-        p[0] = fmaf(s_Rt[0], x, fmaf(s_Rt[1], y, fmaf(s_Rt[2], z, s_Rt[3])));
-        p[1] = fmaf(s_Rt[4], x, fmaf(s_Rt[5], y, fmaf(s_Rt[6], z, s_Rt[7])));
-        p[2] = fmaf(s_Rt[8], x, fmaf(s_Rt[9], y, fmaf(s_Rt[10], z, s_Rt[11])));
-        const float4 qp = __ldg(a.g.pts + bj);
-        const int64_t j = dst_start + (int64_t)__float_as_int(qp.w);
-        const float nx = __ldg(a.dst_n + 3 * j), ny = __ldg(a.dst_n + 3 * j + 1),
-                    nz = __ldg(a.dst_n + 3 * j + 2);
-        if (isfinite(nx) && isfinite(ny) && isfinite(nz)) {
-          row[0] = p[1] * nz - p[2] * ny;
-          row[1] = p[2] * nx - p[0] * nz;
-          row[2] = p[0] * ny - p[1] * nx;
-          row[3] = nx;
-          row[4] = ny;
-          row[5] = nz;
-          row[6] = nx * (p[0] - qp.x) + ny * (p[1] - qp.y) + nz * (p[2] - qp.z);
-          ++cnt;
-        }
-      }
+  }
 #pragma unroll
-      for (int k = 0; k < 7; ++k) s_row[k][u] = row[k];
-    }
-    __syncthreads();
-    if (cnt) atomicAdd(&s_cnt, cnt);
-    // the tile's 21 + 6 + 1 sums: item (q, ch) adds the products of rows
-    // ch, ch + kRowChunks, ... in that order (compensated), then the chunks
-    // are merged in order -- a fixed order, so the result is deterministic
-    for (int w = tid; w < kIcpQ * kRowChunks; w += kIcpThreads) {
-      const int q = w / kRowChunks, ch = w - q * kRowChunks;
-      int ia, ib;
-      q_operands(q, ia, ib);
+  for (int k = 0; k < 7; ++k) s_row[k][tid] = row[k];
+  const int tile_cnt = __syncthreads_count(cnt);
+  // the tile's 21 + 6 + 1 sums: item (q, ch) adds the products of rows
+  // ch, ch + kRowChunks, ... in that order (compensated), then the chunks are
+  // merged in order -- a fixed order, so the result is deterministic
+  for (int w = tid; w < kIcpQ * kRowChunks; w += kIcpThreads) {
+    const int q = w / kRowChunks, ch = w - q * kRowChunks;
+    int ia, ib;
+    q_operands(q, ia, ib);
+    KSum t;
+    t.zero();
+    for (int i = ch; i < kTileSrc; i += kRowChunks) t.add(__fmul_rn(s_row[ia][i], s_row[ib][i]));
+    s_ps[q][ch] = t.s;
+    s_pc[q][ch] = t.c;
+  }
+  __syncthreads();
+  if (tid < kIcpQ) {
+    KSum t;
+    t.zero();
+    for (int ch = 0; ch < kRowChunks; ++ch) t.merge(s_ps[tid][ch], s_pc[tid][ch]);
+    a.part_s[(int64_t)tt * kIcpQ + tid] = t.s;
+    a.part_c[(int64_t)tt * kIcpQ + tid] = t.c;
+  } else if (tid == 32) {
+    a.part_n[tt] = tile_cnt;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    const int ntiles_b = __ldg(a.tile_off + b + 1) - tb;
+    const int gl = (tt - tb) / kIcpGroup;
+    const int gid = a.st[b].grp_begin + gl;
+    const int gsize = min(kIcpGroup, ntiles_b - gl * kIcpGroup);
+    const int old = atomicAdd(a.grp_done + gid, 1);
+    s_last = (old == gsize - 1);
+    s_gid = gid;
+    s_g0 = tb + gl * kIcpGroup;
+    s_gsize = gsize;
+  }
+  __syncthreads();
+  if (!s_last) return;
+
+  // ---- this block reduces its tile group: tile u of the group in lane u,
+  // a fixed compensated shuffle tree ----
+  __threadfence();
+  {
+    const int gid = s_gid, g0 = s_g0, gs = s_gsize;
+    for (int q = warp; q < kIcpQ; q += kIcpWarps) {
       KSum t;
       t.zero();
-      for (int i = ch; i < kTileSrc; i += kRowChunks) t.add(__fmul_rn(s_row[ia][i], s_row[ib][i]));
-      s_ps[q][ch] = t.s;
-      s_pc[q][ch] = t.c;
+      if (lane < gs) {
+        t.s = __ldcg(a.part_s + (int64_t)(g0 + lane) * kIcpQ + q);
+        t.c = __ldcg(a.part_c + (int64_t)(g0 + lane) * kIcpQ + q);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float s2 = __shfl_down_sync(0xffffffffu, t.s, off);
+        const float c2 = __shfl_down_sync(0xffffffffu, t.c, off);
+        t.merge(s2, c2);
+      }
+      if (lane == 0) {
+        a.grp_s[(int64_t)gid * kIcpQ + q] = t.s;
+        a.grp_c[(int64_t)gid * kIcpQ + q] = t.c;
+      }
     }
-    __syncthreads();
-    if (tid < kIcpQ) {
+    if (warp == kIcpWarps - 1) {
+      int n = lane < gs ? __ldcg(a.part_n + g0 + lane) : 0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) n += __shfl_down_sync(0xffffffffu, n, off);
+      if (lane == 0) a.grp_n[gid] = n;
+    }
+    // every tile of this group has been counted for this round; the next
+    // round runs after this launch
+    if (tid == 0) a.grp_done[gid] = 0;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    const int old = atomicAdd(&a.st[b].tiles_done, 1);
+    s_last = (old == a.st[b].n_grp - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+
+  // ---- this block closes the round of pair b: group partials in order ----
+  __threadfence();
+  {
+    const int gb = a.st[b].grp_begin, ge = gb + a.st[b].n_grp;
+    for (int q = warp; q < kIcpQ; q += kIcpWarps) {
       KSum t;
       t.zero();
-      for (int ch = 0; ch < kRowChunks; ++ch) t.merge(s_ps[tid][ch], s_pc[tid][ch]);
-      a.part_s[(int64_t)tt * kIcpQ + tid] = t.s;
-      a.part_c[(int64_t)tt * kIcpQ + tid] = t.c;
-    } else if (tid == 32) {
-      a.part_n[tt] = s_cnt;
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-      const int ntiles_b = __ldg(a.tile_off + b + 1) - tb;
-      const int gl = (tt - tb) / kIcpGroup;
-      const int gid = a.st[b].grp_begin + gl;
-      const int gsize = min(kIcpGroup, ntiles_b - gl * kIcpGroup);
-      const int old = atomicAdd(a.grp_done + gid, 1);
-      s_last = (old == gsize - 1);
-      s_gid = gid;
-      s_g0 = tb + gl * kIcpGroup;
-      s_gsize = gsize;
-    }
-    __syncthreads();
-    if (!s_last) continue;
-
-    // ---- this block reduces its tile group: tile u of the group in lane u,
-    // a fixed compensated shuffle tree ----
-    __threadfence();
-    {
-      const int gid = s_gid, g0 = s_g0, gs = s_gsize;
-      for (int q = warp; q < kIcpQ; q += kIcpWarps) {
-        KSum t;
-        t.zero();
-        if (lane < gs) {
-          t.s = __ldcg(a.part_s + (int64_t)(g0 + lane) * kIcpQ + q);
-          t.c = __ldcg(a.part_c + (int64_t)(g0 + lane) * kIcpQ + q);
-        }
+      for (int u = gb + lane; u < ge; u += 32)
+        t.merge(__ldcg(a.grp_s + (int64_t)u * kIcpQ + q), __ldcg(a.grp_c + (int64_t)u * kIcpQ + q));
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          const float s2 = __shfl_down_sync(0xffffffffu, t.s, off);
-          const float c2 = __shfl_down_sync(0xffffffffu, t.c, off);
-          t.merge(s2, c2);
-        }
-        if (lane == 0) {
-          a.grp_s[(int64_t)gid * kIcpQ + q] = t.s;
-          a.grp_c[(int64_t)gid * kIcpQ + q] = t.c;
-        }
+      for (int off = 16; off > 0; off >>= 1) {
+        const float s2 = __shfl_down_sync(0xffffffffu, t.s, off);
+        const float c2 = __shfl_down_sync(0xffffffffu, t.c, off);
+        t.merge(s2, c2);
       }
-      if (warp == kIcpWarps - 1) {
-        int n = lane < gs ? __ldcg(a.part_n + g0 + lane) : 0;
+      if (lane == 0) sm_tot[q] = (double)t.s + (double)t.c;
+    }
+    if (warp == kIcpWarps - 1) {
+      long long n = 0;
+      for (int u = gb + lane; u < ge; u += 32) n += __ldcg(a.grp_n + u);
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) n += __shfl_down_sync(0xffffffffu, n, off);
-        if (lane == 0) a.grp_n[gid] = n;
-      }
-      // every tile of this group has been counted for this round; the next
-      // round's tiles start only after the round is published
-      if (tid == 0) a.grp_done[gid] = 0;
+      for (int off = 16; off > 0; off >>= 1) n += __shfl_down_sync(0xffffffffu, n, off);
+      if (lane == 0) sm_cnt = n;
     }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-      const int old = atomicAdd(&a.st[b].tiles_done, 1);
-      s_last = (old == a.st[b].n_grp - 1);
-    }
-    __syncthreads();
-    if (!s_last) continue;
-
-    // ---- this block closes round `it` of pair b: group partials in order ----
-    __threadfence();
-    {
-      const int gb = a.st[b].grp_begin, ge = gb + a.st[b].n_grp;
-      for (int q = warp; q < kIcpQ; q += kIcpWarps) {
-        KSum t;
-        t.zero();
-        for (int u = gb + lane; u < ge; u += 32)
-          t.merge(__ldcg(a.grp_s + (int64_t)u * kIcpQ + q), __ldcg(a.grp_c + (int64_t)u * kIcpQ + q));
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          const float s2 = __shfl_down_sync(0xffffffffu, t.s, off);
-          const float c2 = __shfl_down_sync(0xffffffffu, t.c, off);
-          t.merge(s2, c2);
-        }
-        if (lane == 0) sm_tot[q] = (double)t.s + (double)t.c;
-      }
-      if (warp == kIcpWarps - 1) {
-        long long n = 0;
-        for (int u = gb + lane; u < ge; u += 32) n += __ldcg(a.grp_n + u);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) n += __shfl_down_sync(0xffffffffu, n, off);
-        if (lane == 0) sm_cnt = n;
-      }
-    }
-    __syncthreads();
-    if (tid == 0) {
-      IcpPairState& S = a.st[b];
-      close_round(S, sm_tot, sm_cnt, it == a.rounds - 1);
-      S.tiles_done = 0;
-      __threadfence();
-      st_release_i32(&S.iter_done, it + 1);
-    }
-    __syncthreads();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    IcpPairState& S = a.st[b];
+    close_round(S, sm_tot, sm_cnt, round == a.rounds - 1);
+    S.tiles_done = 0;
   }
 }
 
@@ -714,8 +908,9 @@ void icp_plan(IcpPlan& p, Workspace& ws, const int64_t* src_counts, int pairs) {
     p.n_groups += ceil_div(t, kIcpGroup);
   }
   const int nt = p.n_tiles > 0 ? p.n_tiles : 1;
+  const size_t ns = (size_t)(p.n_src > 0 ? p.n_src : 1);
   p.o_state = ws.reserve(sizeof(IcpPairState) * pairs);
-  p.o_order = ws.reserve(sizeof(int) * (size_t)(p.n_src > 0 ? p.n_src : 1));
+  p.o_order = ws.reserve(sizeof(int) * ns);
   p.o_tile_off = ws.reserve(sizeof(int) * (pairs + 1));
   p.o_rt = ws.reserve(sizeof(float) * 12 * pairs);
   p.o_part_s = ws.reserve(sizeof(float) * kIcpQ * nt);
@@ -726,7 +921,9 @@ void icp_plan(IcpPlan& p, Workspace& ws, const int64_t* src_counts, int pairs) {
   p.o_grp_c = ws.reserve(sizeof(float) * kIcpQ * ng);
   p.o_grp_n = ws.reserve(sizeof(int) * ng);
   p.o_grp_done = ws.reserve(sizeof(int) * ng);
-  p.o_work = ws.reserve(sizeof(unsigned) * 4);
+  p.o_corr = ws.reserve(sizeof(int) * ns);
+  p.o_queue = ws.reserve(sizeof(int2) * ns);
+  p.o_qc = ws.reserve(sizeof(unsigned) * 4);
   order_plan(p.order, ws, p.n_src);
 }
 
@@ -743,11 +940,11 @@ cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt, c
   IcpPairState* st = ws.at<IcpPairState>(p.o_state);
   int* tile_off = ws.at<int>(p.o_tile_off);
   float* rt = ws.at<float>(p.o_rt);
-  unsigned* work = ws.at<unsigned>(p.o_work);
+  unsigned* qc = ws.at<unsigned>(p.o_qc);
   note_launches(1);
   k_icp_setup<<<1, 1024, 0, s>>>(st, p.pairs, src_start_dev, p.n_src, tile_off, T_init_dev, Th,
                                  T_init_host != nullptr, dmax_dev, dmax, iters, rt);
-  if (cudaMemsetAsync(work, 0, sizeof(unsigned) * 4, s) != cudaSuccess) return CIL_ERR_CUDA;
+  if (cudaMemsetAsync(qc, 0, sizeof(unsigned) * 4, s) != cudaSuccess) return CIL_ERR_CUDA;
   if (cudaMemsetAsync(ws.at<int>(p.o_grp_done), 0,
                       sizeof(int) * (size_t)(p.n_groups > 0 ? p.n_groups : 1), s) != cudaSuccess)
     return CIL_ERR_CUDA;
@@ -767,6 +964,10 @@ cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt, c
   a.n_tiles = p.n_tiles;
   a.rounds = iters + 1;
   a.st = st;
+  a.corr = ws.at<int>(p.o_corr);
+  a.queue = ws.at<int2>(p.o_queue);
+  a.qcount = qc;
+  a.qhead = qc + 2;
   a.part_s = ws.at<float>(p.o_part_s);
   a.part_c = ws.at<float>(p.o_part_c);
   a.part_n = ws.at<int>(p.o_part_n);
@@ -774,19 +975,26 @@ cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt, c
   a.grp_c = ws.at<float>(p.o_grp_c);
   a.grp_n = ws.at<int>(p.o_grp_n);
   a.grp_done = ws.at<int>(p.o_grp_done);
-  a.work = work;
-  a.abort = reinterpret_cast<int*>(work + 1);
-  a.err = ctx->err;
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_icp, kIcpThreads, 0);
-  if (per_sm < 1) per_sm = 1;
-  const long long want = (long long)p.n_tiles * a.rounds;
-  int grid = ctx->num_sms * per_sm;
-  if (want < grid) grid = (int)want;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_icp_finish, kIcpThreads, 0);
+  const int grid_f = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
   {
     TimedRegion timer("k_icp", s);
-    note_launches(1);
-    k_icp<<<grid, kIcpThreads, 0, s>>>(a);
+    note_launches(3 * a.rounds);
+    for (int r = 0; r < a.rounds; ++r) {
+      {
+        TimedRegion t1("k_icp_search", s);
+        k_icp_search<<<p.n_tiles, kIcpThreads, 0, s>>>(a, r);
+      }
+      {
+        TimedRegion t2("k_icp_finish", s);
+        k_icp_finish<<<grid_f, kIcpThreads, 0, s>>>(a, r);
+      }
+      {
+        TimedRegion t3("k_icp_accumulate", s);
+        k_icp_accumulate<<<p.n_tiles, kIcpThreads, 0, s>>>(a, r);
+      }
+    }
   }
   return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
 }

@@ -9,8 +9,9 @@ frames, ~3.07e5 points), lidar (64 x 2048 sweep, ~1.2e5 returns), batch (256
 surface pairs with sizes log-uniform in [2e3, 2e5]).  Ops: register (grid,
 k-NN normals and point-to-plane ICP), knn (self k-NN), normals, radius
 (radius search), batch (the batched graph run; workload batch only).  Each op
-runs --repeat times after one warm-up call; the per-kernel times recorded by
-the library are printed as one JSON line.
+runs --repeat times after one warm-up call; the CUDA-event time per call and
+the per-kernel times recorded by the library (not inside graph replays) are
+printed as one JSON line.
 """
 from __future__ import annotations
 
@@ -65,11 +66,16 @@ def main(argv=None):
     torch.cuda.synchronize()
     L.cil_timing_reset()
     L.cil_timing_enable(1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
     for _ in range(a.repeat):
         fn()
+    e1.record()
     torch.cuda.synchronize()
     L.cil_timing_enable(0)
-    out = {"workload": a.workload, "op": a.op, "k": k, "iters": a.iters, "repeat": a.repeat}
+    out = {"workload": a.workload, "op": a.op, "k": k, "iters": a.iters, "repeat": a.repeat,
+           "ms_per_call": e0.elapsed_time(e1) / a.repeat}
     for name in ("grid_build", "order_queries", "k_knn", "k_normals", "k_icp", "k_radius"):
         t, c = ctypes.c_double(), ctypes.c_int64()
         L.cil_timing_read(name.encode(), ctypes.byref(t), ctypes.byref(c))
