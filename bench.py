@@ -54,10 +54,10 @@ WORKLOAD = ("depth-frame pair 640x480 (pinhole 525/319.5/239.5, ground + 20 boxe
             "PCA normals of every target point + 30 point-to-plane ICP rounds (d_max 0.05 m) + "
             "final RMSE pass")
 
-# DRAM traffic per k_icp launch measured by ncu on this workload (bytes), with
-# the hash of the kernel sources it was measured on; reported only while the
-# sources are unchanged.
-ICP_TRAFFIC = {"bytes": None, "src_sha": None}
+# DRAM traffic per k_icp_search launch measured by ncu on this workload
+# (bytes), with the hash of the kernel sources it was measured on; reported
+# only while the sources are unchanged.
+ICP_TRAFFIC = {"bytes": 34844416, "src_sha": "f7c9ac27755551a3"}
 
 
 def _peaks():
@@ -285,7 +285,7 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in evs]
     tot_ms = float(sum(step_ms))
     kern = {}
-    for name in ("grid_build", "k_normals", "order_queries", "k_icp"):
+    for name in ("grid_build", "k_normals", "order_queries", "k_icp", "k_icp_search"):
         t = ctypes.c_double(0)
         c = ctypes.c_int64(0)
         L.cil_timing_read(name.encode(), ctypes.byref(t), ctypes.byref(c))
@@ -327,18 +327,19 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel ----
     peaks, peak_kind = _peaks()
-    dom = max(kern, key=lambda k: kern[k]["ms_total"])
     per_launch_ms = {k: (v["ms_total"] / v["launches"] if v["launches"] else None)
                      for k, v in kern.items()}
-    rounds = ICP_ITERS + 1
+    # the dominant kernel by the ncu launch list is k_icp_search (one launch
+    # per ICP round; the ICP loop "k_icp" is 93 launches of three kernels)
+    dom = "k_icp_search"
     alg = {  # algorithmic bytes per launch (roofline section)
-        "k_icp": rounds * (12 * ns + 24 * nt),
+        "k_icp_search": 20 * ns + 16 * nt,
         "k_normals": 40 * nt,
         "grid_build": 52 * nt + 16 * (1 << math.ceil(math.log2(2 * nt))),
         "order_queries": 52 * ns,
     }
     traffic = None
-    if dom == "k_icp" and ICP_TRAFFIC["bytes"] and ICP_TRAFFIC["src_sha"] == _src_sha():
+    if ICP_TRAFFIC["bytes"] and ICP_TRAFFIC["src_sha"] == _src_sha():
         traffic = ICP_TRAFFIC["bytes"]
     achieved = alg[dom] / (per_launch_ms[dom] / 1e3) / 1e9
     roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
