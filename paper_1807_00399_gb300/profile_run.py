@@ -31,6 +31,8 @@ def main(argv=None):
     ap.add_argument("--radius", type=float, default=0.5)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-regions", action="store_true",
+                    help="time the calls only (no per-kernel event records between launches)")
     a = ap.parse_args(argv)
 
     import torch
@@ -65,7 +67,7 @@ def main(argv=None):
     fn()
     torch.cuda.synchronize()
     L.cil_timing_reset()
-    L.cil_timing_enable(1)
+    L.cil_timing_enable(0 if a.no_regions else 1)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
