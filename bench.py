@@ -402,8 +402,9 @@ def run_ours(args):
 
 def run_batched(args, rank: int, B: int = 256, runs: int = 5):
     """256 wavy-surface pairs with point counts log-uniform in [2e3, 2e5]:
-    one graph launch (grid + 10-NN normals + 30 ICP rounds for every pair)
-    against 256 sequential single-pair calls of the same pipeline; both reach
+    one graph launch (grid + 10-NN normals + 30 ICP rounds for every pair,
+    cell size and block shape from the autotuner) against 256 sequential
+    single-pair calls of the same pipeline with default settings; both reach
     the same per-pair RMSE (the batched results are bitwise those of the
     single-pair calls)."""
     import torch
@@ -411,10 +412,17 @@ def run_batched(args, rank: int, B: int = 256, runs: int = 5):
     import paper_1807_00399_gb300 as cil
     from paper_1807_00399_gb300 import synth
 
+    from paper_1807_00399_gb300 import autotune
+
     sizes = synth.batch_sizes(args.seed + rank, B)
     src, dst, T_gt = synth.surface_batch_torch(1000 + args.seed + rank, sizes)
+    # the autotuner picks the cell-size multiplier and query block shape for
+    # this batch shape (cached per GPU and size bucket)
+    tuned = autotune.tune_batch(src, dst, sizes, sizes, k=K_NN, iters=ICP_ITERS,
+                                max_corr_dist=0.1, reps=1)
     h = cil.Batch(sizes, sizes, k=K_NN, iters=ICP_ITERS, max_corr_dist=0.1,
-                  viewpoint=(0.0, 0.0, 10.0))
+                  viewpoint=(0.0, 0.0, 10.0), cell_scale=tuned["cell_scale"],
+                  block=tuned["block"])
     RS = ctypes.sizeof(cil.IcpReport)
     T = torch.empty((B, 16), dtype=torch.float64, device="cuda")
     rep = torch.empty((B, RS), dtype=torch.uint8, device="cuda")
@@ -459,6 +467,10 @@ def run_batched(args, rank: int, B: int = 256, runs: int = 5):
     M = Tb[:, :3, :3] @ np.transpose(Rg[:, :3, :3], (0, 2, 1))
     rot_err = np.degrees(np.arccos(np.clip((np.trace(M, axis1=1, axis2=2) - 1) / 2, -1, 1)))
     return {"pairs": B, "points_per_side": int(sizes.sum()),
+            "autotune": {"cell_scale": tuned["cell_scale"], "block": tuned["block"],
+                         "cached": tuned["cached"],
+                         "table_ms": {f'{r["cell_scale"]}/{r["block"]}': round(r["ms"], 3)
+                                      for r in tuned.get("table", [])}},
             "ms_batched_graph": ms_b, "pairs_per_s_batched": B / (ms_b / 1e3),
             "ms_sequential_plain": ms_s, "pairs_per_s_plain": B / (ms_s / 1e3),
             "speedup": ms_s / ms_b,

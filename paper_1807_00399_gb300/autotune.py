@@ -52,9 +52,13 @@ def _store(path, data):
 
 def time_batch(h, src, dst, reps: int = 3, warmup: int = 1) -> float:
     """Median milliseconds of `reps` runs of a Batch handle."""
+    import ctypes
+
     import torch
+
+    from . import IcpReport
     T = torch.empty((h.B, 16), dtype=torch.float64, device=dst.device)
-    rep = torch.empty((h.B, 32), dtype=torch.uint8, device=dst.device)
+    rep = torch.empty((h.B, ctypes.sizeof(IcpReport)), dtype=torch.uint8, device=dst.device)
     for _ in range(warmup):
         h.run(src, dst, T_out=T, rep=rep)
     ts = []
