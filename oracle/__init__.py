@@ -23,6 +23,10 @@ than the oracle itself):
   equal to numpy.linalg.lstsq on independently built Jacobian rows,
   rigid-motion equivariance, invariance to normal signs and to permutations,
   and a planar (singular) target flagged degenerate.
+
+The ICP variants of Sec. 3 (point-to-point, weighted combination, projective
+association) are in ``icp_variants.py`` (numpy FP64, pinned by
+``tests/test_oracle_icp_variants.py``).
 """
 from __future__ import annotations
 

@@ -201,9 +201,12 @@ def _depth_scene(rng, n_boxes=20, n_spheres=10):
     return lo, hi, sc, radii
 
 
-def _render_depth(rng, pose_wc, scene, width, height, fx, fy, cx, cy, zmin, zmax):
+def _render_depth(rng, pose_wc, scene, width, height, fx, fy, cx, cy, zmin, zmax,
+                  return_pixels: bool = False):
     """Ray-cast a pinhole camera (x right, y down, z forward; pose_wc maps
-    camera to world) and back-project the noisy depth to camera-frame points."""
+    camera to world) and back-project the noisy depth to camera-frame points
+    (raster order of the valid pixels; with return_pixels also their flat
+    pixel indices v * width + u)."""
     lo, hi, sc, radii = scene
     u, v = np.meshgrid(np.arange(width, dtype=np.float64), np.arange(height, dtype=np.float64))
     u = u.ravel()
@@ -223,6 +226,8 @@ def _render_depth(rng, pose_wc, scene, width, height, fx, fy, cx, cy, zmin, zmax
     z = z[valid]
     z = z + rng.normal(0.0, 1.0, size=z.shape) * 0.001 * z * z
     pts = dc[valid] * z[:, None]
+    if return_pixels:
+        return pts, np.nonzero(valid)[0].astype(np.int32)
     return pts
 
 
@@ -241,7 +246,10 @@ def depth_frame_pair(
     Camera 1 sits 1.5 m above the ground pitched 45 deg down; camera 2 is camera
     1 moved by a random rotation <= 3 deg and translation <= 3 cm (expressed in
     camera-1 coordinates).  Target = frame 1 points (camera-1 frame), source =
-    frame 2 points (camera-2 frame), ``T_gt`` = camera-2 -> camera-1."""
+    frame 2 points (camera-2 frame), ``T_gt`` = camera-2 -> camera-1.
+    ``meta["target_pixels"]`` holds the flat pixel index (v * w + u) of each
+    target point and ``meta["intrinsics"]`` (fx, fy, cx, cy): the target frame
+    as an organised image, for projective association."""
     rng = np.random.default_rng(seed)
     scene = _depth_scene(rng)
     s = c = math.sqrt(0.5)
@@ -253,14 +261,16 @@ def depth_frame_pair(
     P1[:3, 3] = [0.0, 0.0, 1.5]
     dT = random_rigid(rng, max_angle_deg, max_trans, "ball")
     P2 = P1 @ dT
-    tgt = _render_depth(rng, P1, scene, width, height, fx, fy, cx, cy, 0.5, 5.0)
+    tgt, tgt_pix = _render_depth(rng, P1, scene, width, height, fx, fy, cx, cy, 0.5, 5.0,
+                                 return_pixels=True)
     src = _render_depth(rng, P2, scene, width, height, fx, fy, cx, cy, 0.5, 5.0)
     return Pair(
         source=src.astype(np.float32),
         target=tgt.astype(np.float32),
         T_gt=dT,
         viewpoint=np.zeros(3),
-        meta={"kind": "depth", "seed": seed, "w": width, "h": height},
+        meta={"kind": "depth", "seed": seed, "w": width, "h": height,
+              "intrinsics": (fx, fy, cx, cy), "target_pixels": tgt_pix},
     )
 
 
