@@ -238,6 +238,62 @@ cil_status cil_register_pair(const float *src, int64_t n_src, const float *dst, 
                              cil_icp_report *rep, const cil_params *params, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * ICP variants (Sec. 3: the ICP loop parameterised by the correspondence
+ * search and the estimator; rigid registration under the point-to-point
+ * metric (Besl & McKay), the point-to-plane metric (Low) and weighted
+ * combinations thereof; correspondences by nearest-neighbour search or by
+ * projective data association).
+ *   metric       CIL_METRIC_POINT_TO_PLANE: as cil_icp_point_to_plane;
+ *                CIL_METRIC_POINT_TO_POINT: each round the closed-form rigid
+ *                motion minimising sum |R p' + t - q|^2 (FP64);
+ *                CIL_METRIC_COMBINED: w_point sum |p' - q|^2 + w_plane sum
+ *                (n.(p' - q))^2, linearised, one FP64 Gauss-Newton step per
+ *                round (w_point, w_plane >= 0, finite).
+ *   association  CIL_ASSOC_NEAREST: exact nearest target point within
+ *                max_corr_dist (as cil_icp_point_to_plane);
+ *                CIL_ASSOC_PROJECTIVE: the target is the organised image of
+ *                its camera (target coordinates = camera frame): p' projects
+ *                to pixel (round(fx x/z + cx), round(fy y/z + cy)) (halves to
+ *                even); pixel_map (device int32[height][width]) holds the
+ *                index of the target point seen at each pixel or -1; the
+ *                point there is the correspondence when |p' - q| <=
+ *                max_corr_dist; z <= 0, outside the image or -1: none.
+ * The report's rmse is the metric's own residual after the final
+ * association pass: point-to-point distance, plane residual, or
+ * sqrt(mean(w_point d^2 + w_plane r^2)).  Rounds whose system does not fix a
+ * motion (fewer than 3 correspondences for the closed form, fewer than 6 or
+ * a Cholesky pivot <= 1e-12 tr H otherwise) keep T and report
+ * CIL_ERR_DEGENERATE.
+ * ------------------------------------------------------------------------- */
+typedef enum {
+  CIL_METRIC_POINT_TO_PLANE = 0,
+  CIL_METRIC_POINT_TO_POINT = 1,
+  CIL_METRIC_COMBINED = 2
+} cil_icp_metric;
+
+typedef enum { CIL_ASSOC_NEAREST = 0, CIL_ASSOC_PROJECTIVE = 1 } cil_icp_association;
+
+typedef struct {
+  int metric;               /* cil_icp_metric                                  */
+  float w_point, w_plane;   /* weights of CIL_METRIC_COMBINED                  */
+  int association;          /* cil_icp_association                             */
+  const int32_t* pixel_map; /* device int32[height][width] (projective only)   */
+  int width, height;        /* image size (projective only)                    */
+  float fx, fy, cx, cy;     /* pinhole intrinsics (projective only)            */
+} cil_icp_options;
+
+/* cil_icp_point_to_plane with a metric and a correspondence search chosen by
+ * `opt` (NULL: point-to-plane, nearest neighbour).  dst_normals may be NULL
+ * for CIL_METRIC_POINT_TO_POINT.  Same argument rules, outputs and
+ * synchronisation as cil_icp_point_to_plane; additionally
+ * CIL_ERR_INVALID_ARG for an unknown metric or association, negative or
+ * non-finite weights, or a projective search without a pixel map, positive
+ * image size and finite intrinsics. */
+cil_status cil_icp(const float *src, int64_t n_src, const float *dst, const float *dst_normals,
+                   int64_t n_dst, const double *T_init, int max_iters, float max_corr_dist,
+                   const cil_icp_options *opt, double *T_out, cil_icp_report *rep, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Batched registration of B independent pairs of uneven sizes (no counterpart
  * in the paper, which registers one pair at a time, Sec. 4).  Per pair: the
  * same target grid + k-NN normals + point-to-plane ICP as cil_register_pair,

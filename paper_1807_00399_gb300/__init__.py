@@ -17,7 +17,8 @@ import numpy as np
 
 __all__ = [
     "CilError", "lib", "knn", "radius_search", "estimate_normals", "icp_point_to_plane",
-    "register_pair", "sync_status", "Params", "STATUS", "MAX_K", "IcpReport", "Batch",
+    "register_pair", "sync_status", "Params", "STATUS", "MAX_K", "IcpReport", "Batch", "icp",
+    "IcpOptions",
     "decode_report", "decode_reports",
 ]
 
@@ -75,6 +76,7 @@ def lib():
         L.cil_estimate_normals.argtypes = [P, I64, I, P, P, P, P]
         L.cil_estimate_normals_ex.argtypes = [P, I64, I, P, P, P, P, P]
         L.cil_icp_point_to_plane.argtypes = [P, I64, P, P, I64, P, I, F, P, P, P]
+        L.cil_icp.argtypes = [P, I64, P, P, I64, P, I, F, P, P, P, P]
         L.cil_register_pair.argtypes = [P, I64, P, I64, I, P, P, I, F, P, P, P, P, P]
         L.cil_icp_batch_create.argtypes = [P, P, I, P, P]
         L.cil_icp_batch_run.argtypes = [P, P, P, P, P, P, P, P]
@@ -288,6 +290,61 @@ def icp_point_to_plane(src, dst, dst_normals, T_init=None, iters: int = 20,
                                       T0, int(iters), float(max_corr_dist), Tout,
                                       ctypes.byref(rep), _stream(stream))
     _check(st, "cil_icp_point_to_plane")
+    return np.array(Tout[:], np.float64).reshape(4, 4), {
+        "rmse": rep.rmse, "n_inliers": int(rep.n_inliers), "iters_done": rep.iters_done,
+        "status": rep.status}
+
+
+class IcpOptions(ctypes.Structure):
+    _fields_ = [("metric", ctypes.c_int), ("w_point", ctypes.c_float), ("w_plane", ctypes.c_float),
+                ("association", ctypes.c_int), ("pixel_map", ctypes.c_void_p),
+                ("width", ctypes.c_int), ("height", ctypes.c_int), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float)]
+
+
+METRICS = {"point_to_plane": 0, "point_to_point": 1, "combined": 2}
+ASSOCIATIONS = {"nearest": 0, "projective": 1}
+
+
+def icp(src, dst, dst_normals=None, T_init=None, iters: int = 20, max_corr_dist: float = 0.1, *,
+        metric: str = "point_to_plane", w_point: float = 0.0, w_plane: float = 1.0,
+        association: str = "nearest", pixel_map=None, intrinsics=None, stream=None):
+    """Rigid ICP with a chosen metric and correspondence search (cil_icp).
+    metric: point_to_plane | point_to_point | combined (weights w_point,
+    w_plane); association: nearest | projective (pixel_map: int32 CUDA tensor
+    (height, width) of target point indices or -1; intrinsics (fx, fy, cx,
+    cy)).  Returns (T 4x4 float64 numpy, report dict)."""
+    src = _points(src, "src")
+    dst = _points(dst, "dst")
+    nrm = None
+    if dst_normals is not None:
+        nrm = _points(dst_normals, "dst_normals")
+        if nrm.shape != dst.shape:
+            raise ValueError("dst_normals must match dst")
+    o = IcpOptions()
+    o.metric = METRICS[metric]
+    o.w_point = float(w_point)
+    o.w_plane = float(w_plane)
+    o.association = ASSOCIATIONS[association]
+    if association == "projective":
+        torch = _torch()
+        if pixel_map is None or intrinsics is None:
+            raise ValueError("projective association needs pixel_map and intrinsics")
+        if pixel_map.dtype != torch.int32 or pixel_map.dim() != 2 or not pixel_map.is_cuda:
+            raise ValueError("pixel_map must be an int32 CUDA tensor (height, width)")
+        pixel_map = pixel_map.contiguous()
+        o.pixel_map = pixel_map.data_ptr()
+        o.height, o.width = int(pixel_map.shape[0]), int(pixel_map.shape[1])
+        o.fx, o.fy, o.cx, o.cy = [float(v) for v in intrinsics]
+    T0 = None
+    if T_init is not None:
+        T0 = (ctypes.c_double * 16)(*np.asarray(T_init, np.float64).reshape(16).tolist())
+    Tout = (ctypes.c_double * 16)()
+    rep = IcpReport()
+    st = lib().cil_icp(_ptr(src), src.shape[0], _ptr(dst), _ptr(nrm) if nrm is not None else None,
+                       dst.shape[0], T0, int(iters), float(max_corr_dist), ctypes.byref(o), Tout,
+                       ctypes.byref(rep), _stream(stream))
+    _check(st, "cil_icp")
     return np.array(Tout[:], np.float64).reshape(4, 4), {
         "rmse": rep.rmse, "n_inliers": int(rep.n_inliers), "iters_done": rep.iters_done,
         "status": rep.status}

@@ -52,7 +52,7 @@ static cil_status enqueue_batch(BatchHandle* h, const float* src, const float* d
   if ((st = launch_normals(g, h->B, h->tot_dst, h->prm.k, nullptr, h->prm.viewpoint, dst, nrm,
                            nullptr, block, s)) != CIL_OK)
     return st;
-  if ((st = icp_run(h->ip, h->ws, g, src, src_start, nrm, T_init, nullptr, h->prm.iters, nullptr,
+  if ((st = icp_run(h->ip, h->ws, g, src, src_start, dst, nrm, T_init, nullptr, h->prm.iters, nullptr,
                     h->prm.max_corr_dist, h->ctx, s)) != CIL_OK)
     return st;
   return icp_export(h->ip, h->ws, T_out, rep, s);

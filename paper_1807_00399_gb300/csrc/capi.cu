@@ -321,14 +321,43 @@ cil_status cil_estimate_normals_radius(const float* xyz, int64_t n, float r, con
   return st;
 }
 
-cil_status cil_icp_point_to_plane(const float* src, int64_t n_src, const float* dst,
-                                  const float* dst_normals, int64_t n_dst, const double* T_init,
-                                  int max_iters, float max_corr_dist, double* T_out,
-                                  cil_icp_report* rep, void* stream) {
+cil_status cil_icp(const float* src, int64_t n_src, const float* dst, const float* dst_normals,
+                   int64_t n_dst, const double* T_init, int max_iters, float max_corr_dist,
+                   const cil_icp_options* opt, double* T_out, cil_icp_report* rep, void* stream) {
+  IcpOptions o;
+  if (opt) {
+    if (opt->metric < CIL_METRIC_POINT_TO_PLANE || opt->metric > CIL_METRIC_COMBINED ||
+        opt->association < CIL_ASSOC_NEAREST || opt->association > CIL_ASSOC_PROJECTIVE)
+      return CIL_ERR_INVALID_ARG;
+    o.metric = opt->metric;
+    o.association = opt->association;
+    if (o.metric == CIL_METRIC_COMBINED) {
+      if (!(opt->w_point >= 0.0f && opt->w_point < INFINITY && opt->w_plane >= 0.0f &&
+            opt->w_plane < INFINITY))
+        return CIL_ERR_INVALID_ARG;
+      o.w_point = opt->w_point;
+      o.w_plane = opt->w_plane;
+    }
+    if (o.association == CIL_ASSOC_PROJECTIVE) {
+      if (!opt->pixel_map || opt->width <= 0 || opt->height <= 0 ||
+          !(fabsf(opt->fx) < INFINITY && fabsf(opt->fy) < INFINITY && fabsf(opt->cx) < INFINITY &&
+            fabsf(opt->cy) < INFINITY))
+        return CIL_ERR_INVALID_ARG;
+      o.pixel_map = opt->pixel_map;
+      o.width = opt->width;
+      o.height = opt->height;
+      o.fx = opt->fx;
+      o.fy = opt->fy;
+      o.cx = opt->cx;
+      o.cy = opt->cy;
+    }
+  }
+  const bool need_normals = o.metric != CIL_METRIC_POINT_TO_POINT;
   if (bad_count(n_src) || bad_count(n_dst) || max_iters < 0 || !(max_corr_dist >= 0.0f) || !T_out ||
       !rep)
     return CIL_ERR_INVALID_ARG;
-  if ((n_src > 0 && !src) || (n_dst > 0 && (!dst || !dst_normals))) return CIL_ERR_INVALID_ARG;
+  if ((n_src > 0 && !src) || (n_dst > 0 && (!dst || (need_normals && !dst_normals))))
+    return CIL_ERR_INVALID_ARG;
   cil_status st = CIL_OK;
   DeviceCtx* ctx = device_ctx(&st);
   if (!ctx) return st;
@@ -343,8 +372,8 @@ cil_status cil_icp_point_to_plane(const float* src, int64_t n_src, const float* 
   if ((st = ws.allocate(ctx, s)) != CIL_OK) return st;
   GridOptions gopt = grid_options(nullptr, 10);
   if ((st = grid_build(gp, ws, dst, nullptr, gopt, ctx, s)) != CIL_OK) return st;
-  if ((st = icp_run(ip, ws, grid_view(gp, ws), src, nullptr, dst_normals, nullptr, T_init, max_iters,
-                    nullptr, max_corr_dist, ctx, s)) != CIL_OK)
+  if ((st = icp_run(ip, ws, grid_view(gp, ws), src, nullptr, dst, need_normals ? dst_normals : nullptr,
+                    nullptr, T_init, max_iters, nullptr, max_corr_dist, ctx, s, &o)) != CIL_OK)
     return st;
   double* Td = ws.at<double>(o_out);
   cil_icp_report* rd = reinterpret_cast<cil_icp_report*>(Td + 16);
@@ -361,6 +390,15 @@ cil_status cil_icp_point_to_plane(const float* src, int64_t n_src, const float* 
   cil_status dev = read_error_word(ctx, s, true);
   if (dev != CIL_OK) return dev;
   return CIL_OK;
+}
+
+cil_status cil_icp_point_to_plane(const float* src, int64_t n_src, const float* dst,
+                                  const float* dst_normals, int64_t n_dst, const double* T_init,
+                                  int max_iters, float max_corr_dist, double* T_out,
+                                  cil_icp_report* rep, void* stream) {
+  if (n_dst > 0 && !dst_normals) return CIL_ERR_INVALID_ARG;
+  return cil_icp(src, n_src, dst, dst_normals, n_dst, T_init, max_iters, max_corr_dist, nullptr,
+                 T_out, rep, stream);
 }
 
 cil_status cil_register_pair(const float* src, int64_t n_src, const float* dst, int64_t n_dst, int k,
@@ -391,7 +429,7 @@ cil_status cil_register_pair(const float* src, int64_t n_src, const float* dst, 
   if ((st = launch_normals(g, 1, n_dst, k, nullptr, viewpoint, dst, nrm, nullptr, block_of(params),
                            s)) != CIL_OK)
     return st;
-  if ((st = icp_run(ip, ws, g, src, nullptr, nrm, T_init, nullptr, max_iters, nullptr, max_corr_dist,
+  if ((st = icp_run(ip, ws, g, src, nullptr, dst, nrm, T_init, nullptr, max_iters, nullptr, max_corr_dist,
                     ctx, s)) != CIL_OK)
     return st;
   st = icp_export(ip, ws, T_out, rep, s);

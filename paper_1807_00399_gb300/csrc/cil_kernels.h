@@ -25,12 +25,24 @@ struct Mat4 {
   double m[16];
 };
 
+// Metric and correspondence search of an ICP run (CIL_METRIC_*, CIL_ASSOC_*;
+// the pixel map is the target's organised image for projective association).
+struct IcpOptions {
+  int metric = CIL_METRIC_POINT_TO_PLANE;
+  float w_point = 0.0f, w_plane = 1.0f;
+  int association = CIL_ASSOC_NEAREST;
+  const int* pixel_map = nullptr;  // device int32[height][width]: target index or -1
+  int width = 0, height = 0;
+  float fx = 0.0f, fy = 0.0f, cx = 0.0f, cy = 0.0f;
+};
+
 struct IcpPairState {
   double T[16];     // current transform (source -> target), row-major
   double rmse;      // final point-to-plane RMSE
   long long n_inl;  // final inlier count
   float Rt[12];     // T as float rows [R | t] for the association passes
   float dmax2;      // squared rejection distance
+  float ref[3];     // reference point of the pair (point-to-point sums are about it)
   int tile_begin, tile_end;
   int grp_begin;    // first tile group of the pair (groups of kIcpGroup tiles)
   int n_grp;        // tile groups of the pair
@@ -63,9 +75,11 @@ void icp_plan(IcpPlan& p, Workspace& ws, const int64_t* src_counts, int pairs);
 // identity) and run all rounds plus the final RMSE pass (three launches per
 // round).  `src_start_dev`: device int[pairs+1] (null for one pair).
 cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt,
-                   const float* src, const int* src_start_dev, const float* dst_normals,
+                   const float* src, const int* src_start_dev, const float* dst,
+                   const float* dst_normals,
                    const double* T_init_dev, const double* T_init_host, int iters,
-                   const float* dmax_dev, float dmax, DeviceCtx* ctx, cudaStream_t s);
+                   const float* dmax_dev, float dmax, DeviceCtx* ctx, cudaStream_t s,
+                   const IcpOptions* opt = nullptr);
 
 IcpPairState* icp_state(const IcpPlan& p, const Workspace& ws);
 

@@ -48,7 +48,8 @@ struct IcpArgs {
   GridView g;
   const float* src;
   const int* order;     // sorted position -> global source index
-  const float* dst_n;   // concatenated target normals
+  const float* dst;     // concatenated target points
+  const float* dst_n;   // concatenated target normals (null for point-to-point)
   const int* tile_off;  // [pairs + 1] tile prefix
   const int* src_start; // [pairs + 1] (null: one pair of n_src1 points)
   int n_src1;
@@ -56,7 +57,7 @@ struct IcpArgs {
   int n_tiles;
   int rounds;           // iterations + 1
   IcpPairState* st;
-  int* corr;            // per sorted source position: sorted target position or -1
+  int* corr;            // per sorted source position: global target index or -1
   int2* queue;          // (sorted source position, pair) of queries for k_icp_finish
   unsigned* qcount;     // [2] queue length of the rounds of each parity
   unsigned* qhead;      // [2] queue items taken
@@ -67,6 +68,7 @@ struct IcpArgs {
   float* grp_c;
   int* grp_n;
   int* grp_done;
+  IcpOptions opt;       // metric and correspondence search
 };
 
 constexpr int kDirLevels = 2;     // directory level = base level + 2 (in the cell table)
@@ -441,37 +443,146 @@ __device__ __forceinline__ void rt_from_T(const double T[16], float Rt[12]) {
     for (int b = 0; b < 4; ++b) Rt[4 * a + b] = (float)T[4 * a + b];
 }
 
+__device__ __forceinline__ double det3(double a, double b, double c, double d, double e, double f,
+                                      double g, double h, double i) {
+  return a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
+}
+
+// Closed-form rigid motion (R, t) minimising sum |R p' + t - q|^2 over the
+// round's correspondences (point-to-point metric, after Besl & McKay), FP64,
+// from the sums of a = p' - o, b = q - o (o = ref), a b^T and |a|^2 + |b|^2:
+// the rotation is the unit quaternion of the largest eigenvalue of Horn's
+// symmetric 4x4 matrix N built from the centred cross-covariance S.  N is
+// traceless, so its characteristic polynomial is l^4 + c2 l^2 + c1 l + c0
+// with c2 = -2 sum S_ij^2, c1 = -8 det S, c0 = det N; Newton's method from
+// the upper bound E0 = (sum |a - ca|^2 + sum |b - cb|^2) / 2 converges to
+// the largest root, and the eigenvector is the column of adj(N - l I) with
+// the largest diagonal cofactor.  False when the configuration does not fix
+// a rotation.
+__device__ bool closed_form_rigid(const double* tot, long long n, const float ref[3], double R[9],
+                                  double t[3]) {
+  const double inv = 1.0 / (double)n;
+  double ca[3], cb[3], S[9];
+  for (int k = 0; k < 3; ++k) {
+    ca[k] = tot[k] * inv;
+    cb[k] = tot[3 + k] * inv;
+  }
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) S[3 * k + l] = tot[6 + 3 * k + l] - (double)n * ca[k] * cb[l];
+  const double E0 = 0.5 * (tot[15] - (double)n * (ca[0] * ca[0] + ca[1] * ca[1] + ca[2] * ca[2] +
+                                                  cb[0] * cb[0] + cb[1] * cb[1] + cb[2] * cb[2]));
+  const double Sxx = S[0], Sxy = S[1], Sxz = S[2], Syx = S[3], Syy = S[4], Syz = S[5], Szx = S[6],
+               Szy = S[7], Szz = S[8];
+  const double N[16] = {Sxx + Syy + Szz, Syz - Szy,        Szx - Sxz,        Sxy - Syx,
+                        Syz - Szy,       Sxx - Syy - Szz,  Sxy + Syx,        Szx + Sxz,
+                        Szx - Sxz,       Sxy + Syx,        -Sxx + Syy - Szz, Syz + Szy,
+                        Sxy - Syx,       Szx + Sxz,        Syz + Szy,        -Sxx - Syy + Szz};
+  double ss = 0.0;
+  for (int k = 0; k < 9; ++k) ss += S[k] * S[k];
+  const double c2 = -2.0 * ss;
+  const double c1 = -8.0 * det3(Sxx, Sxy, Sxz, Syx, Syy, Syz, Szx, Szy, Szz);
+  // det N by cofactors along the first row
+  const double c0 = N[0] * det3(N[5], N[6], N[7], N[9], N[10], N[11], N[13], N[14], N[15]) -
+                    N[1] * det3(N[4], N[6], N[7], N[8], N[10], N[11], N[12], N[14], N[15]) +
+                    N[2] * det3(N[4], N[5], N[7], N[8], N[9], N[11], N[12], N[13], N[15]) -
+                    N[3] * det3(N[4], N[5], N[6], N[8], N[9], N[10], N[12], N[13], N[14]);
+  double lam = E0;
+  for (int it = 0; it < 50; ++it) {
+    const double l2 = lam * lam;
+    const double P = (l2 + c2) * l2 + c1 * lam + c0;
+    const double dP = (4.0 * l2 + 2.0 * c2) * lam + c1;
+    if (!(dP != 0.0)) break;
+    const double step = P / dP;
+    lam -= step;
+    if (fabs(step) <= 1e-14 * fabs(lam)) break;
+  }
+  double A[16];
+  for (int k = 0; k < 16; ++k) A[k] = N[k];
+  for (int k = 0; k < 4; ++k) A[5 * k] -= lam;
+  // cofactor C(i, j) of A (A symmetric, so adj(A) = C)
+  auto cof = [&](int i, int j) {
+    int r[3], c[3];
+    for (int u = 0, m = 0; u < 4; ++u)
+      if (u != i) r[m++] = u;
+    for (int u = 0, m = 0; u < 4; ++u)
+      if (u != j) c[m++] = u;
+    const double d = det3(A[4 * r[0] + c[0]], A[4 * r[0] + c[1]], A[4 * r[0] + c[2]],
+                          A[4 * r[1] + c[0]], A[4 * r[1] + c[1]], A[4 * r[1] + c[2]],
+                          A[4 * r[2] + c[0]], A[4 * r[2] + c[1]], A[4 * r[2] + c[2]]);
+    return ((i + j) & 1) ? -d : d;
+  };
+  int best = 0;
+  double dmax = -1.0;
+  for (int k = 0; k < 4; ++k) {
+    const double d = fabs(cof(k, k));
+    if (d > dmax) {
+      dmax = d;
+      best = k;
+    }
+  }
+  if (!(dmax > 1e-30 * E0 * E0 * E0) || !isfinite(dmax)) return false;
+  double qv[4];
+  for (int k = 0; k < 4; ++k) qv[k] = cof(k, best);
+  const double qn = rsqrt(qv[0] * qv[0] + qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]);
+  const double q0 = qv[0] * qn, qx = qv[1] * qn, qy = qv[2] * qn, qz = qv[3] * qn;
+  R[0] = q0 * q0 + qx * qx - qy * qy - qz * qz;
+  R[1] = 2.0 * (qx * qy - q0 * qz);
+  R[2] = 2.0 * (qx * qz + q0 * qy);
+  R[3] = 2.0 * (qy * qx + q0 * qz);
+  R[4] = q0 * q0 - qx * qx + qy * qy - qz * qz;
+  R[5] = 2.0 * (qy * qz - q0 * qx);
+  R[6] = 2.0 * (qz * qx - q0 * qy);
+  R[7] = 2.0 * (qz * qy + q0 * qx);
+  R[8] = q0 * q0 - qx * qx - qy * qy + qz * qz;
+  // q - o = R (p - o) + t' with t' = cb - R ca, so t = o + cb - R (ca + o)
+  for (int u = 0; u < 3; ++u)
+    t[u] = (double)ref[u] + cb[u] -
+           (R[3 * u] * (ca[0] + (double)ref[0]) + R[3 * u + 1] * (ca[1] + (double)ref[1]) +
+            R[3 * u + 2] * (ca[2] + (double)ref[2]));
+  return true;
+}
+
 // Round close of one pair (one thread): the final round records the RMSE and
-// inlier count; any other solves H xi = -g and left-composes the update.
-// Out of line so that its FP64 temporaries do not count against the
-// registers of the search.
+// inlier count; any other computes the round's rigid update (closed form for
+// the point-to-point metric, else the FP64 Cholesky solve of the linearised
+// normal equations) and left-composes it onto T.  Out of line so that its
+// FP64 temporaries do not count against the registers of the kernel.
 __device__ __noinline__ void close_round(IcpPairState& S, const double* tot, long long n,
-                                         bool final_round) {
+                                         bool final_round, int metric) {
   if (final_round) {
     S.n_inl = n;
     S.rmse = n > 0 ? sqrt(tot[27] / (double)n) : __longlong_as_double(0x7ff8000000000000ll);
     return;
   }
-  double H[36], g[6], xi[6];
-  int q = 0;
-  for (int u = 0; u < 6; ++u)
-    for (int v = u; v < 6; ++v) {
-      H[6 * u + v] = tot[q];
-      H[6 * v + u] = tot[q];
-      ++q;
+  double dR[9], dt[3];
+  if (metric == CIL_METRIC_POINT_TO_POINT) {
+    if (n < 3 || !closed_form_rigid(tot, n, S.ref, dR, dt)) {
+      S.status = CIL_ERR_DEGENERATE;
+      return;
     }
-  for (int u = 0; u < 6; ++u) g[u] = tot[21 + u];
-  if (n < 6 || !chol_solve6(H, g, xi)) {
-    S.status = CIL_ERR_DEGENERATE;
-    return;
+  } else {
+    double H[36], g[6], xi[6];
+    int q = 0;
+    for (int u = 0; u < 6; ++u)
+      for (int v = u; v < 6; ++v) {
+        H[6 * u + v] = tot[q];
+        H[6 * v + u] = tot[q];
+        ++q;
+      }
+    for (int u = 0; u < 6; ++u) g[u] = tot[21 + u];
+    if (n < 6 || !chol_solve6(H, g, xi)) {
+      S.status = CIL_ERR_DEGENERATE;
+      return;
+    }
+    so3_exp_d(xi, dR);
+    for (int u = 0; u < 3; ++u) dt[u] = xi[3 + u];
   }
-  double T[16], dR[9], Tn[16];
+  double T[16], Tn[16];
   for (int j = 0; j < 16; ++j) T[j] = __ldcg(&S.T[j]);
-  so3_exp_d(xi, dR);
   for (int u = 0; u < 3; ++u) {
     for (int v = 0; v < 4; ++v)
       Tn[4 * u + v] = dR[3 * u] * T[v] + dR[3 * u + 1] * T[4 + v] + dR[3 * u + 2] * T[8 + v];
-    Tn[4 * u + 3] += xi[3 + u];
+    Tn[4 * u + 3] += dt[u];
   }
   Tn[12] = 0.0;
   Tn[13] = 0.0;
@@ -485,7 +596,8 @@ __device__ __noinline__ void close_round(IcpPairState& S, const double* tot, lon
 
 __global__ void k_icp_setup(IcpPairState* st, int pairs, const int* src_start, int64_t n_src_single,
                             int* tile_off, const double* T_init, Mat4 T_host, int use_host_T,
-                            const float* dmax_dev, float dmax, int iters, float* rt_out) {
+                            const float* dmax_dev, float dmax, int iters, float* rt_out,
+                            const GridParams* prm, const float* dst) {
   // single block: tile prefix over pairs
   __shared__ int carry, gcarry;
   __shared__ int tmp[1024], gtmp[1024];
@@ -534,6 +646,9 @@ __global__ void k_icp_setup(IcpPairState* st, int pairs, const int* src_start, i
       }
       const float d = dmax_dev ? dmax_dev[b] : dmax;
       S.dmax2 = d * d;
+      // the pair's first target point (point-to-point sums are taken about it)
+      const bool has_dst = prm[b].n > 0;
+      for (int k = 0; k < 3; ++k) S.ref[k] = has_dst ? dst[3 * (int64_t)prm[b].start + k] : 0.0f;
       S.tile_begin = tmp[threadIdx.x];
       S.tile_end = tmp[threadIdx.x] + nt;
       tile_off[b] = tmp[threadIdx.x];
@@ -549,23 +664,6 @@ __global__ void k_icp_setup(IcpPairState* st, int pairs, const int* src_start, i
     __syncthreads();
   }
   if (threadIdx.x == 0) tile_off[pairs] = carry;
-}
-
-// Operands of sum q of the normal equations in a row (J0..J5, r):
-// q = 0..20 the upper triangle of J J^T row by row, 21..26 J r, 27 r r.
-__device__ __forceinline__ void q_operands(int q, int& ia, int& ib) {
-  if (q >= 21) {
-    ia = q == 27 ? 6 : q - 21;
-    ib = 6;
-    return;
-  }
-  int u = 0, base = 0;
-  while (q >= base + 6 - u) {
-    base += 6 - u;
-    ++u;
-  }
-  ia = u;
-  ib = u + (q - base);
 }
 
 constexpr int kRowChunks = 8;  // chunks of a tile's rows summed in parallel
@@ -603,6 +701,26 @@ __device__ __forceinline__ void transformed_source(const IcpArgs& a, const float
   p[2] = fmaf(Rt[8], x, fmaf(Rt[9], y, fmaf(Rt[10], z, Rt[11])));
 }
 
+// Projective data association (Sec. 3): the target is the organised image of
+// its camera (target coordinates = camera frame, pinhole fx, fy, cx, cy); p'
+// projects to the pixel round-half-even(f x / z + c), and the target point
+// seen there is the correspondence when |p' - q| <= d_max.  Returns its
+// global index or -1.
+__device__ __forceinline__ int projective_match(const IcpArgs& a, int dst_start, const float p[3],
+                                                float dmax2) {
+  const IcpOptions& o = a.opt;
+  if (!(p[2] > 0.0f)) return -1;
+  const float u = rintf(__fdiv_rn(o.fx * p[0], p[2]) + o.cx);
+  const float v = rintf(__fdiv_rn(o.fy * p[1], p[2]) + o.cy);
+  if (!(u >= 0.0f && u < (float)o.width && v >= 0.0f && v < (float)o.height)) return -1;
+  const int k = __ldg(o.pixel_map + (int64_t)v * o.width + (int64_t)u);
+  if (k < 0) return -1;
+  const int64_t j = dst_start + (int64_t)k;
+  const float d2 = sqdist(__ldg(a.dst + 3 * j), __ldg(a.dst + 3 * j + 1), __ldg(a.dst + 3 * j + 2),
+                          p[0], p[1], p[2]);
+  return d2 <= dmax2 ? (int)j : -1;
+}
+
 // Stage one of round `round` for the tile blockIdx.x.
 __global__ void __launch_bounds__(kIcpThreads) k_icp_search(IcpArgs a, int round) {
   __shared__ float s_Rt[12];
@@ -624,15 +742,21 @@ __global__ void __launch_bounds__(kIcpThreads) k_icp_search(IcpArgs a, int round
   const int sb = a.src_start ? __ldg(a.src_start + b) : 0;
   const int se = a.src_start ? __ldg(a.src_start + b + 1) : a.n_src1;
   const int pos = sb + (tt - tb) * kTileSrc + tid;
+  const int dst_start = a.g.prm[b].start;
   bool queued = false;
   if (pos < se) {
     float p[3];
     transformed_source(a, s_Rt, pos, p);
-    u64 best;
-    int bj;
-    float lim;
-    queued = !base_search(a.g, b, p, s_dmax2, best, bj, lim);
-    a.corr[pos] = bj;  // final, or stage one's best for k_icp_finish
+    if (a.opt.association == CIL_ASSOC_PROJECTIVE) {
+      a.corr[pos] = projective_match(a, dst_start, p, s_dmax2);
+    } else {
+      u64 best;
+      int bj;
+      float lim;
+      queued = !base_search(a.g, b, p, s_dmax2, best, bj, lim);
+      // final, or stage one's best for k_icp_finish
+      a.corr[pos] = best == kEmptyKey ? -1 : dst_start + key_idx(best);
+    }
   }
   // warp-aggregated append to the queue
   const unsigned m = __ballot_sync(0xffffffffu, queued);
@@ -654,13 +778,14 @@ __device__ __forceinline__ void queued_query(const IcpArgs& a, int pos, int b, f
   for (int j = 0; j < 12; ++j) Rt[j] = a.st[b].Rt[j];
   dmax2 = a.st[b].dmax2;
   transformed_source(a, Rt, pos, q);
-  bj = a.corr[pos];
+  const int j = a.corr[pos];
+  bj = -1;
   best = kEmptyKey;
   lim = dmax2;
-  if (bj >= 0) {
-    const float4 qp = __ldg(a.g.pts + bj);
-    lim = sqdist(qp.x, qp.y, qp.z, q[0], q[1], q[2]);
-    best = pack_key(lim, __float_as_int(qp.w));
+  if (j >= 0) {
+    lim = sqdist(__ldg(a.dst + 3 * (int64_t)j), __ldg(a.dst + 3 * (int64_t)j + 1),
+                 __ldg(a.dst + 3 * (int64_t)j + 2), q[0], q[1], q[2]);
+    best = pack_key(lim, j - a.g.prm[b].start);
   }
   const GridParams& P = a.g.prm[b];
   CellFrame f;
@@ -699,7 +824,7 @@ __global__ void __launch_bounds__(kIcpThreads) k_icp_finish(IcpArgs a, int round
         queued_query(a, e.x, e.y, q, dmax2, best, bj, lim, c);
         if (!lane_directory(a.g, e.y, q, dmax2, c, best, bj, lim))
           escalate_rings(a.g, e.y, q, dmax2, best, bj, lim);
-        a.corr[e.x] = bj;
+        a.corr[e.x] = best == kEmptyKey ? -1 : a.g.prm[e.y].start + key_idx(best);
       }
     }
     return;
@@ -719,17 +844,110 @@ __global__ void __launch_bounds__(kIcpThreads) k_icp_finish(IcpArgs a, int round
       // a ball spanning many directory cells (large rejection distance)
       if (lane == 0) escalate_rings(a.g, e.y, q, dmax2, best, bj, lim);
     }
-    if (lane == 0) a.corr[e.x] = bj;
+    if (lane == 0) a.corr[e.x] = best == kEmptyKey ? -1 : a.g.prm[e.y].start + key_idx(best);
     __syncwarp();
   }
 }
 
+// Operand pair (qa(q), qb(q)) of sum q of the linearised metrics, in a row
+// (J0..J5, r = element 6): q = 0..20 the upper triangle of H row by row,
+// 21..26 g, 27 r r (constant-folded wherever q is).
+__host__ __device__ constexpr int qa(int q) {
+  return q < 6 ? 0 : q < 11 ? 1 : q < 15 ? 2 : q < 18 ? 3 : q < 20 ? 4 : q < 21 ? 5
+       : q < 27 ? q - 21 : 6;
+}
+__host__ __device__ constexpr int qb(int q) {
+  return q < 6 ? q : q < 11 ? q - 5 : q < 15 ? q - 9 : q < 18 ? q - 12 : q < 20 ? q - 14
+       : q < 21 ? 5 : 6;
+}
+static_assert(qa(20) == 5 && qb(20) == 5 && qa(14) == 2 && qb(14) == 5 && qa(26) == 5 &&
+                  qb(26) == 6 && qa(27) == 6 && qb(27) == 6 && qa(7) == 1 && qb(7) == 2,
+              "operand order");
+
+// Term q of the point-to-point rows [-[p']x | I] (per coordinate) in the q
+// order of the linearised metrics: H = [[|p|^2 I - p p^T, [p]x], [[p]x^T, I]],
+// g = [p x d; d], and |d|^2 (d = p' - q).
+__device__ __forceinline__ float point_row_term(int q, const float p[3], float pp, const float d[3]) {
+  switch (q) {
+    case 0: return pp - p[0] * p[0];
+    case 1: return -p[0] * p[1];
+    case 2: return -p[0] * p[2];
+    case 4: return -p[2];
+    case 5: return p[1];
+    case 6: return pp - p[1] * p[1];
+    case 7: return -p[1] * p[2];
+    case 8: return p[2];
+    case 10: return -p[0];
+    case 11: return pp - p[2] * p[2];
+    case 12: return -p[1];
+    case 13: return p[0];
+    case 15: case 18: case 20: return 1.0f;
+    case 21: return p[1] * d[2] - p[2] * d[1];
+    case 22: return p[2] * d[0] - p[0] * d[2];
+    case 23: return p[0] * d[1] - p[1] * d[0];
+    case 24: return d[0];
+    case 25: return d[1];
+    case 26: return d[2];
+    case 27: return fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
+    default: return 0.0f;
+  }
+}
+
+// One correspondence's contribution to the round's 28 sums, written to
+// column u of sc; returns 1 if it counts (0: a plane metric and a non-finite
+// target normal, and then nothing is written).
+//  point-to-plane  products of the row (J, r), J = [p' x n, n], r = n.(p' - q);
+//  combination     w_plane x those + w_point x point_row_term;
+//  point-to-point  0..2 a, 3..5 b, 6..14 a_i b_j, 15 |a|^2 + |b|^2, 27 |d|^2
+//                  with a = p' - o, b = q - o about the pair's reference
+//                  point o (the sums of the closed form); the rest 0.
+__device__ __forceinline__ int point_contribution(const IcpArgs& a, int b, const float p[3],
+                                                  const float qv[3], int j,
+                                                  float (*sc)[kTileSrc + 8], int u) {
+  const IcpOptions& o = a.opt;
+  const float d[3] = {p[0] - qv[0], p[1] - qv[1], p[2] - qv[2]};
+  if (o.metric == CIL_METRIC_POINT_TO_POINT) {
+    const float* ref = a.st[b].ref;
+    const float av[3] = {p[0] - ref[0], p[1] - ref[1], p[2] - ref[2]};
+    const float bv[3] = {qv[0] - ref[0], qv[1] - ref[1], qv[2] - ref[2]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      sc[k][u] = av[k];
+      sc[3 + k][u] = bv[k];
+#pragma unroll
+      for (int l = 0; l < 3; ++l) sc[6 + 3 * k + l][u] = av[k] * bv[l];
+    }
+    sc[15][u] = fmaf(av[0], av[0], fmaf(av[1], av[1], av[2] * av[2])) +
+                fmaf(bv[0], bv[0], fmaf(bv[1], bv[1], bv[2] * bv[2]));
+#pragma unroll
+    for (int q = 16; q < kIcpQ - 1; ++q) sc[q][u] = 0.0f;
+    sc[27][u] = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
+    return 1;
+  }
+  const float nx = __ldg(a.dst_n + 3 * (int64_t)j), ny = __ldg(a.dst_n + 3 * (int64_t)j + 1),
+              nz = __ldg(a.dst_n + 3 * (int64_t)j + 2);
+  if (!(isfinite(nx) && isfinite(ny) && isfinite(nz))) return 0;
+  const float row[7] = {p[1] * nz - p[2] * ny, p[2] * nx - p[0] * nz, p[0] * ny - p[1] * nx,
+                        nx, ny, nz, nx * d[0] + ny * d[1] + nz * d[2]};
+  if (o.metric == CIL_METRIC_COMBINED) {
+    const float wl = o.w_plane, wp = o.w_point;
+    const float pp = fmaf(p[0], p[0], fmaf(p[1], p[1], p[2] * p[2]));
+#pragma unroll
+    for (int q = 0; q < kIcpQ; ++q)
+      sc[q][u] = fmaf(wp, point_row_term(q, p, pp, d), wl * __fmul_rn(row[qa(q)], row[qb(q)]));
+  } else {
+#pragma unroll
+    for (int q = 0; q < kIcpQ; ++q) sc[q][u] = __fmul_rn(row[qa(q)], row[qb(q)]);
+  }
+  return 1;
+}
+
 // Stage three of round `round` for the tile blockIdx.x: rows, tile sums,
 // group reduction and, in the last block of a pair, the round's solve.
-__global__ void __launch_bounds__(kIcpThreads) k_icp_accumulate(IcpArgs a, int round) {
+__global__ void __launch_bounds__(kIcpThreads, 4) k_icp_accumulate(IcpArgs a, int round) {
   __shared__ float s_Rt[12];
   __shared__ int s_pair, s_last, s_gid, s_g0, s_gsize;
-  __shared__ float s_row[7][kTileSrc + 8];  // J (6) and r per tile point; +8 spreads banks
+  __shared__ float s_c[kIcpQ][kTileSrc + 8];  // contributions per tile point; +8 spreads banks
   __shared__ float s_ps[kIcpQ][kRowChunks], s_pc[kIcpQ][kRowChunks];
   __shared__ double sm_tot[kIcpQ];
   __shared__ long long sm_cnt;
@@ -753,44 +971,31 @@ __global__ void __launch_bounds__(kIcpThreads) k_icp_accumulate(IcpArgs a, int r
   const int tb = __ldg(a.tile_off + b);
   const int sb = a.src_start ? __ldg(a.src_start + b) : 0;
   const int se = a.src_start ? __ldg(a.src_start + b + 1) : a.n_src1;
-  const int dst_start = a.g.prm[b].start;
   const int pos = sb + (tt - tb) * kTileSrc + tid;
-  // the residual and Jacobian row of the thread's point (zeros where there
-  // is no correspondence)
-  float row[7] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  // the thread's contribution to the round's 28 sums (zeros where there is
+  // no correspondence)
   int cnt = 0;
-  const int bj = pos < se ? a.corr[pos] : -1;
-  if (bj >= 0) {
+  const int j = pos < se ? a.corr[pos] : -1;
+  if (j >= 0) {
     float p[3];
     transformed_source(a, s_Rt, pos, p);
-    const float4 qp = __ldg(a.g.pts + bj);
-    const int64_t j = dst_start + (int64_t)__float_as_int(qp.w);
-    const float nx = __ldg(a.dst_n + 3 * j), ny = __ldg(a.dst_n + 3 * j + 1),
-                nz = __ldg(a.dst_n + 3 * j + 2);
-    if (isfinite(nx) && isfinite(ny) && isfinite(nz)) {
-      row[0] = p[1] * nz - p[2] * ny;
-      row[1] = p[2] * nx - p[0] * nz;
-      row[2] = p[0] * ny - p[1] * nx;
-      row[3] = nx;
-      row[4] = ny;
-      row[5] = nz;
-      row[6] = nx * (p[0] - qp.x) + ny * (p[1] - qp.y) + nz * (p[2] - qp.z);
-      cnt = 1;
-    }
+    const float qv[3] = {__ldg(a.dst + 3 * (int64_t)j), __ldg(a.dst + 3 * (int64_t)j + 1),
+                         __ldg(a.dst + 3 * (int64_t)j + 2)};
+    cnt = point_contribution(a, b, p, qv, j, s_c, tid);
   }
+  if (!cnt) {
 #pragma unroll
-  for (int k = 0; k < 7; ++k) s_row[k][tid] = row[k];
+    for (int q = 0; q < kIcpQ; ++q) s_c[q][tid] = 0.0f;
+  }
   const int tile_cnt = __syncthreads_count(cnt);
-  // the tile's 21 + 6 + 1 sums: item (q, ch) adds the products of rows
-  // ch, ch + kRowChunks, ... in that order (compensated), then the chunks are
-  // merged in order -- a fixed order, so the result is deterministic
+  // the tile's 28 sums: item (q, ch) adds rows ch, ch + kRowChunks, ... of
+  // quantity q in that order (compensated), then the chunks are merged in
+  // order -- a fixed order, so the result is deterministic
   for (int w = tid; w < kIcpQ * kRowChunks; w += kIcpThreads) {
     const int q = w / kRowChunks, ch = w - q * kRowChunks;
-    int ia, ib;
-    q_operands(q, ia, ib);
     KSum t;
     t.zero();
-    for (int i = ch; i < kTileSrc; i += kRowChunks) t.add(__fmul_rn(s_row[ia][i], s_row[ib][i]));
+    for (int i = ch; i < kTileSrc; i += kRowChunks) t.add(s_c[q][i]);
     s_ps[q][ch] = t.s;
     s_pc[q][ch] = t.c;
   }
@@ -890,7 +1095,7 @@ __global__ void __launch_bounds__(kIcpThreads) k_icp_accumulate(IcpArgs a, int r
   __syncthreads();
   if (tid == 0) {
     IcpPairState& S = a.st[b];
-    close_round(S, sm_tot, sm_cnt, round == a.rounds - 1);
+    close_round(S, sm_tot, sm_cnt, round == a.rounds - 1, a.opt.metric);
     S.tiles_done = 0;
   }
 }
@@ -967,9 +1172,10 @@ IcpPairState* icp_state(const IcpPlan& p, const Workspace& ws) {
 }
 
 cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt, const float* src,
-                   const int* src_start_dev, const float* dst_normals, const double* T_init_dev,
-                   const double* T_init_host, int iters, const float* dmax_dev, float dmax,
-                   DeviceCtx* ctx, cudaStream_t s) {
+                   const int* src_start_dev, const float* dst, const float* dst_normals,
+                   const double* T_init_dev, const double* T_init_host, int iters,
+                   const float* dmax_dev, float dmax, DeviceCtx* ctx, cudaStream_t s,
+                   const IcpOptions* opt) {
   Mat4 Th;
   for (int j = 0; j < 16; ++j) Th.m[j] = T_init_host ? T_init_host[j] : 0.0;
   IcpPairState* st = ws.at<IcpPairState>(p.o_state);
@@ -978,7 +1184,7 @@ cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt, c
   unsigned* qc = ws.at<unsigned>(p.o_qc);
   note_launches(1);
   k_icp_setup<<<1, 1024, 0, s>>>(st, p.pairs, src_start_dev, p.n_src, tile_off, T_init_dev, Th,
-                                 T_init_host != nullptr, dmax_dev, dmax, iters, rt);
+                                 T_init_host != nullptr, dmax_dev, dmax, iters, rt, tgt.prm, dst);
   if (cudaMemsetAsync(qc, 0, sizeof(unsigned) * 4, s) != cudaSuccess) return CIL_ERR_CUDA;
   if (cudaMemsetAsync(ws.at<int>(p.o_grp_done), 0,
                       sizeof(int) * (size_t)(p.n_groups > 0 ? p.n_groups : 1), s) != cudaSuccess)
@@ -991,7 +1197,9 @@ cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt, c
   a.g = tgt;
   a.src = src;
   a.order = order;
+  a.dst = dst;
   a.dst_n = dst_normals;
+  a.opt = opt ? *opt : IcpOptions();
   a.tile_off = tile_off;
   a.src_start = src_start_dev;
   a.n_src1 = (int)p.n_src;

@@ -8,7 +8,8 @@ Workloads: surface (10,000-point wavy surface pair), depth (640x480 depth
 frames, ~3.07e5 points), lidar (64 x 2048 sweep, ~1.2e5 returns), batch (256
 surface pairs with sizes log-uniform in [2e3, 2e5]).  Ops: register (grid,
 k-NN normals and point-to-plane ICP), knn (self k-NN), normals, radius
-(radius search), batch (the batched graph run; workload batch only).  Each op
+(radius search), icp (ICP alone on library normals, with --metric and
+--association), batch (the batched graph run; workload batch only).  Each op
 runs --repeat times after one warm-up call; the CUDA-event time per call and
 the per-kernel times recorded by the library (not inside graph replays) are
 printed as one JSON line.
@@ -24,13 +25,17 @@ import sys
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_1807_00399_gb300.profile_run")
     ap.add_argument("--workload", choices=["surface", "depth", "lidar", "batch"], default="depth")
-    ap.add_argument("--op", choices=["register", "knn", "normals", "radius", "batch"],
+    ap.add_argument("--op", choices=["register", "knn", "normals", "radius", "batch", "icp"],
                     default="register")
     ap.add_argument("--iters", type=int, default=30, help="ICP iterations")
     ap.add_argument("--k", type=int, default=0, help="neighbours (default: 16 lidar, else 10)")
     ap.add_argument("--radius", type=float, default=0.5)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--metric", choices=["point_to_plane", "point_to_point", "combined"],
+                    default=None, help="op icp: the ICP metric (default point_to_plane)")
+    ap.add_argument("--association", choices=["nearest", "projective"], default="nearest",
+                    help="op icp: correspondence search (projective: depth workload only)")
     ap.add_argument("--no-regions", action="store_true",
                     help="time the calls only (no per-kernel event records between launches)")
     a = ap.parse_args(argv)
@@ -57,7 +62,22 @@ def main(argv=None):
         dst = torch.from_numpy(p.target).cuda()
         nrm = torch.empty_like(dst)
         vp = p.viewpoint
+        icp_kw = {}
+        if a.op == "icp":
+            # target normals from the library, then ICP alone with the chosen variant
+            nrm, _ = cil.estimate_normals(dst, k, vp)
+            icp_kw = {"metric": a.metric or "point_to_plane", "association": a.association,
+                      "w_point": 0.1, "w_plane": 1.0}
+            if a.association == "projective":
+                if a.workload != "depth":
+                    raise SystemExit("projective association needs the depth workload")
+                w, h = p.meta["w"], p.meta["h"]
+                pm = torch.full((w * h,), -1, dtype=torch.int32)
+                pm[torch.from_numpy(p.meta["target_pixels"]).long()] = torch.arange(
+                    len(p.target), dtype=torch.int32)
+                icp_kw.update(pixel_map=pm.reshape(h, w).cuda(), intrinsics=p.meta["intrinsics"])
         fn = {
+            "icp": lambda: cil.icp(src, dst, nrm, iters=a.iters, max_corr_dist=dmax, **icp_kw),
             "register": lambda: cil.register_pair(src, dst, k, vp, a.iters, dmax, out_normals=nrm),
             "knn": lambda: cil.knn(dst, dst, k),
             "normals": lambda: cil.estimate_normals(dst, k, vp),
