@@ -354,6 +354,9 @@ def run_ours(args):
     learned_res = None
     if not args.no_learned:
         learned_res = run_learned(args, rank)
+    variants = None
+    if not args.no_variants:
+        variants = run_variants(args, rank)
 
     # ---- CPU baseline (oracle, rank 0, N = 1 only) ----
     cpu = None
@@ -390,6 +393,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "batched": batched,
             "learned": learned_res,
+            "icp_variants": variants,
             "gpu_launches": int(n1 - n0),
             "clocks": clocks,
         }
@@ -481,6 +485,49 @@ def run_batched(args, rank: int, B: int = 256, runs: int = 5):
             "median_rot_err_deg_vs_generator": float(np.median(rot_err))}
 
 
+def run_variants(args, rank: int, reps: int = 5):
+    """The ICP variants of Sec. 3 on the depth-frame pair (cil_icp: target grid
+    + 30 rounds + final pass per call, normals given): median ms per call for
+    each metric with nearest-neighbour association, and point-to-plane /
+    point-to-point with projective association on the target's pixel grid."""
+    import torch
+
+    import paper_1807_00399_gb300 as cil
+    from paper_1807_00399_gb300 import synth
+
+    pair = synth.depth_frame_pair(args.seed + rank)
+    src = torch.from_numpy(pair.source).cuda()
+    dst = torch.from_numpy(pair.target).cuda()
+    nrm, _ = cil.estimate_normals(dst, K_NN, pair.viewpoint)
+    w, h = pair.meta["w"], pair.meta["h"]
+    pm = torch.full((w * h,), -1, dtype=torch.int32)
+    pm[torch.from_numpy(pair.meta["target_pixels"]).long()] = torch.arange(len(pair.target),
+                                                                           dtype=torch.int32)
+    pm = pm.reshape(h, w).cuda()
+    out = {}
+    for metric in ("point_to_plane", "point_to_point", "combined"):
+        for assoc in ("nearest", "projective"):
+            if assoc == "projective" and metric == "combined":
+                continue
+            kw = dict(metric=metric, association=assoc, w_point=0.1, w_plane=1.0)
+            if assoc == "projective":
+                kw.update(pixel_map=pm, intrinsics=pair.meta["intrinsics"])
+            cil.icp(src, dst, nrm, iters=ICP_ITERS, max_corr_dist=DMAX, **kw)
+            ms = []
+            rep = None
+            for _ in range(reps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                _, rep = cil.icp(src, dst, nrm, iters=ICP_ITERS, max_corr_dist=DMAX, **kw)
+                b.record()
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            out[f"{metric}/{assoc}"] = {"ms_per_pair": float(np.median(ms)), "rmse": rep["rmse"],
+                                        "n_inliers": rep["n_inliers"]}
+    return out
+
+
 def run_learned(args, rank: int, B: int = 256):
     """Learned warm start + batched ICP against batched ICP from identity on
     256 held-out pairs (10,000-point wavy surfaces, rotations up to 90 deg,
@@ -512,6 +559,8 @@ def main():
                     help="skip the 256-pair batched-vs-sequential measurement")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned warm-start measurement")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the ICP-variant timings")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
