@@ -63,7 +63,8 @@ typedef enum {
  *   cell_size   > 0: grid cell edge in input units (rounded to the nearest
  *               power-of-two multiple of the cloud's fine Morton resolution,
  *               max_extent / 1023); 0: chosen from the data.
- *   cell_scale  multiplier applied to the data-driven cell size (0 = 1.0).
+ *   cell_scale  multiplier applied to the data-driven cell size (the median
+ *               distance of sampled points to their k-th neighbour; 0 = 1.5).
  *   block       threads per block of the query kernels (0 = default 128;
  *               64, 128, 256 accepted). */
 typedef struct {

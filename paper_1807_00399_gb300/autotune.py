@@ -2,9 +2,10 @@
 
 Searches the grid cell-size multiplier (the cell edge is the nearest
 power-of-two multiple of each cloud's fine lattice to scale x the data-driven
-neighbourhood radius, so scales 0.5 / 1 / 2 select the levels one below, at
-and one above the estimate) and the query-kernel block size, timing whole
-batch runs with CUDA events.  The winner is cached as JSON keyed by GPU name
+neighbourhood radius, so scales 1 / 1.5 / 2 select the estimate's level or
+the one above, depending on where the estimate falls between two levels; 1.5
+is the library default) and the query-kernel block size, timing whole batch
+runs with CUDA events.  The winner is cached as JSON keyed by GPU name
 and a size bucket (pairs rounded up to a power of two, mean cloud size to the
 nearest power of two, k, rounds), in $CIL_TUNE_CACHE or
 ~/.cache/cil_gb300/tuning.json.
@@ -17,7 +18,7 @@ import os
 
 import numpy as np
 
-SCALES = (0.5, 1.0, 2.0)
+SCALES = (1.0, 1.5, 2.0)
 BLOCKS = (64, 128, 256)
 
 

@@ -44,7 +44,7 @@ static cil_status enqueue_batch(BatchHandle* h, const float* src, const float* d
   GridOptions opt;
   opt.k_est = h->prm.k;
   opt.cell_size = h->prm.tune.cell_size > 0.0f ? h->prm.tune.cell_size : 0.0f;
-  opt.cell_scale = h->prm.tune.cell_scale > 0.0f ? h->prm.tune.cell_scale : 1.0f;
+  opt.cell_scale = h->prm.tune.cell_scale > 0.0f ? h->prm.tune.cell_scale : kDefaultCellScale;
   cil_status st = grid_build(h->gp, h->ws, dst, dst_start, opt, h->ctx, s);
   if (st != CIL_OK) return st;
   const GridView g = grid_view(h->gp, h->ws);

@@ -134,7 +134,7 @@ static GridOptions grid_options(const cil_params* prm, int k) {
   o.k_est = k;
   if (prm) {
     o.cell_size = prm->cell_size > 0.0f ? prm->cell_size : 0.0f;
-    o.cell_scale = prm->cell_scale > 0.0f ? prm->cell_scale : 1.0f;
+    o.cell_scale = prm->cell_scale > 0.0f ? prm->cell_scale : kDefaultCellScale;
   }
   return o;
 }

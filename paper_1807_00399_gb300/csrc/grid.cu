@@ -516,7 +516,7 @@ __global__ void __launch_bounds__(1024) k_choose_level(GridParams* prm, const fl
     } else {
       const float med = ns > 0 ? est[ns / 2] : __int_as_float(0x7f800000);
       const float R = isfinite(med) ? sqrtf(med) : fine * (float)kFineDim;
-      target = (cell_scale > 0.0f ? cell_scale : 1.0f) * R;
+      target = (cell_scale > 0.0f ? cell_scale : kDefaultCellScale) * R;
     }
     const float ratio = target / fine;
     int L = ratio <= 1.0f ? 0 : (int)rintf(log2f(ratio));

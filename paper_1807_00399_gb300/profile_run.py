@@ -30,6 +30,8 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=30, help="ICP iterations")
     ap.add_argument("--k", type=int, default=0, help="neighbours (default: 16 lidar, else 10)")
     ap.add_argument("--radius", type=float, default=0.5)
+    ap.add_argument("--cell-scale", type=float, default=0.0,
+                    help="grid cell-size multiplier (0: the library default)")
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--metric", choices=["point_to_plane", "point_to_point", "combined"],
@@ -78,9 +80,10 @@ def main(argv=None):
                 icp_kw.update(pixel_map=pm.reshape(h, w).cuda(), intrinsics=p.meta["intrinsics"])
         fn = {
             "icp": lambda: cil.icp(src, dst, nrm, iters=a.iters, max_corr_dist=dmax, **icp_kw),
-            "register": lambda: cil.register_pair(src, dst, k, vp, a.iters, dmax, out_normals=nrm),
-            "knn": lambda: cil.knn(dst, dst, k),
-            "normals": lambda: cil.estimate_normals(dst, k, vp),
+            "register": lambda: cil.register_pair(src, dst, k, vp, a.iters, dmax, out_normals=nrm,
+                                                  cell_scale=a.cell_scale),
+            "knn": lambda: cil.knn(dst, dst, k, cell_scale=a.cell_scale),
+            "normals": lambda: cil.estimate_normals(dst, k, vp, cell_scale=a.cell_scale),
             "radius": lambda: cil.radius_search(dst, dst, a.radius),
         }[a.op]
     L = cil.lib()
