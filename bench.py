@@ -357,6 +357,9 @@ def run_ours(args):
     variants = None
     if not args.no_variants:
         variants = run_variants(args, rank)
+    segmentation = None
+    if not args.no_segmentation:
+        segmentation = run_segmentation(args, rank)
 
     # ---- CPU baseline (oracle, rank 0, N = 1 only) ----
     cpu = None
@@ -394,6 +397,7 @@ def run_ours(args):
             "batched": batched,
             "learned": learned_res,
             "icp_variants": variants,
+            "smooth_segmentation": segmentation,
             "gpu_launches": int(n1 - n0),
             "clocks": clocks,
         }
@@ -528,6 +532,45 @@ def run_variants(args, rank: int, reps: int = 5):
     return out
 
 
+def run_segmentation(args, rank: int, reps: int = 3):
+    """Smooth segmentation of an apartment-scale scan (Sec. 4's first test:
+    5 mm voxel grid, k = 30 normals, connected components of the k = 30
+    graph under a 2.8 rad normal angle), on a synthetic stand-in for the
+    scan: 7.8M points on a furnished flat, resident on the device.  Median ms
+    per call of each stage and of the chain."""
+    import torch
+
+    import paper_1807_00399_gb300 as cil
+    from paper_1807_00399_gb300 import synth
+
+    P = torch.from_numpy(synth.apartment_scene(args.seed + rank)).cuda()
+    vp = synth.APARTMENT_VIEWPOINT
+
+    def chain():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record()
+        v, _ = cil.voxel_downsample(P, 0.005)
+        ev[1].record()
+        nrm, _ = cil.estimate_normals(v, 30, vp, with_curvature=False)
+        ev[2].record()
+        lab, nc = cil.segment(v, nrm, k=30, theta=2.8)
+        ev[3].record()
+        torch.cuda.synchronize()
+        return [ev[i].elapsed_time(ev[i + 1]) for i in range(3)], v, lab, nc
+
+    chain()
+    runs = [chain() for _ in range(reps)]
+    ms = np.array([r[0] for r in runs])
+    _, v, lab, nc = runs[-1]
+    sizes = torch.bincount(lab.long(), minlength=1)
+    return {"workload": f"apartment-scale scan stand-in, {P.shape[0]} points -> {v.shape[0]} voxels "
+                        f"(5 mm), k=30, theta=2.8 rad",
+            "ms_voxel": float(np.median(ms[:, 0])), "ms_normals": float(np.median(ms[:, 1])),
+            "ms_segment": float(np.median(ms[:, 2])), "ms_total": float(np.median(ms.sum(1))),
+            "segments": nc, "segments_ge_100_points": int((sizes >= 100).sum().item()),
+            "paper_cpu_s_context": 3.65}
+
+
 def run_learned(args, rank: int, B: int = 256):
     """Learned warm start + batched ICP against batched ICP from identity on
     256 held-out pairs (10,000-point wavy surfaces, rotations up to 90 deg,
@@ -561,6 +604,8 @@ def main():
                     help="skip the learned warm-start measurement")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the ICP-variant timings")
+    ap.add_argument("--no-segmentation", action="store_true",
+                    help="skip the apartment-scale smooth-segmentation timing")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -239,6 +239,29 @@ cil_status cil_register_pair(const float *src, int64_t n_src, const float *dst, 
                              cil_icp_report *rep, const cil_params *params, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Connected-component segmentation on the k-NN graph (Sec. 3: connected
+ * components under a point-wise similarity, e.g. smooth segments; Sec. 4
+ * segments a reconstruction with k = 30 and a normal-angle threshold).
+ *   xyz, normals  device float[n][3] (oriented unit normals, e.g. from
+ *                 cil_estimate_normals; a point with a non-finite normal has
+ *                 no edge)
+ *   k             neighbours per point, self included (1..CIL_MAX_K)
+ *   theta         normal-angle threshold in radians (>= 0): i and j are
+ *                 joined when j is among the k nearest of i (or i of j) and
+ *                 n_i . n_j >= cos(theta)
+ *   radius        > 0: additionally |p_i - p_j| <= radius; 0: no distance test
+ *   out_labels    device int32[n]: the smallest point index of each point's
+ *                 component
+ *   out_count     host: number of components
+ * The similarity tests are evaluated in FP32 ((x x + y y) + z z, no fused
+ * multiply-add, thresholds rounded to FP32).  Synchronises the stream.
+ * CIL_ERR_INVALID_ARG for bad sizes, k, theta or radius, or null pointers;
+ * CIL_ERR_NONFINITE for non-finite coordinates.
+ * ------------------------------------------------------------------------- */
+cil_status cil_segment(const float *xyz, const float *normals, int64_t n, int k, float theta,
+                       float radius, int32_t *out_labels, int64_t *out_count, void *stream);
+
+/* ---------------------------------------------------------------------------
  * ICP variants (Sec. 3: the ICP loop parameterised by the correspondence
  * search and the estimator; rigid registration under the point-to-point
  * metric (Besl & McKay), the point-to-plane metric (Low) and weighted

@@ -18,7 +18,7 @@ import numpy as np
 __all__ = [
     "CilError", "lib", "knn", "radius_search", "estimate_normals", "icp_point_to_plane",
     "register_pair", "sync_status", "Params", "STATUS", "MAX_K", "IcpReport", "Batch", "icp",
-    "IcpOptions",
+    "IcpOptions", "segment",
     "decode_report", "decode_reports",
 ]
 
@@ -77,6 +77,7 @@ def lib():
         L.cil_estimate_normals_ex.argtypes = [P, I64, I, P, P, P, P, P]
         L.cil_icp_point_to_plane.argtypes = [P, I64, P, P, I64, P, I, F, P, P, P]
         L.cil_icp.argtypes = [P, I64, P, P, I64, P, I, F, P, P, P, P]
+        L.cil_segment.argtypes = [P, P, I64, I, F, F, P, P, P]
         L.cil_register_pair.argtypes = [P, I64, P, I64, I, P, P, I, F, P, P, P, P, P]
         L.cil_icp_batch_create.argtypes = [P, P, I, P, P]
         L.cil_icp_batch_run.argtypes = [P, P, P, P, P, P, P, P]
@@ -348,6 +349,23 @@ def icp(src, dst, dst_normals=None, T_init=None, iters: int = 20, max_corr_dist:
     return np.array(Tout[:], np.float64).reshape(4, 4), {
         "rmse": rep.rmse, "n_inliers": int(rep.n_inliers), "iters_done": rep.iters_done,
         "status": rep.status}
+
+
+def segment(xyz, normals, k: int = 30, theta: float = 2.8, radius: float = 0.0, stream=None):
+    """Connected components of the k-NN graph under the normal-angle (and
+    optional distance) similarity (cil_segment).  Returns (labels int32 CUDA
+    tensor: smallest index of each point's component, number of components)."""
+    torch = _torch()
+    xyz = _points(xyz, "xyz")
+    nrm = _points(normals, "normals")
+    if nrm.shape != xyz.shape:
+        raise ValueError("normals must match xyz")
+    labels = torch.empty(xyz.shape[0], dtype=torch.int32, device=xyz.device)
+    count = ctypes.c_int64()
+    st = lib().cil_segment(_ptr(xyz), _ptr(nrm), xyz.shape[0], int(k), float(theta), float(radius),
+                           _ptr(labels), ctypes.byref(count), _stream(stream))
+    _check(st, "cil_segment")
+    return labels, int(count.value)
 
 
 def register_pair(src, dst, k: int, viewpoint, iters: int, max_corr_dist: float, *,

@@ -18,6 +18,12 @@ cil_status launch_knn_hybrid(const GridView& g, const float* qry, int64_t nq, co
 cil_status launch_normals_radius(const GridView& g, int64_t n, float r, const float* vp_host,
                                  float* out_n, float* out_c, int* out_cnt, cudaStream_t s);
 
+// connected-component segmentation over k-NN edges (segment.cu): labels =
+// smallest index of each component, count = number of components
+cil_status launch_segment(const int* knn_idx, int k, const float* xyz, const float* nrm, int64_t n,
+                          float cos_t, float r2, int* parent, int32_t* labels,
+                          unsigned long long* count, int* err, cudaStream_t s);
+
 // ---------------------------------------------------------------------------
 // point-to-plane ICP over B pairs (B = 1 for a single registration)
 // ---------------------------------------------------------------------------

@@ -6,10 +6,13 @@ profilers (ncu) and quick timing.
 
 Workloads: surface (10,000-point wavy surface pair), depth (640x480 depth
 frames, ~3.07e5 points), lidar (64 x 2048 sweep, ~1.2e5 returns), batch (256
-surface pairs with sizes log-uniform in [2e3, 2e5]).  Ops: register (grid,
+surface pairs with sizes log-uniform in [2e3, 2e5]), apartment (7.8M points on
+a furnished flat; op segment only).  Ops: register (grid,
 k-NN normals and point-to-plane ICP), knn (self k-NN), normals, radius
 (radius search), icp (ICP alone on library normals, with --metric and
---association), batch (the batched graph run; workload batch only).  Each op
+--association), batch (the batched graph run; workload batch only), segment
+(5 mm voxel grid, k = 30 normals, smooth segmentation with k = 30 and a
+2.8 rad angle; workload apartment only).  Each op
 runs --repeat times after one warm-up call; the CUDA-event time per call and
 the per-kernel times recorded by the library (not inside graph replays) are
 printed as one JSON line.
@@ -24,9 +27,10 @@ import sys
 
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_1807_00399_gb300.profile_run")
-    ap.add_argument("--workload", choices=["surface", "depth", "lidar", "batch"], default="depth")
-    ap.add_argument("--op", choices=["register", "knn", "normals", "radius", "batch", "icp"],
-                    default="register")
+    ap.add_argument("--workload", choices=["surface", "depth", "lidar", "batch", "apartment"],
+                    default="depth")
+    ap.add_argument("--op", choices=["register", "knn", "normals", "radius", "batch", "icp",
+                                     "segment"], default="register")
     ap.add_argument("--iters", type=int, default=30, help="ICP iterations")
     ap.add_argument("--k", type=int, default=0, help="neighbours (default: 16 lidar, else 10)")
     ap.add_argument("--radius", type=float, default=0.5)
@@ -47,8 +51,17 @@ def main(argv=None):
     import paper_1807_00399_gb300 as cil
     from paper_1807_00399_gb300 import synth
 
-    k = a.k or (16 if a.workload == "lidar" else 10)
-    if a.workload == "batch":
+    k = a.k or {"lidar": 16, "apartment": 30}.get(a.workload, 10)
+    if (a.op == "segment") != (a.workload == "apartment"):
+        raise SystemExit("op segment runs on the apartment workload, and only it")
+    if a.workload == "apartment":
+        P = torch.from_numpy(synth.apartment_scene(a.seed)).cuda()
+
+        def fn():
+            v, _ = cil.voxel_downsample(P, 0.005)
+            nrm, _ = cil.estimate_normals(v, k, synth.APARTMENT_VIEWPOINT, with_curvature=False)
+            return cil.segment(v, nrm, k=k, theta=2.8)
+    elif a.workload == "batch":
         sizes = synth.batch_sizes(a.seed, 256)
         src, dst, _ = synth.surface_batch_torch(1000 + a.seed, sizes)
         h = cil.Batch(sizes, sizes, k=k, iters=a.iters, max_corr_dist=0.1, viewpoint=(0.0, 0.0, 10.0))
@@ -101,7 +114,8 @@ def main(argv=None):
     L.cil_timing_enable(0)
     out = {"workload": a.workload, "op": a.op, "k": k, "iters": a.iters, "repeat": a.repeat,
            "ms_per_call": e0.elapsed_time(e1) / a.repeat}
-    for name in ("grid_build", "order_queries", "k_knn", "k_normals", "k_icp", "k_radius"):
+    for name in ("grid_build", "order_queries", "k_knn", "k_normals", "k_icp", "k_radius",
+                 "voxel_downsample", "segment"):
         t, c = ctypes.c_double(), ctypes.c_int64()
         L.cil_timing_read(name.encode(), ctypes.byref(t), ctypes.byref(c))
         if c.value:
