@@ -262,6 +262,26 @@ cil_status cil_segment(const float *xyz, const float *normals, int64_t n, int k,
                        float radius, int32_t *out_labels, int64_t *out_count, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Smooth segmentation in one search (Sec. 3 normals and connected components;
+ * Sec. 4's first test): the k nearest neighbours of every point are found
+ * once, give its PCA normal (as cil_estimate_normals, oriented towards
+ * viewpoint) and its edges of the graph of cil_segment.
+ *   xyz           device float[n][3]
+ *   k             neighbours per point, self included (1..CIL_MAX_K), for
+ *                 both the normals and the graph
+ *   viewpoint     host float[3]
+ *   theta, radius as cil_segment
+ *   out_normals   device float[n][3] or NULL (then kept internally)
+ *   out_labels    device int32[n]: smallest point index of each component
+ *   out_count     host: number of components
+ * Labels equal cil_segment's on the same normals.  Synchronises the stream.
+ * Errors as cil_segment; CIL_ERR_INVALID_ARG for a null viewpoint.
+ * ------------------------------------------------------------------------- */
+cil_status cil_smooth_segment(const float *xyz, int64_t n, int k, const float *viewpoint,
+                              float theta, float radius, float *out_normals, int32_t *out_labels,
+                              int64_t *out_count, void *stream);
+
+/* ---------------------------------------------------------------------------
  * ICP variants (Sec. 3: the ICP loop parameterised by the correspondence
  * search and the estimator; rigid registration under the point-to-point
  * metric (Besl & McKay), the point-to-plane metric (Low) and weighted

@@ -91,10 +91,16 @@ def segment(P, N, k: int = 30, theta: float = 2.8, radius: float = 0.0, method: 
     return lab, int(np.sum(lab == np.arange(n)))
 
 
-def bounds(P, N, k: int = 30, theta: float = 2.8, radius: float = 0.0, rel: float = 1e-6):
+def bounds(P, N, k: int = 30, theta: float = 2.8, radius: float = 0.0, rel: float = 1e-6,
+           eps=None):
     """(lower, upper) partitions: without / with every edge the definition
     leaves open (k-th-rank distance ties and similarity values within `rel` of
-    their thresholds)."""
+    their thresholds).  `eps` (optional, per point, radians): how far the
+    normal a compared result used may lie from N; since unit vectors turned by
+    angles a and b change their dot product by at most a + b, an edge is also
+    open where |n_i . n_j - cos theta| <= rel + eps_i + eps_j, and wherever
+    eps_i + eps_j >= 2 (the dot product of unit vectors spans [-1, 1], so the
+    edge is then undecided whatever N holds, a non-finite normal included)."""
     P = _f32(P)
     n = len(P)
     idx, d2 = knn_edges(P, k)
@@ -113,7 +119,9 @@ def bounds(P, N, k: int = 30, theta: float = 2.8, radius: float = 0.0, rel: floa
     cos_t = np.float32(np.cos(np.float64(np.float32(theta))))
     r2 = np.float32(float(np.float32(radius)) ** 2) if radius > 0 else np.float32(0)
     dot, dd2, ok = similarity(P, N, cand_i, cand_j, cos_t, r2)
-    near = np.abs(dot.astype(np.float64) - float(cos_t)) <= rel
+    slack = rel if eps is None else rel + np.asarray(eps, np.float64)[cand_i] + \
+        np.asarray(eps, np.float64)[np.maximum(cand_j, 0)]
+    near = (np.abs(dot.astype(np.float64) - float(cos_t)) <= slack) | (slack >= 2.0 + rel)
     if radius > 0:
         near |= np.abs(dd2.astype(np.float64) - float(r2)) <= rel * float(r2)
     lo = valid & sure & ok & ~near

@@ -18,7 +18,7 @@ import numpy as np
 __all__ = [
     "CilError", "lib", "knn", "radius_search", "estimate_normals", "icp_point_to_plane",
     "register_pair", "sync_status", "Params", "STATUS", "MAX_K", "IcpReport", "Batch", "icp",
-    "IcpOptions", "segment",
+    "IcpOptions", "segment", "smooth_segment",
     "decode_report", "decode_reports",
 ]
 
@@ -78,6 +78,7 @@ def lib():
         L.cil_icp_point_to_plane.argtypes = [P, I64, P, P, I64, P, I, F, P, P, P]
         L.cil_icp.argtypes = [P, I64, P, P, I64, P, I, F, P, P, P, P]
         L.cil_segment.argtypes = [P, P, I64, I, F, F, P, P, P]
+        L.cil_smooth_segment.argtypes = [P, I64, I, P, F, F, P, P, P, P]
         L.cil_register_pair.argtypes = [P, I64, P, I64, I, P, P, I, F, P, P, P, P, P]
         L.cil_icp_batch_create.argtypes = [P, P, I, P, P]
         L.cil_icp_batch_run.argtypes = [P, P, P, P, P, P, P, P]
@@ -366,6 +367,23 @@ def segment(xyz, normals, k: int = 30, theta: float = 2.8, radius: float = 0.0, 
                            _ptr(labels), ctypes.byref(count), _stream(stream))
     _check(st, "cil_segment")
     return labels, int(count.value)
+
+
+def smooth_segment(xyz, k: int = 30, viewpoint=(0.0, 0.0, 0.0), theta: float = 2.8,
+                   radius: float = 0.0, stream=None):
+    """PCA normals and smooth segments from one k-NN search
+    (cil_smooth_segment): (normals (N,3), labels int32, number of segments)."""
+    torch = _torch()
+    xyz = _points(xyz, "xyz")
+    n = xyz.shape[0]
+    nrm = torch.empty((n, 3), dtype=torch.float32, device=xyz.device)
+    labels = torch.empty(n, dtype=torch.int32, device=xyz.device)
+    vp = (ctypes.c_float * 3)(*[float(v) for v in np.asarray(viewpoint, np.float64).reshape(3)])
+    count = ctypes.c_int64()
+    st = lib().cil_smooth_segment(_ptr(xyz), n, int(k), vp, float(theta), float(radius), _ptr(nrm),
+                                  _ptr(labels), ctypes.byref(count), _stream(stream))
+    _check(st, "cil_smooth_segment")
+    return nrm, labels, int(count.value)
 
 
 def register_pair(src, dst, k: int, viewpoint, iters: int, max_corr_dist: float, *,

@@ -392,14 +392,17 @@ cil_status cil_icp(const float* src, int64_t n_src, const float* dst, const floa
   return CIL_OK;
 }
 
-cil_status cil_segment(const float* xyz, const float* normals, int64_t n, int k, float theta,
-                       float radius, int32_t* out_labels, int64_t* out_count, void* stream) {
+// Shared body of cil_segment (normals given) and cil_smooth_segment (normals
+// computed here from the same k-NN lists that define the graph: one search).
+static cil_status segment_impl(const float* xyz, const float* normals_in, const float* viewpoint,
+                               int64_t n, int k, float theta, float radius, float* out_normals,
+                               int32_t* out_labels, int64_t* out_count, void* stream) {
   if (k < 1 || k > CIL_MAX_K || bad_count(n) || !out_count || !(theta >= 0.0f) ||
       !(theta < INFINITY) || !(radius >= 0.0f) || !(radius < INFINITY))
     return CIL_ERR_INVALID_ARG;
   *out_count = 0;
   if (n == 0) return CIL_OK;
-  if (!xyz || !normals || !out_labels) return CIL_ERR_INVALID_ARG;
+  if (!xyz || (!normals_in && !viewpoint) || !out_labels) return CIL_ERR_INVALID_ARG;
   cil_status st = CIL_OK;
   DeviceCtx* ctx = device_ctx(&st);
   if (!ctx) return st;
@@ -410,18 +413,27 @@ cil_status cil_segment(const float* xyz, const float* normals, int64_t n, int k,
   const size_t o_idx = ws.reserve(sizeof(int) * (size_t)n * (size_t)k);
   const size_t o_parent = ws.reserve(sizeof(int) * (size_t)n);
   const size_t o_count = ws.reserve(sizeof(unsigned long long));
+  const bool own_normals = !normals_in && !out_normals;
+  const size_t o_nrm = own_normals ? ws.reserve(sizeof(float) * 3 * (size_t)n) : 0;
   if ((st = ws.allocate(ctx, s)) != CIL_OK) return st;
   if ((st = grid_build(gp, ws, xyz, nullptr, grid_options(nullptr, k), ctx, s)) != CIL_OK) return st;
   int* idx = ws.at<int>(o_idx);
-  if ((st = launch_knn(grid_view(gp, ws), xyz, n, nullptr, k, idx, nullptr, block_of(nullptr), s)) !=
-      CIL_OK)
-    return st;
+  const float* nrm = normals_in;
+  if (normals_in) {
+    st = launch_knn(grid_view(gp, ws), xyz, n, nullptr, k, idx, nullptr, block_of(nullptr), s);
+  } else {
+    float* nout = own_normals ? ws.at<float>(o_nrm) : out_normals;
+    st = launch_normals(grid_view(gp, ws), 1, n, k, nullptr, viewpoint, xyz, nout, nullptr,
+                        block_of(nullptr), s, idx);
+    nrm = nout;
+  }
+  if (st != CIL_OK) return st;
   // the thresholds as FP32 values, the same rounding the oracle applies
   const float cos_t = (float)cos((double)theta);
   const float r2 = radius > 0.0f ? (float)((double)radius * (double)radius) : 0.0f;
   unsigned long long* count = ws.at<unsigned long long>(o_count);
-  if ((st = launch_segment(idx, k, xyz, normals, n, cos_t, r2, ws.at<int>(o_parent), out_labels,
-                           count, ctx->err, s)) != CIL_OK)
+  if ((st = launch_segment(idx, k, xyz, nrm, n, cos_t, r2, ws.at<int>(o_parent), out_labels, count,
+                           ctx->err, s)) != CIL_OK)
     return st;
   unsigned long long c = 0;
   if (cudaMemcpyAsync(&c, count, sizeof(c), cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -430,6 +442,21 @@ cil_status cil_segment(const float* xyz, const float* normals, int64_t n, int k,
   if (cudaStreamSynchronize(s) != cudaSuccess) return CIL_ERR_CUDA;
   *out_count = (int64_t)c;
   return read_error_word(ctx, s, true);
+}
+
+cil_status cil_segment(const float* xyz, const float* normals, int64_t n, int k, float theta,
+                       float radius, int32_t* out_labels, int64_t* out_count, void* stream) {
+  if (n > 0 && !normals) return CIL_ERR_INVALID_ARG;
+  return segment_impl(xyz, normals, nullptr, n, k, theta, radius, nullptr, out_labels, out_count,
+                      stream);
+}
+
+cil_status cil_smooth_segment(const float* xyz, int64_t n, int k, const float* viewpoint,
+                              float theta, float radius, float* out_normals, int32_t* out_labels,
+                              int64_t* out_count, void* stream) {
+  if (!viewpoint) return CIL_ERR_INVALID_ARG;
+  return segment_impl(xyz, nullptr, viewpoint, n, k, theta, radius, out_normals, out_labels,
+                      out_count, stream);
 }
 
 cil_status cil_icp_point_to_plane(const float* src, int64_t n_src, const float* dst,

@@ -9,9 +9,11 @@ cil_status launch_knn(const GridView& g, const float* qry, int64_t nq, const int
                       int* out_idx, float* out_d2, int block, cudaStream_t s);
 
 // viewpoints: vp_dev (device float[3 * clouds]) or, when null, vp_host[3]
+// out_idx (optional, single cloud): the k neighbour indices of every point,
+// row-major (n, k), -1 past the cloud's size -- the lists the normals used
 cil_status launch_normals(const GridView& g, int clouds, int64_t n, int k, const float* vp_dev,
                           const float* vp_host, const float* xyz, float* out_n, float* out_c,
-                          int block, cudaStream_t s);
+                          int block, cudaStream_t s, int* out_idx = nullptr);
 
 cil_status launch_knn_hybrid(const GridView& g, const float* qry, int64_t nq, const int* order,
                              int k, float r, int* out_idx, float* out_d2, cudaStream_t s);

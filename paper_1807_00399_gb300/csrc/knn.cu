@@ -262,7 +262,8 @@ __global__ void __launch_bounds__(256) k_normals(GridView g, int cloud_count, in
                                                  const float* __restrict__ vp_all, float vx,
                                                  float vy, float vz,
                                                  const float* __restrict__ xyz,
-                                                 float* __restrict__ out_n, float* __restrict__ out_c) {
+                                                 float* __restrict__ out_n, float* __restrict__ out_c,
+                                                 int* __restrict__ out_idx) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float4 p = g.pts[i];
@@ -292,6 +293,12 @@ __global__ void __launch_bounds__(256) k_normals(GridView g, int cloud_count, in
   out_n[3 * gi + 1] = nv[1];
   out_n[3 * gi + 2] = nv[2];
   if (out_c) out_c[gi] = c;
+  if (out_idx) {
+    int* oi = out_idx + gi * k;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j < k) oi[j] = top.v[j] == kEmptyKey ? -1 : key_idx(top.v[j]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -431,7 +438,7 @@ cil_status launch_knn(const GridView& g, const float* qry, int64_t nq, const int
 
 cil_status launch_normals(const GridView& g, int clouds, int64_t n, int k, const float* vp_dev,
                           const float* vp_host, const float* xyz, float* out_n, float* out_c,
-                          int block, cudaStream_t s) {
+                          int block, cudaStream_t s, int* out_idx) {
   if (n <= 0) return CIL_OK;
   if (block != 64 && block != 128 && block != 256) block = 128;
   const int grid = ceil_div(n, block);
@@ -440,7 +447,7 @@ cil_status launch_normals(const GridView& g, int clouds, int64_t n, int k, const
   const float vx = vp_host ? vp_host[0] : 0.0f, vy = vp_host ? vp_host[1] : 0.0f,
               vz = vp_host ? vp_host[2] : 0.0f;
   CIL_FOR_K(k, (k_normals<KM><<<grid, block, 0, s>>>(g, clouds, n, k, vp_dev, vx, vy, vz, xyz,
-                                                     out_n, out_c)));
+                                                     out_n, out_c, out_idx)));
   return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
 }
 

@@ -11,8 +11,8 @@ a furnished flat; op segment only).  Ops: register (grid,
 k-NN normals and point-to-plane ICP), knn (self k-NN), normals, radius
 (radius search), icp (ICP alone on library normals, with --metric and
 --association), batch (the batched graph run; workload batch only), segment
-(5 mm voxel grid, k = 30 normals, smooth segmentation with k = 30 and a
-2.8 rad angle; workload apartment only).  Each op
+(5 mm voxel grid, then k = 30 normals and smooth segments with a 2.8 rad
+angle from one search; workload apartment only).  Each op
 runs --repeat times after one warm-up call; the CUDA-event time per call and
 the per-kernel times recorded by the library (not inside graph replays) are
 printed as one JSON line.
@@ -59,8 +59,7 @@ def main(argv=None):
 
         def fn():
             v, _ = cil.voxel_downsample(P, 0.005)
-            nrm, _ = cil.estimate_normals(v, k, synth.APARTMENT_VIEWPOINT, with_curvature=False)
-            return cil.segment(v, nrm, k=k, theta=2.8)
+            return cil.smooth_segment(v, k, synth.APARTMENT_VIEWPOINT, theta=2.8)
     elif a.workload == "batch":
         sizes = synth.batch_sizes(a.seed, 256)
         src, dst, _ = synth.surface_batch_torch(1000 + a.seed, sizes)

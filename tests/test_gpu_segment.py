@@ -12,6 +12,18 @@ from oracle import segment as sg
 from paper_1807_00399_gb300 import synth
 
 pytestmark = pytest.mark.gpu
+GATE = 1e-2  # eigen-gap gate of the normal parity bar: (l1 - l0) >= GATE l2
+TOL_ANGLE = 1e-4  # normal parity bar (rad) where the gap clears the gate
+
+
+def _normal_eps(P, on, oev, vp):
+    """Per-point bound on the angle between the library's normal and the
+    oracle's: the normal parity bar where the eigenvector is well conditioned
+    and the orientation clear of the viewpoint plane, else unbounded."""
+    good = (oev[:, 1] - oev[:, 0]) >= GATE * oev[:, 2]
+    v = np.asarray(vp, np.float64) - P.astype(np.float64)
+    clear = np.abs((on * v).sum(1)) / np.linalg.norm(v, axis=1) > 1e-3
+    return np.where(good & clear & np.isfinite(on).all(1), TOL_ANGLE, 3.0)
 
 
 def _check(P, N, k, theta, radius=0.0):
@@ -41,6 +53,30 @@ def test_depth_frame_smooth_segments():
     on, _, _ = oracle.normals(p.target, 30, p.viewpoint, method="kdtree")
     lab, nc = _check(p.target, on.astype(np.float32), 30, 2.8)
     assert 1 <= nc < len(p.target)
+
+
+def test_smooth_segment_equals_the_two_step_path():
+    p = synth.depth_frame_pair(0)
+    x = torch.from_numpy(p.target).cuda()
+    nrm, lab, nc = cil.smooth_segment(x, 30, p.viewpoint, theta=2.8)
+    gn, _ = cil.estimate_normals(x, 30, p.viewpoint)
+    assert torch.equal(nrm, gn)
+    lab2, nc2 = cil.segment(x, gn, k=30, theta=2.8)
+    assert torch.equal(lab, lab2) and nc == nc2
+
+
+@pytest.mark.parametrize("k,theta", [(10, 0.2), (30, 2.8)])
+def test_smooth_segment_oracle_bounds(k, theta):
+    p = synth.depth_frame_pair(1)
+    on, _, oev = oracle.normals(p.target, k, p.viewpoint, method="kdtree")
+    nrm, lab, nc = cil.smooth_segment(torch.from_numpy(p.target).cuda(), k, p.viewpoint, theta=theta)
+    lab = lab.cpu().numpy()
+    eps = _normal_eps(p.target, on, oev, p.viewpoint)
+    lo, hi = sg.bounds(p.target, on.astype(np.float32), k=k, theta=theta, eps=eps)
+    assert sg.consistent(lab, lo, hi)
+    assert nc == int(np.sum(lab == np.arange(len(lab))))
+    if theta < 1:
+        assert nc > 10  # box faces meeting at right angles are cut
 
 
 def test_empty_and_invalid():
@@ -91,7 +127,7 @@ def test_apartment_scale_smooth_segmentation():
     P = synth.apartment_scene(0)
     V, _ = oracle.voxel_downsample(P, 0.005)
     V = V.astype(np.float32)
-    N, _, _ = oracle.normals(V, 30, synth.APARTMENT_VIEWPOINT, method="kdtree")
+    N, _, oev = oracle.normals(V, 30, synth.APARTMENT_VIEWPOINT, method="kdtree")
     N = N.astype(np.float32)
     lab, nc = cil.segment(torch.from_numpy(V).cuda(), torch.from_numpy(N).cuda(), k=30, theta=2.8)
     lab = lab.cpu().numpy()
@@ -101,3 +137,11 @@ def test_apartment_scale_smooth_segmentation():
     lo, hi = sg.bounds(V, N, k=30, theta=2.8)
     assert sg.consistent(lab, lo, hi)
     assert len(np.unique(lo)) >= nc >= len(np.unique(hi))
+    # one search for normals and graph, against bounds widened by the normals'
+    # parity bar
+    _, lab, nc = cil.smooth_segment(torch.from_numpy(V).cuda(), 30, synth.APARTMENT_VIEWPOINT,
+                                    theta=2.8)
+    lab = lab.cpu().numpy()
+    eps = _normal_eps(V, N.astype(np.float64), oev, synth.APARTMENT_VIEWPOINT)
+    lo, hi = sg.bounds(V, N, k=30, theta=2.8, eps=eps)
+    assert sg.consistent(lab, lo, hi)

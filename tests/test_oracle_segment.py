@@ -103,3 +103,17 @@ def test_bounds_bracket_the_definition():
         u = np.unique(hi)
         bad[bad == u[1]] = u[0]
         assert not sg.consistent(bad, lo, hi)
+
+
+def test_bounds_with_uncertain_normals():
+    P, _ = _cloud(7, 400)
+    N = np.tile(np.float32([0, 0, 1]), (400, 1))
+    # every normal fully uncertain: nothing is certain to join, everything may
+    lo, hi = sg.bounds(P, N, k=6, theta=0.5, eps=np.full(400, 3.0))
+    np.testing.assert_array_equal(lo, np.arange(400))
+    np.testing.assert_array_equal(hi, _bfs_labels(P, N, 6, 0.5, 0.0))
+    # no uncertainty: the plain bounds
+    a = sg.bounds(P, N, k=6, theta=0.5)
+    b = sg.bounds(P, N, k=6, theta=0.5, eps=np.zeros(400))
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
