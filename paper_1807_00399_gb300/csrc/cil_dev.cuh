@@ -12,6 +12,7 @@
 // stop only when no unvisited cell can hold a closer point (exact results).
 #pragma once
 
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -303,7 +304,98 @@ struct TopK {
   }
   __device__ __forceinline__ bool full() const { return thr != kEmptyKey; }
   __device__ __forceinline__ float thr_d2() const { return key_d2(thr); }
+  __device__ __forceinline__ void bind(u64*, int) {}
+  __device__ __forceinline__ void finish() {}
+  // slot j (a compile-time index in unrolled loops): ascending order
+  __device__ __forceinline__ u64 key_at(int j) const { return v[j]; }
 };
+
+// The k smallest keys as a binary max-heap in shared memory (this thread's
+// slot j at h[j * stride], so the lanes of a warp touch consecutive words).
+// A key below the root replaces it and sifts down: at most log2(k) levels of
+// two loads and one store, where the register list above shifts all KMAX
+// slots with integer selects -- for large k that shifting saturates the
+// integer pipe.  Keys are unique (the index fills the low word), so the set
+// of the k smallest is well defined; heap order is not ascending until
+// finish() sorts it.
+template <int KMAX>
+struct TopKHeap {
+  u64* h;
+  u64 thr;  // the root once k keys are held, else kEmptyKey
+  int stride, k, cnt;
+
+  __device__ __forceinline__ void bind(u64* base, int st) {
+    h = base;
+    stride = st;
+  }
+  __device__ __forceinline__ void init(int kk) {
+    k = kk;
+    cnt = 0;
+    thr = kEmptyKey;
+  }
+  __device__ __forceinline__ u64 at(int j) const { return h[j * stride]; }
+  __device__ __forceinline__ void put(int j, u64 x) { h[j * stride] = x; }
+  // place `key` at the root of the heap h[0, n) and restore heap order
+  __device__ __forceinline__ void sift_down(u64 key, int n) {
+    int j = 0;
+    for (;;) {
+      int c = 2 * j + 1;
+      if (c >= n) break;
+      u64 cv = at(c);
+      if (c + 1 < n) {
+        const u64 c2 = at(c + 1);
+        if (c2 > cv) {
+          cv = c2;
+          ++c;
+        }
+      }
+      if (cv <= key) break;
+      put(j, cv);
+      j = c;
+    }
+    put(j, key);
+  }
+  __device__ __forceinline__ void push(u64 key) {
+    if (key >= thr) return;
+    if (cnt < k) {
+      int j = cnt++;
+      while (j > 0) {
+        const int p = (j - 1) >> 1;
+        const u64 pv = at(p);
+        if (pv >= key) break;
+        put(j, pv);
+        j = p;
+      }
+      put(j, key);
+      if (cnt == k) thr = at(0);
+    } else {
+      sift_down(key, k);
+      thr = at(0);
+    }
+  }
+  __device__ __forceinline__ bool full() const { return thr != kEmptyKey; }
+  __device__ __forceinline__ float thr_d2() const { return key_d2(thr); }
+  // ascending order in place (heap sort of the cnt held keys)
+  __device__ __forceinline__ void finish() {
+    for (int e = cnt - 1; e > 0; --e) {
+      const u64 top = at(0);
+      const u64 last = at(e);
+      put(e, top);
+      sift_down(last, e);
+    }
+  }
+  __device__ __forceinline__ u64 key_at(int j) const { return j < cnt ? at(j) : kEmptyKey; }
+};
+
+// Register list for small k, shared-memory heap from kHeapFromK on (a block
+// of B threads then needs B * KMAX * 8 bytes of dynamic shared memory).
+constexpr int kHeapFromK = 16;
+template <int KMAX>
+using TopKFor = typename std::conditional<(KMAX >= kHeapFromK), TopKHeap<KMAX>, TopK<KMAX>>::type;
+template <int KMAX>
+constexpr int topk_smem_per_thread() {
+  return KMAX >= kHeapFromK ? KMAX * (int)sizeof(u64) : 0;
+}
 
 // Exact k nearest neighbours of q among the points of cloud `cloud`.
 // Rings of cells are searched at the cloud's level; a search that has not
@@ -311,8 +403,8 @@ struct TopK {
 // from the cloud) restarts at an 8x coarser level, up to the level whose one
 // cell spans the whole cloud, so every query visits at most a few hundred
 // cells per level.
-template <int KMAX>
-__device__ __forceinline__ void grid_knn(const GridView& g, int cloud, const float q[3], TopK<KMAX>& top,
+template <int KMAX, class Top>
+__device__ __forceinline__ void grid_knn(const GridView& g, int cloud, const float q[3], Top& top,
                                          int* visited_cells = nullptr) {
   const GridParams& P = g.prm[cloud];
   const float inv_fine = P.inv_fine;
@@ -361,9 +453,9 @@ __device__ __forceinline__ void grid_knn(const GridView& g, int cloud, const flo
 // Exact k nearest neighbours of q among the points within squared distance r2
 // (inclusive): the search, the pruning and the stopping bound all use
 // min(current k-th distance, r2); levels escalate as in grid_knn.
-template <int KMAX>
+template <int KMAX, class Top>
 __device__ __forceinline__ void grid_knn_within(const GridView& g, int cloud, const float q[3],
-                                                float r2, TopK<KMAX>& top) {
+                                                float r2, Top& top) {
   const GridParams& P = g.prm[cloud];
   const float inv_fine = P.inv_fine;
   for (int lvl = P.level;; lvl = next_level(lvl)) {

@@ -39,15 +39,18 @@ __global__ void __launch_bounds__(256) k_knn(GridView g, const float* __restrict
     q[1] = p.y;
     q[2] = p.z;
   }
-  TopK<KMAX> top;
+  extern __shared__ u64 s_topk[];
+  TopKFor<KMAX> top;
+  top.bind(s_topk + threadIdx.x, blockDim.x);
   top.init(k);
   grid_knn<KMAX>(g, 0, q, top);
+  top.finish();
   int* oi = out_idx + qi * k;
   float* od = out_d2 ? out_d2 + qi * k : nullptr;
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) {
     if (j < k) {
-      const u64 key = top.v[j];
+      const u64 key = top.key_at(j);
       const bool none = key == kEmptyKey;
       oi[j] = none ? -1 : key_idx(key);
       if (od) od[j] = none ? __int_as_float(0x7f800000) : key_d2(key);
@@ -210,8 +213,8 @@ __device__ __forceinline__ void finish_normal(const float C[6], const float q[3]
 
 // PCA normal + curvature of one point from its neighbour keys.  `xyz` and the
 // key indices are relative to the same cloud.
-template <int KMAX>
-__device__ __forceinline__ void normal_from_topk(const TopK<KMAX>& top, int k,
+template <int KMAX, class Top>
+__device__ __forceinline__ void normal_from_topk(const Top& top, int k,
                                                  const float* __restrict__ xyz, const float q[3],
                                                  const float vp[3], float out_n[3], float& out_c) {
   // pass 1: mean offset of the neighbours from the query (offsets of nearby
@@ -221,8 +224,9 @@ __device__ __forceinline__ void normal_from_topk(const TopK<KMAX>& top, int k,
   int m = 0;
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) {
-    if (j < k && top.v[j] != kEmptyKey) {
-      const int64_t id = key_idx(top.v[j]);
+    const u64 key = top.key_at(j);
+    if (j < k && key != kEmptyKey) {
+      const int64_t id = key_idx(key);
       sx += xyz[3 * id] - q[0];
       sy += xyz[3 * id + 1] - q[1];
       sz += xyz[3 * id + 2] - q[2];
@@ -240,8 +244,9 @@ __device__ __forceinline__ void normal_from_topk(const TopK<KMAX>& top, int k,
   float cxx = 0.f, cxy = 0.f, cxz = 0.f, cyy = 0.f, cyz = 0.f, czz = 0.f;
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) {
-    if (j < k && top.v[j] != kEmptyKey) {
-      const int64_t id = key_idx(top.v[j]);
+    const u64 key = top.key_at(j);
+    if (j < k && key != kEmptyKey) {
+      const int64_t id = key_idx(key);
       const float ex = (xyz[3 * id] - q[0]) - mx;
       const float ey = (xyz[3 * id + 1] - q[1]) - my;
       const float ez = (xyz[3 * id + 2] - q[2]) - mz;
@@ -281,7 +286,9 @@ __global__ void __launch_bounds__(256) k_normals(GridView g, int cloud_count, in
   const int start = g.prm[cloud].start;
   const int64_t local = __float_as_int(p.w);
   const float q[3] = {p.x, p.y, p.z};
-  TopK<KMAX> top;
+  extern __shared__ u64 s_topk[];
+  TopKFor<KMAX> top;
+  top.bind(s_topk + threadIdx.x, blockDim.x);
   top.init(k);
   grid_knn<KMAX>(g, cloud, q, top);
   const float vp[3] = {vp_all ? vp_all[3 * cloud] : vx, vp_all ? vp_all[3 * cloud + 1] : vy,
@@ -296,8 +303,10 @@ __global__ void __launch_bounds__(256) k_normals(GridView g, int cloud_count, in
   if (out_idx) {
     int* oi = out_idx + gi * k;
 #pragma unroll
-    for (int j = 0; j < KMAX; ++j)
-      if (j < k) oi[j] = top.v[j] == kEmptyKey ? -1 : key_idx(top.v[j]);
+    for (int j = 0; j < KMAX; ++j) {
+      const u64 key = top.key_at(j);
+      if (j < k) oi[j] = key == kEmptyKey ? -1 : key_idx(key);
+    }
   }
 }
 
@@ -326,15 +335,18 @@ __global__ void __launch_bounds__(256) k_knn_hybrid(GridView g, const float* __r
     q[1] = p.y;
     q[2] = p.z;
   }
-  TopK<KMAX> top;
+  extern __shared__ u64 s_topk[];
+  TopKFor<KMAX> top;
+  top.bind(s_topk + threadIdx.x, blockDim.x);
   top.init(k);
   grid_knn_within<KMAX>(g, 0, q, r2, top);
+  top.finish();
   int* oi = out_idx + qi * k;
   float* od = out_d2 ? out_d2 + qi * k : nullptr;
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) {
     if (j < k) {
-      const u64 key = top.v[j];
+      const u64 key = top.key_at(j);
       const bool none = key == kEmptyKey;
       oi[j] = none ? -1 : key_idx(key);
       if (od) od[j] = none ? __int_as_float(0x7f800000) : key_d2(key);
@@ -425,14 +437,38 @@ __global__ void __launch_bounds__(128) k_normals_radius(GridView g, int64_t n, f
 // host launchers: dispatch on the smallest compiled register capacity >= k
 // (CIL_FOR_K, cil_dev.cuh)
 // ---------------------------------------------------------------------------
+// Threads per block for a top-k kind: the heap variants keep KMAX keys per
+// thread in shared memory and run at most 128 threads per block (32 KB at
+// KMAX = 32), so no launch needs the opt-in above 48 KB.
+template <int KM>
+static int topk_block(int block) {
+  if (block != 64 && block != 128 && block != 256) block = 128;
+  return KM >= kHeapFromK ? (block < 128 ? block : 128) : block;
+}
+
+template <int KM>
+static void knn_launch(const GridView& g, const float* qry, int64_t nq, const int* order, int k,
+                       int* out_idx, float* out_d2, int block, cudaStream_t s) {
+  const int b = topk_block<KM>(block);
+  k_knn<KM><<<ceil_div(nq, b), b, topk_smem_per_thread<KM>() * b, s>>>(g, qry, nq, order, k,
+                                                                       out_idx, out_d2);
+}
+
+template <int KM>
+static void normals_launch(const GridView& g, int clouds, int64_t n, int k, const float* vp_dev,
+                           float vx, float vy, float vz, const float* xyz, float* out_n,
+                           float* out_c, int* out_idx, int block, cudaStream_t s) {
+  const int b = topk_block<KM>(block);
+  k_normals<KM><<<ceil_div(n, b), b, topk_smem_per_thread<KM>() * b, s>>>(
+      g, clouds, n, k, vp_dev, vx, vy, vz, xyz, out_n, out_c, out_idx);
+}
+
 cil_status launch_knn(const GridView& g, const float* qry, int64_t nq, const int* order, int k,
                       int* out_idx, float* out_d2, int block, cudaStream_t s) {
   if (nq <= 0) return CIL_OK;
-  if (block != 64 && block != 128 && block != 256) block = 128;
-  const int grid = ceil_div(nq, block);
   TimedRegion timer("k_knn", s);
   note_launches(1);
-  CIL_FOR_K(k, (k_knn<KM><<<grid, block, 0, s>>>(g, qry, nq, order, k, out_idx, out_d2)));
+  CIL_FOR_K(k, (knn_launch<KM>(g, qry, nq, order, k, out_idx, out_d2, block, s)));
   return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
 }
 
@@ -440,14 +476,12 @@ cil_status launch_normals(const GridView& g, int clouds, int64_t n, int k, const
                           const float* vp_host, const float* xyz, float* out_n, float* out_c,
                           int block, cudaStream_t s, int* out_idx) {
   if (n <= 0) return CIL_OK;
-  if (block != 64 && block != 128 && block != 256) block = 128;
-  const int grid = ceil_div(n, block);
   TimedRegion timer("k_normals", s);
   note_launches(1);
   const float vx = vp_host ? vp_host[0] : 0.0f, vy = vp_host ? vp_host[1] : 0.0f,
               vz = vp_host ? vp_host[2] : 0.0f;
-  CIL_FOR_K(k, (k_normals<KM><<<grid, block, 0, s>>>(g, clouds, n, k, vp_dev, vx, vy, vz, xyz,
-                                                     out_n, out_c, out_idx)));
+  CIL_FOR_K(k, (normals_launch<KM>(g, clouds, n, k, vp_dev, vx, vy, vz, xyz, out_n, out_c, out_idx,
+                                   block, s)));
   return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
 }
 
@@ -462,7 +496,8 @@ cil_status launch_knn_hybrid(const GridView& g, const float* qry, int64_t nq, co
   TimedRegion timer("k_knn_hybrid", s);
   note_launches(1);
   const float r2 = r * r;
-  CIL_FOR_K(k, (k_knn_hybrid<KM><<<grid, 128, 0, s>>>(g, qry, nq, order, k, r2, out_idx, out_d2)));
+  CIL_FOR_K(k, (k_knn_hybrid<KM><<<grid, 128, topk_smem_per_thread<KM>() * 128, s>>>(
+                   g, qry, nq, order, k, r2, out_idx, out_d2)));
   return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
 }
 

@@ -61,20 +61,22 @@ def test_lattice_exact_ties():
     assert np.array_equal(gd.astype(np.float64), od)
 
 
-def test_duplicates_and_coincident_points():
+@pytest.mark.parametrize("k", [10, 24])  # register list / shared-memory heap
+def test_duplicates_and_coincident_points(k):
     base = _cube(3, 400)
     ref = np.concatenate([base, base, base[:123]])
-    _check(ref, None, 10, self_query=True)
+    _check(ref, None, k, self_query=True)
     same = np.zeros((50, 3), np.float32)
-    gi, gd = _gpu_knn(same, None, 10, self_query=True)
-    assert np.all(gd == 0) and np.array_equal(np.sort(gi, 1), np.tile(np.arange(10), (50, 1)))
-    assert np.array_equal(gi, np.tile(np.arange(10), (50, 1)))
+    gi, gd = _gpu_knn(same, None, k, self_query=True)
+    assert np.all(gd == 0) and np.array_equal(np.sort(gi, 1), np.tile(np.arange(k), (50, 1)))
+    assert np.array_equal(gi, np.tile(np.arange(k), (50, 1)))
 
 
-def test_k_larger_than_reference_pads():
+@pytest.mark.parametrize("k", [8, 20])
+def test_k_larger_than_reference_pads(k):
     ref = _cube(4, 5)
-    gi, gd = _gpu_knn(ref, _cube(5, 9), 8)
-    oi, od = oracle.knn(ref, _cube(5, 9), 8)
+    gi, gd = _gpu_knn(ref, _cube(5, 9), k)
+    oi, od = oracle.knn(ref, _cube(5, 9), k)
     assert np.array_equal(gi, oi)
     assert np.all(np.isinf(gd[:, 5:])) and np.all(gi[:, 5:] == -1)
 
@@ -101,6 +103,8 @@ def test_far_outliers_and_mixed_density():
         np.float32)
     _check(ref, qry, 10)
     _check(ref, None, 10, self_query=True)
+    _check(ref, qry, 32)
+    _check(ref, None, 32, self_query=True)
 
 
 @pytest.mark.parametrize("kw", [{"cell_scale": 0.25}, {"cell_scale": 4.0}, {"cell_size": 1e-4},
@@ -109,6 +113,7 @@ def test_cell_size_and_block_do_not_change_results(kw):
     p = synth.surface_pair(10, n=5003)
     _check(p.target, None, 10, self_query=True, **kw)
     _check(p.target, p.source, 10, **kw)
+    _check(p.target, p.source, 30, **kw)
 
 
 def test_deterministic():
