@@ -389,7 +389,7 @@ struct TopKHeap {
 
 // Register list for small k, shared-memory heap from kHeapFromK on (a block
 // of B threads then needs B * KMAX * 8 bytes of dynamic shared memory).
-constexpr int kHeapFromK = 16;
+constexpr int kHeapFromK = 8;
 template <int KMAX>
 using TopKFor = typename std::conditional<(KMAX >= kHeapFromK), TopKHeap<KMAX>, TopK<KMAX>>::type;
 template <int KMAX>

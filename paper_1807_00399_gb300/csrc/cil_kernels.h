@@ -10,8 +10,8 @@ cil_status launch_knn(const GridView& g, const float* qry, int64_t nq, const int
 
 // viewpoints: vp_dev (device float[3 * clouds]) or, when null, vp_host[3]
 // out_idx (optional, single cloud): the k neighbour indices of every point,
-// row-major (n, k), -1 past the cloud's size -- the lists the normals used,
-// ascending for k < 16, in heap order from k = 16 on
+// row-major (n, k), ascending (d2, index), -1 past the cloud's size -- the
+// lists the normals used
 cil_status launch_normals(const GridView& g, int clouds, int64_t n, int k, const float* vp_dev,
                           const float* vp_host, const float* xyz, float* out_n, float* out_c,
                           int block, cudaStream_t s, int* out_idx = nullptr);

@@ -291,6 +291,9 @@ __global__ void __launch_bounds__(256) k_normals(GridView g, int cloud_count, in
   top.bind(s_topk + threadIdx.x, blockDim.x);
   top.init(k);
   grid_knn<KMAX>(g, cloud, q, top);
+  // ascending keys, so the sums below run in one order whatever order the
+  // search met the points in (results independent of cell size and block)
+  top.finish();
   const float vp[3] = {vp_all ? vp_all[3 * cloud] : vx, vp_all ? vp_all[3 * cloud + 1] : vy,
                        vp_all ? vp_all[3 * cloud + 2] : vz};
   float nv[3], c;
