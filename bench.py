@@ -57,7 +57,7 @@ WORKLOAD = ("depth-frame pair 640x480 (pinhole 525/319.5/239.5, ground + 20 boxe
 # DRAM traffic per k_icp_search launch measured by ncu on this workload
 # (bytes), with the hash of the kernel sources it was measured on; reported
 # only while the sources are unchanged.
-ICP_TRAFFIC = {"bytes": 34844416, "src_sha": "f7c9ac27755551a3"}
+ICP_TRAFFIC = {"bytes": 17863424, "src_sha": "b3cf6ae2ef4635c3"}
 
 
 def _peaks():
@@ -360,6 +360,9 @@ def run_ours(args):
     segmentation = None
     if not args.no_segmentation:
         segmentation = run_segmentation(args, rank)
+    queries = None
+    if not args.no_queries:
+        queries = run_queries(args, rank)
 
     # ---- CPU baseline (oracle, rank 0, N = 1 only) ----
     cpu = None
@@ -398,6 +401,7 @@ def run_ours(args):
             "learned": learned_res,
             "icp_variants": variants,
             "smooth_segmentation": segmentation,
+            "queries": queries,
             "gpu_launches": int(n1 - n0),
             "clocks": clocks,
         }
@@ -532,6 +536,65 @@ def run_variants(args, rank: int, reps: int = 5):
     return out
 
 
+def run_queries(args, rank: int, reps: int = 10):
+    """Standalone self-queries of the whole cloud on each workload (Sec. 3
+    k-NN, radius and normal queries): median ms per call through the C ABI
+    (grid build + query, end to end) and the query kernel's own time from the
+    library's CUDA events (grid prebuilt), as queries/s."""
+    import ctypes
+
+    import torch
+
+    import paper_1807_00399_gb300 as cil
+    from paper_1807_00399_gb300 import synth
+
+    L = cil.lib()
+    cases = []
+    surf = synth.surface_pair(args.seed + rank, n=10_000).target
+    depth = synth.depth_frame_pair(args.seed + rank).target
+    lidar = synth.lidar_sweep_pair(args.seed + rank).target
+    for name, pts, op, k, kernel in (
+            ("surface 10k, knn k=10", surf, "knn", 10, "k_knn"),
+            ("depth frame, knn k=10", depth, "knn", 10, "k_knn"),
+            ("depth frame, normals k=10", depth, "normals", 10, "k_normals"),
+            ("lidar sweep, knn k=16", lidar, "knn", 16, "k_knn"),
+            ("lidar sweep, radius r=0.5 m", lidar, "radius", 0.5, "k_radius")):
+        x = torch.from_numpy(pts).cuda()
+        if op == "knn":
+            fn = lambda x=x, k=k: cil.knn(x, x, k)  # noqa: E731
+        elif op == "normals":
+            fn = lambda x=x, k=k: cil.estimate_normals(x, k, (0.0, 0.0, 0.0))  # noqa: E731
+        else:
+            # the capacity from one sizing call, so each timed call is one pass
+            cap = int(cil.radius_search(x, x, k)[1].numel())
+            fn = lambda x=x, k=k, cap=cap: cil.radius_search(x, x, k, capacity=cap)  # noqa: E731
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        L.cil_timing_reset()
+        L.cil_timing_enable(1)
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        L.cil_timing_enable(0)
+        t, c = ctypes.c_double(), ctypes.c_int64()
+        L.cil_timing_read(kernel.encode(), ctypes.byref(t), ctypes.byref(c))
+        q_ms = t.value / reps
+        L.cil_timing_read(b"grid_build", ctypes.byref(t), ctypes.byref(c))
+        g_ms = t.value / reps
+        L.cil_timing_reset()
+        e2e = float(np.median(ms))
+        cases.append({"case": name, "n": len(pts), "ms_end_to_end": e2e, "ms_grid_build": g_ms,
+                      "ms_query_kernel": q_ms, "queries_per_s_end_to_end": len(pts) / e2e * 1e3,
+                      "queries_per_s_query_only": len(pts) / q_ms * 1e3})
+    return cases
+
+
 def run_segmentation(args, rank: int, reps: int = 3):
     """Smooth segmentation of an apartment-scale scan (Sec. 4's first test:
     5 mm voxel grid, k = 30 normals, connected components of the k = 30
@@ -612,6 +675,8 @@ def main():
                     help="skip the ICP-variant timings")
     ap.add_argument("--no-segmentation", action="store_true",
                     help="skip the apartment-scale smooth-segmentation timing")
+    ap.add_argument("--no-queries", action="store_true",
+                    help="skip the standalone k-NN / normals / radius query timings")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
