@@ -147,6 +147,16 @@ def _barrier_max(x: float, ws: int) -> float:
     return float(t.item())
 
 
+def _sum_over_ranks(x: float, ws: int) -> float:
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def _barrier(ws: int):
     if ws > 1:
         import torch.distributed as dist
@@ -293,7 +303,8 @@ def run_ours(args):
     L.cil_timing_reset()
     rep_h = cil.decode_report(rep)
     tot_max = _barrier_max(tot_ms, ws)
-    value = ws * nt * args.steps / (tot_max / 1e3)
+    nt_all = _sum_over_ranks(nt, ws)  # ranks register different frame pairs (seed + rank)
+    value = nt_all * args.steps / (tot_max / 1e3)
 
     # ---- end to end through the same call with host buffers ----
     src_h = torch.from_numpy(pair.source).pin_memory()
@@ -323,7 +334,7 @@ def run_ours(args):
         e_evs[i][1].record()
     torch.cuda.synchronize()
     e2e_ms = _barrier_max(float(sum(a.elapsed_time(b) for a, b in e_evs)), ws)
-    e2e_value = ws * nt * e2e_steps / (e2e_ms / 1e3)
+    e2e_value = nt_all * e2e_steps / (e2e_ms / 1e3)
 
     # ---- roofline of the dominant kernel ----
     peaks, peak_kind = _peaks()
