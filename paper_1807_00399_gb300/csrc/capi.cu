@@ -432,8 +432,8 @@ static cil_status segment_impl(const float* xyz, const float* normals_in, const 
   const float cos_t = (float)cos((double)theta);
   const float r2 = radius > 0.0f ? (float)((double)radius * (double)radius) : 0.0f;
   unsigned long long* count = ws.at<unsigned long long>(o_count);
-  if ((st = launch_segment(idx, k, xyz, nrm, n, cos_t, r2, ws.at<int>(o_parent), out_labels, count,
-                           ctx->err, s)) != CIL_OK)
+  if ((st = launch_segment(idx, k, xyz, nrm, n, grid_view(gp, ws).pts, cos_t, r2,
+                           ws.at<int>(o_parent), out_labels, count, ctx->err, s)) != CIL_OK)
     return st;
   unsigned long long c = 0;
   if (cudaMemcpyAsync(&c, count, sizeof(c), cudaMemcpyDeviceToHost, s) != cudaSuccess)

@@ -22,10 +22,11 @@ cil_status launch_normals_radius(const GridView& g, int64_t n, float r, const fl
                                  float* out_n, float* out_c, int* out_cnt, cudaStream_t s);
 
 // connected-component segmentation over k-NN edges (segment.cu): labels =
-// smallest index of each component, count = number of components
+// smallest index of each component, count = number of components; `sorted`
+// (optional): the grid's sorted points, whose order the union pass follows
 cil_status launch_segment(const int* knn_idx, int k, const float* xyz, const float* nrm, int64_t n,
-                          float cos_t, float r2, int* parent, int32_t* labels,
-                          unsigned long long* count, int* err, cudaStream_t s);
+                          const float4* sorted, float cos_t, float r2, int* parent,
+                          int32_t* labels, unsigned long long* count, int* err, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // point-to-plane ICP over B pairs (B = 1 for a single registration)

@@ -79,10 +79,14 @@ __global__ void k_seg_init(int* parent, int64_t n) {
 __global__ void __launch_bounds__(kSegThreads) k_seg_union(const int* __restrict__ idx, int k,
                                                            const float* __restrict__ xyz,
                                                            const float* __restrict__ nrm, int64_t n,
+                                                           const float4* __restrict__ sorted,
                                                            float cos_t, float r2, int* parent,
                                                            int* err) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  // points in the grid's Morton order: a warp's points are a compact blob
+  // whose neighbour lists overlap, so their normals and parents hit in L1
+  const int64_t i = sorted ? (int64_t)__float_as_int(__ldg(sorted + t).w) : t;
   const float nx = __ldg(nrm + 3 * i), ny = __ldg(nrm + 3 * i + 1), nz = __ldg(nrm + 3 * i + 2);
   const float px = __ldg(xyz + 3 * i), py = __ldg(xyz + 3 * i + 1), pz = __ldg(xyz + 3 * i + 2);
   int ra = (int)i;
@@ -119,13 +123,14 @@ __global__ void k_seg_labels(int* parent, int64_t n, int32_t* labels, unsigned l
 }
 
 cil_status launch_segment(const int* knn_idx, int k, const float* xyz, const float* nrm, int64_t n,
-                          float cos_t, float r2, int* parent, int32_t* labels,
+                          const float4* sorted, float cos_t, float r2, int* parent, int32_t* labels,
                           unsigned long long* count, int* err, cudaStream_t s) {
   TimedRegion timer("segment", s);
   note_launches(3);
   const int blocks = ceil_div(n, kSegThreads);
   k_seg_init<<<blocks, kSegThreads, 0, s>>>(parent, n);
-  k_seg_union<<<blocks, kSegThreads, 0, s>>>(knn_idx, k, xyz, nrm, n, cos_t, r2, parent, err);
+  k_seg_union<<<blocks, kSegThreads, 0, s>>>(knn_idx, k, xyz, nrm, n, sorted, cos_t, r2, parent,
+                                             err);
   if (cudaMemsetAsync(count, 0, sizeof(unsigned long long), s) != cudaSuccess) return CIL_ERR_CUDA;
   k_seg_labels<<<blocks, kSegThreads, 0, s>>>(parent, n, labels, count);
   return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
