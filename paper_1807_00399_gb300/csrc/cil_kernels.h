@@ -51,6 +51,8 @@ struct IcpPairState {
   double rmse;      // final point-to-plane RMSE
   long long n_inl;  // final inlier count
   float Rt[12];     // T as float rows [R | t] for the association passes
+  float Rt_prev[12];  // the previous round's Rt (certificates of unchanged neighbours)
+  int has_prev;     // Rt_prev holds a round's transform
   float dmax2;      // squared rejection distance
   float ref[3];     // reference point of the pair (point-to-point sums are about it)
   int tile_begin, tile_end;
@@ -69,7 +71,7 @@ struct IcpPlan {
   int n_groups = 0;  // tile groups over all pairs
   size_t o_state, o_order, o_tile_off, o_rt, o_part_s, o_part_c, o_part_n;
   size_t o_grp_s, o_grp_c, o_grp_n, o_grp_done;
-  size_t o_corr, o_queue, o_qc;
+  size_t o_corr, o_lbd, o_queue, o_qc;
   OrderPlan order;
 };
 

@@ -58,6 +58,8 @@ struct IcpArgs {
   int rounds;           // iterations + 1
   IcpPairState* st;
   int* corr;            // per sorted source position: global target index or -1
+  float* lbd;           // per sorted source position: lower bound on the distance from the
+                        // round's p' to every target point but corr (0: none known)
   int2* queue;          // (sorted source position, pair) of queries for k_icp_finish
   unsigned* qcount;     // [2] queue length of the rounds of each parity
   unsigned* qhead;      // [2] queue items taken
@@ -125,26 +127,53 @@ __device__ __forceinline__ void escalate_rings(const GridView& g, int cloud, con
   }
 }
 
+// scan_cell that also keeps the second smallest squared distance within
+// dmax2 (best2)
+__device__ __forceinline__ void scan_cell2(const GridView& g, int s, int n, const float q[3],
+                                           float dmax2, u64& best, int& bj, float& lim,
+                                           float& best2) {
+  for_points(g.pts, s, n, [&](const float4& p, int j) {
+    const float d2 = sqdist(p.x, p.y, p.z, q[0], q[1], q[2]);
+    if (d2 <= dmax2) {
+      const u64 key = pack_key(d2, __float_as_int(p.w));
+      if (key < best) {
+        if (best != kEmptyKey) best2 = fminf(best2, key_d2(best));
+        best = key;
+        bj = j;
+        lim = fminf(lim, d2);
+      } else {
+        best2 = fminf(best2, d2);
+      }
+    }
+  });
+}
+
 // First stage of the correspondence search of one query (per thread).  At
 // the cloud's own level the query's cell is scanned first, then only the
 // cells of its 3x3x3 block that meet the ball of the best distance so far (a
 // converged source point finds its neighbour there).  Returns true when that
 // is exact (the ball stays inside the block).  best / bj / lim: packed key,
 // sorted position (-1: none) and min(dmax2, best d^2) of the best point.
+// lb2 (when exact): a lower bound on the squared distance from q to every
+// target point but the best -- the second best seen, the cells skipped or
+// outside the searched box (by their padded ranges), the space outside the
+// block and dmax2, whichever is least.
 __device__ __forceinline__ bool base_search(const GridView& g, int cloud, const float q[3],
-                                            float dmax2, u64& best, int& bj, float& lim) {
+                                            float dmax2, u64& best, int& bj, float& lim,
+                                            float& lb2) {
   const GridParams& P = g.prm[cloud];
   const float inv_fine = P.inv_fine;
   best = kEmptyKey;
   bj = -1;
   lim = dmax2;
+  lb2 = dmax2;
   CellFrame f;
   f.load(P, cloud);
   const int c[3] = {f.cell_of(q[0], 0, inv_fine), f.cell_of(q[1], 1, inv_fine),
                     f.cell_of(q[2], 2, inv_fine)};
   int s, n;
   if (cell_lookup(g, cell_key(f.level, cloud, c[0], c[1], c[2]), s, n))
-    scan_cell(g, s, n, q, dmax2, best, bj, lim);
+    scan_cell2(g, s, n, q, dmax2, best, bj, lim, lb2);
   if (f.level >= kFineBits) return true;  // one cell holds the whole cloud
   // cells of the block meeting the ball of radius sqrt(lim) (padded)
   const float rad = fmaf(sqrtf(lim), 1.0f + 1e-6f, f.eps);
@@ -153,19 +182,34 @@ __device__ __forceinline__ bool base_search(const GridView& g, int cloud, const 
   for (int a = 0; a < 3; ++a) {
     lo[a] = max(f.cell_of(q[a] - rad, a, inv_fine), c[a] - 1);
     hi[a] = min(f.cell_of(q[a] + rad, a, inv_fine), c[a] + 1);
+    // block cells below lo / above hi on this axis: beyond these faces
+    if (lo[a] > c[a] - 1 && lo[a] > 0) {
+      const float gap = fmaxf(q[a] - (fmaf((float)lo[a], f.c, f.o[a]) + f.eps), 0.0f);
+      lb2 = fminf(lb2, gap * gap);
+    }
+    if (hi[a] < c[a] + 1 && hi[a] < f.hi[a]) {
+      const float gap = fmaxf((fmaf((float)(hi[a] + 1), f.c, f.o[a]) - f.eps) - q[a], 0.0f);
+      lb2 = fminf(lb2, gap * gap);
+    }
   }
   for (int z = lo[2]; z <= hi[2]; ++z)
     for (int y = lo[1]; y <= hi[1]; ++y)
       for (int x = lo[0]; x <= hi[0]; ++x) {
         if (x == c[0] && y == c[1] && z == c[2]) continue;
         const int c3[3] = {x, y, z};
-        if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > lim) continue;
+        const float rd2 = f.range_d2(q, c3, c3);
+        if (rd2 * (1.0f - 1e-6f) > lim) {
+          lb2 = fminf(lb2, rd2);
+          continue;
+        }
         if (cell_lookup(g, cell_key(f.level, cloud, x, y, z), s, n))
-          scan_cell(g, s, n, q, dmax2, best, bj, lim);
+          scan_cell2(g, s, n, q, dmax2, best, bj, lim, lb2);
       }
   const int e0[3] = {c[0] - 1, c[1] - 1, c[2] - 1};
   const int e1[3] = {c[0] + 1, c[1] + 1, c[2] + 1};
-  return f.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim;
+  const float out2 = f.unexplored_d2(q, e0, e1);
+  lb2 = fminf(lb2, out2);
+  return out2 * (1.0f - 1e-6f) > lim;
 }
 
 // The per-lane form of warp_directory (same cells, same result), for queues
@@ -554,6 +598,9 @@ __device__ __noinline__ void close_round(IcpPairState& S, const double* tot, lon
     S.rmse = n > 0 ? sqrt(tot[27] / (double)n) : __longlong_as_double(0x7ff8000000000000ll);
     return;
   }
+  // the transform this round's searches used, for the next round's certificates
+  for (int j = 0; j < 12; ++j) S.Rt_prev[j] = S.Rt[j];
+  S.has_prev = 1;
   double dR[9], dt[3];
   if (metric == CIL_METRIC_POINT_TO_POINT) {
     if (n < 3 || !closed_form_rigid(tot, n, S.ref, dR, dt)) {
@@ -642,8 +689,10 @@ __global__ void k_icp_setup(IcpPairState* st, int pairs, const int* src_start, i
       rt_from_T(T, Rt);
       for (int j = 0; j < 12; ++j) {
         S.Rt[j] = Rt[j];
+        S.Rt_prev[j] = Rt[j];
         rt_out[12 * b + j] = Rt[j];
       }
+      S.has_prev = 0;
       const float d = dmax_dev ? dmax_dev[b] : dmax;
       S.dmax2 = d * d;
       // the pair's first target point (point-to-point sums are taken about it)
@@ -722,11 +771,23 @@ __device__ __forceinline__ int projective_match(const IcpArgs& a, int dst_start,
 }
 
 // Stage one of round `round` for the tile blockIdx.x.
+//
+// Certificate of an unchanged neighbour: a query whose previous round found
+// the target point q at FP32 position p0 = R0 p + t0, with every other target
+// point at least lb from p0, keeps q exactly when |p' - q| (1 + 1e-5) +
+// delta < lb, delta = |p' - p0| (1 + 1e-5): every other point is at least
+// lb - delta from p', more than |p' - q| by a relative margin far above the
+// FP32 rounding of squared distances, so the exact search would return q
+// too.  Converged rounds move points by micrometres, so most queries are
+// settled that way; the rest are packed onto the block's first threads for
+// the full first stage (whose lanes then do similar work).
 __global__ void __launch_bounds__(kIcpThreads) k_icp_search(IcpArgs a, int round) {
-  __shared__ float s_Rt[12];
+  __shared__ float s_Rt[12], s_Rp[12];
   __shared__ float s_dmax2;
-  __shared__ int s_pair;
-  const int tid = threadIdx.x, lane = tid & 31;
+  __shared__ int s_pair, s_prev;
+  __shared__ int s_wn[kIcpWarps];
+  __shared__ int s_list[kTileSrc];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tt = blockIdx.x;
   wait_previous_kernel();
   allow_next_kernel();
@@ -734,8 +795,13 @@ __global__ void __launch_bounds__(kIcpThreads) k_icp_search(IcpArgs a, int round
     const int b = pair_of(a.tile_off, a.pairs, tt);
     s_pair = b;
     s_dmax2 = a.st[b].dmax2;
+    s_prev = a.st[b].has_prev && a.opt.association != CIL_ASSOC_PROJECTIVE;
   }
-  if (tid < 12) s_Rt[tid] = a.st[pair_of(a.tile_off, a.pairs, tt)].Rt[tid];
+  if (tid < 12) {
+    const IcpPairState& S = a.st[pair_of(a.tile_off, a.pairs, tt)];
+    s_Rt[tid] = S.Rt[tid];
+    s_Rp[tid] = S.Rt_prev[tid];
+  }
   __syncthreads();
   const int b = s_pair;
   const int tb = __ldg(a.tile_off + b);
@@ -743,28 +809,76 @@ __global__ void __launch_bounds__(kIcpThreads) k_icp_search(IcpArgs a, int round
   const int se = a.src_start ? __ldg(a.src_start + b + 1) : a.n_src1;
   const int pos = sb + (tt - tb) * kTileSrc + tid;
   const int dst_start = a.g.prm[b].start;
+  const float dmax2 = s_dmax2;
+  bool todo = pos < se;
+  if (todo && s_prev) {
+    const int j = a.corr[pos];
+    const float lb = a.lbd[pos];
+    if (j >= 0 && lb > 0.0f) {
+      const int64_t si = __ldg(a.order + pos);
+      const float x = __ldg(a.src + 3 * si), y = __ldg(a.src + 3 * si + 1),
+                  z = __ldg(a.src + 3 * si + 2);
+      const float* R = s_Rt;
+      const float* R0 = s_Rp;
+      // the same operations as transformed_source
+      const float p[3] = {fmaf(R[0], x, fmaf(R[1], y, fmaf(R[2], z, R[3]))),
+                          fmaf(R[4], x, fmaf(R[5], y, fmaf(R[6], z, R[7]))),
+                          fmaf(R[8], x, fmaf(R[9], y, fmaf(R[10], z, R[11])))};
+      const float p0[3] = {fmaf(R0[0], x, fmaf(R0[1], y, fmaf(R0[2], z, R0[3]))),
+                           fmaf(R0[4], x, fmaf(R0[5], y, fmaf(R0[6], z, R0[7]))),
+                           fmaf(R0[8], x, fmaf(R0[9], y, fmaf(R0[10], z, R0[11])))};
+      const float delta = sqrtf(sqdist(p[0], p[1], p[2], p0[0], p0[1], p0[2])) * (1.0f + 1e-5f);
+      const float d2 = sqdist(__ldg(a.dst + 3 * (int64_t)j), __ldg(a.dst + 3 * (int64_t)j + 1),
+                              __ldg(a.dst + 3 * (int64_t)j + 2), p[0], p[1], p[2]);
+      if (fmaf(sqrtf(d2), 1.0f + 1e-5f, delta) < lb) {
+        todo = false;
+        const bool in = d2 <= dmax2;
+        a.corr[pos] = in ? j : -1;
+        a.lbd[pos] = in ? lb - delta : 0.0f;
+      }
+    }
+  }
+  // the remaining queries of the tile onto threads 0, 1, ... (in tile order)
+  const unsigned m = __ballot_sync(0xffffffffu, todo);
+  if (lane == 0) s_wn[warp] = __popc(m);
+  __syncthreads();
+  int off = 0, cnt = 0;
+#pragma unroll
+  for (int w = 0; w < kIcpWarps; ++w) {
+    off += w < warp ? s_wn[w] : 0;
+    cnt += s_wn[w];
+  }
+  if (todo) s_list[off + __popc(m & ((1u << lane) - 1u))] = pos;
+  __syncthreads();
   bool queued = false;
-  if (pos < se) {
+  int qpos = 0;
+  if (tid < cnt) {
+    qpos = s_list[tid];
     float p[3];
-    transformed_source(a, s_Rt, pos, p);
+    transformed_source(a, s_Rt, qpos, p);
+    int j;
+    float lb = 0.0f;
     if (a.opt.association == CIL_ASSOC_PROJECTIVE) {
-      a.corr[pos] = projective_match(a, dst_start, p, s_dmax2);
+      j = projective_match(a, dst_start, p, dmax2);
     } else {
       u64 best;
       int bj;
-      float lim;
-      queued = !base_search(a.g, b, p, s_dmax2, best, bj, lim);
+      float lim, lb2;
+      queued = !base_search(a.g, b, p, dmax2, best, bj, lim, lb2);
       // final, or stage one's best for k_icp_finish
-      a.corr[pos] = best == kEmptyKey ? -1 : dst_start + key_idx(best);
+      j = best == kEmptyKey ? -1 : dst_start + key_idx(best);
+      if (!queued && j >= 0) lb = sqrtf(lb2) * (1.0f - 1e-5f);
     }
+    a.corr[qpos] = j;
+    a.lbd[qpos] = lb;
   }
   // warp-aggregated append to the queue
-  const unsigned m = __ballot_sync(0xffffffffu, queued);
-  if (m) {
+  const unsigned mq = __ballot_sync(0xffffffffu, queued);
+  if (mq) {
     unsigned base = 0;
-    if (lane == __ffs(m) - 1) base = atomicAdd(a.qcount + (round & 1), (unsigned)__popc(m));
-    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-    if (queued) a.queue[base + __popc(m & ((1u << lane) - 1u))] = make_int2(pos, b);
+    if (lane == __ffs(mq) - 1) base = atomicAdd(a.qcount + (round & 1), (unsigned)__popc(mq));
+    base = __shfl_sync(0xffffffffu, base, __ffs(mq) - 1);
+    if (queued) a.queue[base + __popc(mq & ((1u << lane) - 1u))] = make_int2(qpos, b);
   }
 }
 
@@ -1162,6 +1276,7 @@ void icp_plan(IcpPlan& p, Workspace& ws, const int64_t* src_counts, int pairs) {
   p.o_grp_n = ws.reserve(sizeof(int) * ng);
   p.o_grp_done = ws.reserve(sizeof(int) * ng);
   p.o_corr = ws.reserve(sizeof(int) * ns);
+  p.o_lbd = ws.reserve(sizeof(float) * ns);
   p.o_queue = ws.reserve(sizeof(int2) * ns);
   p.o_qc = ws.reserve(sizeof(unsigned) * 4);
   order_plan(p.order, ws, p.n_src);
@@ -1208,6 +1323,7 @@ cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt, c
   a.rounds = iters + 1;
   a.st = st;
   a.corr = ws.at<int>(p.o_corr);
+  a.lbd = ws.at<float>(p.o_lbd);
   a.queue = ws.at<int2>(p.o_queue);
   a.qcount = qc;
   a.qhead = qc + 2;
