@@ -154,10 +154,11 @@ __device__ __forceinline__ void scan_cell2(const GridView& g, int s, int n, cons
 // converged source point finds its neighbour there).  Returns true when that
 // is exact (the ball stays inside the block).  best / bj / lim: packed key,
 // sorted position (-1: none) and min(dmax2, best d^2) of the best point.
-// lb2 (when exact): a lower bound on the squared distance from q to every
-// target point but the best -- the second best seen, the cells skipped or
-// outside the searched box (by their padded ranges), the space outside the
-// block and dmax2, whichever is least.
+// With kBound, lb2 (when exact): a lower bound on the squared distance from
+// q to every target point but the best -- the second best seen, the cells
+// skipped or outside the searched box (by their padded ranges), the space
+// outside the block and dmax2, whichever is least.
+template <bool kBound>
 __device__ __forceinline__ bool base_search(const GridView& g, int cloud, const float q[3],
                                             float dmax2, u64& best, int& bj, float& lim,
                                             float& lb2) {
@@ -172,8 +173,10 @@ __device__ __forceinline__ bool base_search(const GridView& g, int cloud, const 
   const int c[3] = {f.cell_of(q[0], 0, inv_fine), f.cell_of(q[1], 1, inv_fine),
                     f.cell_of(q[2], 2, inv_fine)};
   int s, n;
-  if (cell_lookup(g, cell_key(f.level, cloud, c[0], c[1], c[2]), s, n))
-    scan_cell2(g, s, n, q, dmax2, best, bj, lim, lb2);
+  if (cell_lookup(g, cell_key(f.level, cloud, c[0], c[1], c[2]), s, n)) {
+    if (kBound) scan_cell2(g, s, n, q, dmax2, best, bj, lim, lb2);
+    else scan_cell(g, s, n, q, dmax2, best, bj, lim);
+  }
   if (f.level >= kFineBits) return true;  // one cell holds the whole cloud
   // cells of the block meeting the ball of radius sqrt(lim) (padded)
   const float rad = fmaf(sqrtf(lim), 1.0f + 1e-6f, f.eps);
@@ -183,11 +186,11 @@ __device__ __forceinline__ bool base_search(const GridView& g, int cloud, const 
     lo[a] = max(f.cell_of(q[a] - rad, a, inv_fine), c[a] - 1);
     hi[a] = min(f.cell_of(q[a] + rad, a, inv_fine), c[a] + 1);
     // block cells below lo / above hi on this axis: beyond these faces
-    if (lo[a] > c[a] - 1 && lo[a] > 0) {
+    if (kBound && lo[a] > c[a] - 1 && lo[a] > 0) {
       const float gap = fmaxf(q[a] - (fmaf((float)lo[a], f.c, f.o[a]) + f.eps), 0.0f);
       lb2 = fminf(lb2, gap * gap);
     }
-    if (hi[a] < c[a] + 1 && hi[a] < f.hi[a]) {
+    if (kBound && hi[a] < c[a] + 1 && hi[a] < f.hi[a]) {
       const float gap = fmaxf((fmaf((float)(hi[a] + 1), f.c, f.o[a]) - f.eps) - q[a], 0.0f);
       lb2 = fminf(lb2, gap * gap);
     }
@@ -199,16 +202,18 @@ __device__ __forceinline__ bool base_search(const GridView& g, int cloud, const 
         const int c3[3] = {x, y, z};
         const float rd2 = f.range_d2(q, c3, c3);
         if (rd2 * (1.0f - 1e-6f) > lim) {
-          lb2 = fminf(lb2, rd2);
+          if (kBound) lb2 = fminf(lb2, rd2);
           continue;
         }
-        if (cell_lookup(g, cell_key(f.level, cloud, x, y, z), s, n))
-          scan_cell2(g, s, n, q, dmax2, best, bj, lim, lb2);
+        if (cell_lookup(g, cell_key(f.level, cloud, x, y, z), s, n)) {
+          if (kBound) scan_cell2(g, s, n, q, dmax2, best, bj, lim, lb2);
+          else scan_cell(g, s, n, q, dmax2, best, bj, lim);
+        }
       }
   const int e0[3] = {c[0] - 1, c[1] - 1, c[2] - 1};
   const int e1[3] = {c[0] + 1, c[1] + 1, c[2] + 1};
   const float out2 = f.unexplored_d2(q, e0, e1);
-  lb2 = fminf(lb2, out2);
+  if (kBound) lb2 = fminf(lb2, out2);
   return out2 * (1.0f - 1e-6f) > lim;
 }
 
@@ -780,10 +785,14 @@ __device__ __forceinline__ int projective_match(const IcpArgs& a, int dst_start,
 // FP32 rounding of squared distances, so the exact search would return q
 // too.  Converged rounds move points by micrometres, so most queries are
 // settled that way; the rest are packed onto the block's first threads for
-// the full first stage (whose lanes then do similar work).
-__global__ void __launch_bounds__(kIcpThreads) k_icp_search(IcpArgs a, int round) {
+// the full first stage (whose lanes then do similar work).  The full search
+// records the bound for the next round only for a query that moved less
+// than kCertMove cell edges in this round (one that moves more would rarely
+// certify next round, and the bound costs registers and instructions).
+constexpr float kCertMove = 0.1f;
+__global__ void __launch_bounds__(kIcpThreads, 4) k_icp_search(IcpArgs a, int round) {
   __shared__ float s_Rt[12], s_Rp[12];
-  __shared__ float s_dmax2;
+  __shared__ float s_dmax2, s_move;
   __shared__ int s_pair, s_prev;
   __shared__ int s_wn[kIcpWarps];
   __shared__ int s_list[kTileSrc];
@@ -796,6 +805,7 @@ __global__ void __launch_bounds__(kIcpThreads) k_icp_search(IcpArgs a, int round
     s_pair = b;
     s_dmax2 = a.st[b].dmax2;
     s_prev = a.st[b].has_prev && a.opt.association != CIL_ASSOC_PROJECTIVE;
+    s_move = kCertMove * a.g.prm[b].cell;
   }
   if (tid < 12) {
     const IcpPairState& S = a.st[pair_of(a.tile_off, a.pairs, tt)];
@@ -811,10 +821,11 @@ __global__ void __launch_bounds__(kIcpThreads) k_icp_search(IcpArgs a, int round
   const int dst_start = a.g.prm[b].start;
   const float dmax2 = s_dmax2;
   bool todo = pos < se;
+  bool want_lb = false;  // record the bound for the next round
   if (todo && s_prev) {
     const int j = a.corr[pos];
     const float lb = a.lbd[pos];
-    if (j >= 0 && lb > 0.0f) {
+    {
       const int64_t si = __ldg(a.order + pos);
       const float x = __ldg(a.src + 3 * si), y = __ldg(a.src + 3 * si + 1),
                   z = __ldg(a.src + 3 * si + 2);
@@ -828,13 +839,16 @@ __global__ void __launch_bounds__(kIcpThreads) k_icp_search(IcpArgs a, int round
                            fmaf(R0[4], x, fmaf(R0[5], y, fmaf(R0[6], z, R0[7]))),
                            fmaf(R0[8], x, fmaf(R0[9], y, fmaf(R0[10], z, R0[11])))};
       const float delta = sqrtf(sqdist(p[0], p[1], p[2], p0[0], p0[1], p0[2])) * (1.0f + 1e-5f);
-      const float d2 = sqdist(__ldg(a.dst + 3 * (int64_t)j), __ldg(a.dst + 3 * (int64_t)j + 1),
-                              __ldg(a.dst + 3 * (int64_t)j + 2), p[0], p[1], p[2]);
-      if (fmaf(sqrtf(d2), 1.0f + 1e-5f, delta) < lb) {
-        todo = false;
-        const bool in = d2 <= dmax2;
-        a.corr[pos] = in ? j : -1;
-        a.lbd[pos] = in ? lb - delta : 0.0f;
+      want_lb = delta < s_move;
+      if (j >= 0 && lb > 0.0f) {
+        const float d2 = sqdist(__ldg(a.dst + 3 * (int64_t)j), __ldg(a.dst + 3 * (int64_t)j + 1),
+                                __ldg(a.dst + 3 * (int64_t)j + 2), p[0], p[1], p[2]);
+        if (fmaf(sqrtf(d2), 1.0f + 1e-5f, delta) < lb) {
+          todo = false;
+          const bool in = d2 <= dmax2;
+          a.corr[pos] = in ? j : -1;
+          a.lbd[pos] = in ? lb - delta : 0.0f;
+        }
       }
     }
   }
@@ -848,12 +862,14 @@ __global__ void __launch_bounds__(kIcpThreads) k_icp_search(IcpArgs a, int round
     off += w < warp ? s_wn[w] : 0;
     cnt += s_wn[w];
   }
-  if (todo) s_list[off + __popc(m & ((1u << lane) - 1u))] = pos;
+  if (todo) s_list[off + __popc(m & ((1u << lane) - 1u))] = want_lb ? (pos | (1 << 31)) : pos;
   __syncthreads();
   bool queued = false;
   int qpos = 0;
   if (tid < cnt) {
-    qpos = s_list[tid];
+    const int e = s_list[tid];
+    const bool bound = e < 0;
+    qpos = e & 0x7fffffff;
     float p[3];
     transformed_source(a, s_Rt, qpos, p);
     int j;
@@ -864,10 +880,11 @@ __global__ void __launch_bounds__(kIcpThreads) k_icp_search(IcpArgs a, int round
       u64 best;
       int bj;
       float lim, lb2;
-      queued = !base_search(a.g, b, p, dmax2, best, bj, lim, lb2);
+      queued = bound ? !base_search<true>(a.g, b, p, dmax2, best, bj, lim, lb2)
+                     : !base_search<false>(a.g, b, p, dmax2, best, bj, lim, lb2);
       // final, or stage one's best for k_icp_finish
       j = best == kEmptyKey ? -1 : dst_start + key_idx(best);
-      if (!queued && j >= 0) lb = sqrtf(lb2) * (1.0f - 1e-5f);
+      if (bound && !queued && j >= 0) lb = sqrtf(lb2) * (1.0f - 1e-5f);
     }
     a.corr[qpos] = j;
     a.lbd[qpos] = lb;
