@@ -83,15 +83,20 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_rows(const long long* __r
   const long long b = off[row];
   const int n = (int)(off[row + 1] - b);
   if (n <= 1) return;
-  int np = 1;
-  while (np < n) np <<= 1;
+  int np = 1, lg = 0;
+  while (np < n) {
+    np <<= 1;
+    ++lg;
+  }
   if (n <= kRowCap) {
     for (int i = threadIdx.x; i < n; i += kSortThreads) sk[i] = pack_key(d2[b + i], idx[b + i]);
     __syncthreads();
-    for (int size = 2; size <= np; size <<= 1) {
+    // sizes are powers of two: block and offset by shift and mask
+    for (int ls = 1; ls <= lg; ++ls) {
+      const int size = 1 << ls, half = size >> 1;
       for (int t = threadIdx.x; t < np / 2; t += kSortThreads) {
-        const int blk = t / (size / 2), o = t % (size / 2);
-        const int i = blk * size + o, j = blk * size + size - 1 - o;
+        const int blk = t >> (ls - 1), o = t & (half - 1);
+        const int i = (blk << ls) + o, j = (blk << ls) + size - 1 - o;
         if (j < n) cmp_swap_keys(sk[i], sk[j]);
       }
       __syncthreads();
@@ -109,14 +114,15 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_rows(const long long* __r
       idx[b + i] = key_idx(sk[i]);
     }
   } else {
-    for (int size = 2; size <= np; size <<= 1) {
+    for (int ls = 1; ls <= lg; ++ls) {
+      const int size = 1 << ls;
       for (int stride = size / 2; stride > 0; stride >>= 1) {
         for (int t = threadIdx.x; t < np / 2; t += kSortThreads) {
           int i, j;
           if (stride == size / 2) {
-            const int blk = t / (size / 2), o = t % (size / 2);
-            i = blk * size + o;
-            j = blk * size + size - 1 - o;
+            const int blk = t >> (ls - 1), o = t & (stride - 1);
+            i = (blk << ls) + o;
+            j = (blk << ls) + size - 1 - o;
           } else {
             i = 2 * t - (t & (stride - 1));
             j = i + stride;
