@@ -84,3 +84,18 @@ def test_lidar_sampled():
     p = synth.lidar_sweep_pair(0)
     rows = np.random.default_rng(3).choice(len(p.target), 300, replace=False)
     _check(p.target, None, 0.5, rows=rows)
+
+
+@pytest.mark.parametrize("r", [1.0, 2.9, 4.0, 5.0, 6.0])
+def test_lattice_rows_across_sort_paths(r):
+    """Integer lattice (exact distances, many exact ties, so the index order
+    inside equal distances is checked bit for bit) with row lengths from a
+    few to about a thousand: rows up to 512 keys take the register sort,
+    longer ones the shared-memory sort."""
+    pts = synth.lattice_points((16, 16, 16))
+    go, gi, gd = _gpu_radius(pts, None, r)
+    oo, oi, od = oracle.radius(pts, pts, r)
+    assert np.array_equal(go, oo) and np.array_equal(gi, oi)
+    assert np.array_equal(gd.astype(np.float64), od)
+    lengths = np.diff(go)
+    assert lengths.max() >= 7
