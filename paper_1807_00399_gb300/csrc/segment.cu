@@ -21,6 +21,7 @@ namespace cil {
 
 constexpr int kSegThreads = 256;
 constexpr int kUnionSteps = 1 << 20;  // a union needs far fewer; the cap only bounds the loop
+constexpr int kSegFirst = 3;           // list entries joined before the compression pass
 
 __device__ __forceinline__ int parent_of(const int* parent, int x) {
   return *reinterpret_cast<const volatile int*>(parent + x);
@@ -70,13 +71,13 @@ __global__ void k_seg_init(int* parent, int64_t n) {
   if (i < n) parent[i] = (int)i;
 }
 
-// One thread per point i, one union per kept edge of its list.  ra tracks a
-// member of i's set; an edge whose far end hangs directly below ra (or is ra)
-// is skipped with one load, which after path halving is most edges inside a
-// grown component.  (Measured on the 4.49M-point scan: 3.8 ms against 4.1 ms
-// for a find from both ends per edge, and 5.1 ms when all similarities are
-// taken before the first union.)
+// One thread per point i, one union per kept edge among list entries
+// [m0, m1).  ra tracks a member of i's set (its parent to begin with); an
+// edge whose far end hangs directly below ra (or is ra) is skipped with one
+// load, which after a compression pass is nearly every edge inside a grown
+// component.
 __global__ void __launch_bounds__(kSegThreads) k_seg_union(const int* __restrict__ idx, int k,
+                                                           int m0, int m1,
                                                            const float* __restrict__ xyz,
                                                            const float* __restrict__ nrm, int64_t n,
                                                            const float4* __restrict__ sorted,
@@ -89,8 +90,8 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_union(const int* __restrict
   const int64_t i = sorted ? (int64_t)__float_as_int(__ldg(sorted + t).w) : t;
   const float nx = __ldg(nrm + 3 * i), ny = __ldg(nrm + 3 * i + 1), nz = __ldg(nrm + 3 * i + 2);
   const float px = __ldg(xyz + 3 * i), py = __ldg(xyz + 3 * i + 1), pz = __ldg(xyz + 3 * i + 2);
-  int ra = (int)i;
-  for (int m = 0; m < k; ++m) {
+  int ra = parent_of(parent, (int)i);
+  for (int m = m0; m < m1; ++m) {
     const int j = __ldg(idx + i * k + m);
     if (j < 0 || j == (int)i) continue;
     const float dot = dot3_rn(nx, ny, nz, __ldg(nrm + 3 * (int64_t)j),
@@ -110,6 +111,12 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_union(const int* __restrict
   }
 }
 
+// every point straight below its root (no union runs meanwhile)
+__global__ void k_seg_compress(int* parent, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) parent[i] = find_root(parent, (int)i);
+}
+
 __global__ void k_seg_labels(int* parent, int64_t n, int32_t* labels, unsigned long long* count) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int roots = 0;
@@ -126,11 +133,17 @@ cil_status launch_segment(const int* knn_idx, int k, const float* xyz, const flo
                           const float4* sorted, float cos_t, float r2, int* parent, int32_t* labels,
                           unsigned long long* count, int* err, cudaStream_t s) {
   TimedRegion timer("segment", s);
-  note_launches(3);
+  note_launches(5);
   const int blocks = ceil_div(n, kSegThreads);
   k_seg_init<<<blocks, kSegThreads, 0, s>>>(parent, n);
-  k_seg_union<<<blocks, kSegThreads, 0, s>>>(knn_idx, k, xyz, nrm, n, sorted, cos_t, r2, parent,
-                                             err);
+  // the nearest few edges first (mostly distinct small trees, little
+  // contention), every point then straight below its root, then the rest
+  const int mA = k < kSegFirst ? k : kSegFirst;
+  k_seg_union<<<blocks, kSegThreads, 0, s>>>(knn_idx, k, 0, mA, xyz, nrm, n, sorted, cos_t, r2,
+                                             parent, err);
+  k_seg_compress<<<blocks, kSegThreads, 0, s>>>(parent, n);
+  k_seg_union<<<blocks, kSegThreads, 0, s>>>(knn_idx, k, mA, k, xyz, nrm, n, sorted, cos_t, r2,
+                                             parent, err);
   if (cudaMemsetAsync(count, 0, sizeof(unsigned long long), s) != cudaSuccess) return CIL_ERR_CUDA;
   k_seg_labels<<<blocks, kSegThreads, 0, s>>>(parent, n, labels, count);
   return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
