@@ -38,9 +38,7 @@ struct GridParams {
   int start;           // offset of this cloud in the concatenated arrays
   unsigned bbox_enc[6];// order-preserving integer encodings (min x,y,z, max x,y,z)
   int nonfinite;       // number of non-finite coordinates seen
-  int level2;          // correspondence-search level (ICP), -1 if not built
-  float cell2;         // fine * 2^level2
-  int pad;
+  int pad[3];
 };
 
 struct __align__(16) CellEntry {
@@ -55,8 +53,6 @@ struct GridView {
   const float4* pts;      // sorted points: x, y, z, local index (int bits)
   const CellEntry* tab;   // hash table of the k-NN level
   unsigned mask;          // table size - 1 (power of two)
-  const CellEntry* tab2;  // hash table of the correspondence level (or null)
-  unsigned mask2;
 };
 
 // ---------------------------------------------------------------------------

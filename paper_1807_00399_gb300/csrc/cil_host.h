@@ -62,8 +62,6 @@ class Workspace {
 struct GridPlan {
   int64_t n = 0;        // total points
   int clouds = 1;
-  bool icp_table = false;  // also build the correspondence-level table
-  size_t o_tab2 = 0;
   unsigned mask = 0;    // table size - 1
   int radix_blocks = 0;
   // workspace offsets
@@ -81,13 +79,10 @@ struct GridOptions {
   int k_est = 10;          // neighbourhood size the level is tuned for
   float cell_size = 0.0f;  // > 0: requested cell edge
   float cell_scale = kDefaultCellScale;  // multiplier on the data-driven size
-  float icp_dmax = 0.0f;   // > 0: correspondence level with cell >= icp_scale * icp_dmax
-  float icp_scale = 0.5f;
 };
 
-// Reserve the workspace parts of a grid over `n` points in `clouds` clouds
-// (with `icp_table`, also the hash table of the correspondence level).
-void grid_plan(GridPlan& p, Workspace& ws, int64_t n, int clouds, bool icp_table = false);
+// Reserve the workspace parts of a grid over `n` points in `clouds` clouds.
+void grid_plan(GridPlan& p, Workspace& ws, int64_t n, int clouds);
 
 // Enqueue the build.  `xyz` holds the concatenated clouds; `cloud_start_dev`
 // (device, clouds+1 int32) their offsets (may be null when clouds == 1).

@@ -67,9 +67,7 @@ __global__ void k_init_params(GridParams* prm, int clouds, const int* cs, int64_
   P.level = 0;
   P.cell = 1.0f;
   P.nonfinite = 0;
-  P.level2 = -1;
-  P.cell2 = 1.0f;
-  P.pad = 0;
+  P.pad[0] = P.pad[1] = P.pad[2] = 0;
   prm[b] = P;
 }
 
@@ -464,8 +462,7 @@ __global__ void k_gather_sorted(const u64* __restrict__ keys, const int* __restr
 template <int KMAX>
 __global__ void __launch_bounds__(1024) k_choose_level(GridParams* prm, const float4* __restrict__ pts,
                                                        int k_default, const int* cloud_k,
-                                                       float cell_size, float cell_scale,
-                                                       float icp_dmax, float icp_scale) {
+                                                       float cell_size, float cell_scale) {
   constexpr int S = 1024;
   __shared__ float est[S];
   GridParams& P = prm[blockIdx.x];
@@ -523,28 +520,16 @@ __global__ void __launch_bounds__(1024) k_choose_level(GridParams* prm, const fl
     L = max(0, min(L, kFineBits));
     P.level = L;
     P.cell = ldexpf(fine, L);
-    if (icp_dmax > 0.0f) {
-      // correspondence level: cells of at least icp_scale * d_max, so a search
-      // bounded by d_max never visits more than (2 ceil(1/icp_scale) + 1)^3 cells
-      const float r2 = (icp_dmax * icp_scale) / fine;
-      int L2 = r2 <= 1.0f ? 0 : (int)ceilf(log2f(r2));
-      L2 = max(0, min(L2, kFineBits));
-      P.level2 = L2;
-      P.cell2 = ldexpf(fine, L2);
-    }
   }
 }
 
 // ---------------------------------------------------------------------------
 // 6. cell table
 // ---------------------------------------------------------------------------
-// Levels hashed in a table: table 0 holds the cloud's level L, the
-// directory level of the correspondence search (L + 2) and the k-NN
-// escalation levels (L + 3, + 6, + 9), each capped at 10, duplicates
-// dropped; table 1 the correspondence level only.  -1 when the table has no
-// such slot.
-__device__ __forceinline__ int table_level(const GridParams& P, int which, int slot) {
-  if (which) return slot == 0 ? P.level2 : -1;
+// Levels hashed in the table: the cloud's level L, the directory level of
+// the correspondence search (L + 2) and the k-NN escalation levels (L + 3,
+// + 6, + 9), each capped at 10, duplicates dropped (-1).
+__device__ __forceinline__ int table_level(const GridParams& P, int slot) {
   const int add[5] = {0, 2, 3, 6, 9};
   const int lvl = min(P.level + add[slot], kFineBits);
   if (slot > 0 && lvl == min(P.level + add[slot - 1], kFineBits)) return -1;
@@ -565,13 +550,13 @@ __device__ __forceinline__ u64 key_cell(u64 key, int L) {
 }
 
 __global__ void k_cells_insert(const u64* __restrict__ keys, int64_t n, const GridParams* prm,
-                               int which, CellEntry* tab, unsigned mask) {
+                               CellEntry* tab, unsigned mask) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const u64 key = keys[i];
   const GridParams& P = prm[(int)(key >> 30)];
   for (int slot = 0; slot < kTableSlots; ++slot) {
-    const int L = table_level(P, which, slot);
+    const int L = table_level(P, slot);
     if (L < 0) break;
     if (i > 0 && same_cell(keys[i - 1], key, L)) continue;
     const u64 K = key_cell(key, L);
@@ -587,13 +572,13 @@ __global__ void k_cells_insert(const u64* __restrict__ keys, int64_t n, const Gr
 }
 
 __global__ void k_cells_count(const u64* __restrict__ keys, int64_t n, const GridParams* prm,
-                              int which, CellEntry* tab, unsigned mask) {
+                              CellEntry* tab, unsigned mask) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const u64 key = keys[i];
   const GridParams& P = prm[(int)(key >> 30)];
   for (int slot = 0; slot < kTableSlots; ++slot) {
-    const int L = table_level(P, which, slot);
+    const int L = table_level(P, slot);
     if (L < 0) break;
     if (i + 1 < n && same_cell(keys[i + 1], key, L)) continue;
     const u64 K = key_cell(key, L);
@@ -611,10 +596,9 @@ __global__ void k_cells_count(const u64* __restrict__ keys, int64_t n, const Gri
 // ---------------------------------------------------------------------------
 // host drivers
 // ---------------------------------------------------------------------------
-void grid_plan(GridPlan& p, Workspace& ws, int64_t n, int clouds, bool icp_table) {
+void grid_plan(GridPlan& p, Workspace& ws, int64_t n, int clouds) {
   p.n = n;
   p.clouds = clouds;
-  p.icp_table = icp_table;
   // cells hashed in the table: at most min(points, cells of the level) for
   // each of its <= 5 levels (L, L+2, L+3, L+6, L+9); whatever the cloud's
   // level, that is <= 3n + 16^3 + 2^3 per cloud.  Keep the load factor <= 1/2.
@@ -632,7 +616,6 @@ void grid_plan(GridPlan& p, Workspace& ws, int64_t n, int clouds, bool icp_table
   p.o_counts = ws.reserve(sizeof(int) * (size_t)kRadix * p.radix_blocks);
   p.o_scan = ws.reserve(sizeof(int) * scan_tmp_ints((int64_t)kRadix * p.radix_blocks));
   p.o_starts = 0;
-  p.o_tab2 = icp_table ? ws.reserve(sizeof(CellEntry) * slots) : 0;
 }
 
 GridView grid_view(const GridPlan& p, const Workspace& ws) {
@@ -641,8 +624,6 @@ GridView grid_view(const GridPlan& p, const Workspace& ws) {
   g.pts = ws.at<float4>(p.o_pts);
   g.tab = ws.at<CellEntry>(p.o_tab);
   g.mask = p.mask;
-  g.tab2 = p.icp_table ? ws.at<CellEntry>(p.o_tab2) : nullptr;
-  g.mask2 = p.mask;
   return g;
 }
 
@@ -663,10 +644,6 @@ cil_status grid_build(const GridPlan& p, const Workspace& ws, const float* xyz,
   if (cudaMemsetAsync(ws.at<CellEntry>(p.o_tab), 0xff, sizeof(CellEntry) * (size_t)slots, s) !=
       cudaSuccess)
     return CIL_ERR_CUDA;
-  if (p.icp_table &&
-      cudaMemsetAsync(ws.at<CellEntry>(p.o_tab2), 0xff, sizeof(CellEntry) * (size_t)slots, s) !=
-          cudaSuccess)
-    return CIL_ERR_CUDA;
   if (n > 0) {
     u64* k0 = ws.at<u64>(p.o_keys0);
     u64* k1 = ws.at<u64>(p.o_keys1);
@@ -681,19 +658,10 @@ cil_status grid_build(const GridPlan& p, const Workspace& ws, const float* xyz,
     float4* pts = ws.at<float4>(p.o_pts);
     k_gather_sorted<<<ceil_div(n, 256), 256, 0, s>>>(ks, vs, n, xyz, prm, pts);
     const int kk = opt.k_est < 1 ? 1 : (opt.k_est > 32 ? 32 : opt.k_est);
-    const float icp_d = p.icp_table ? opt.icp_dmax : 0.0f;
-    const float icp_s = opt.icp_scale > 0.0f ? opt.icp_scale : 0.5f;
     CIL_FOR_K(kk, (k_choose_level<KM><<<p.clouds, 1024, 0, s>>>(prm, pts, kk, nullptr, opt.cell_size,
-                                                                opt.cell_scale, icp_d, icp_s)));
-    k_cells_insert<<<ceil_div(n, 256), 256, 0, s>>>(ks, n, prm, 0, ws.at<CellEntry>(p.o_tab), p.mask);
-    k_cells_count<<<ceil_div(n, 256), 256, 0, s>>>(ks, n, prm, 0, ws.at<CellEntry>(p.o_tab), p.mask);
-    if (p.icp_table) {
-      note_launches(2);
-      k_cells_insert<<<ceil_div(n, 256), 256, 0, s>>>(ks, n, prm, 1, ws.at<CellEntry>(p.o_tab2),
-                                                      p.mask);
-      k_cells_count<<<ceil_div(n, 256), 256, 0, s>>>(ks, n, prm, 1, ws.at<CellEntry>(p.o_tab2),
-                                                     p.mask);
-    }
+                                                                opt.cell_scale)));
+    k_cells_insert<<<ceil_div(n, 256), 256, 0, s>>>(ks, n, prm, ws.at<CellEntry>(p.o_tab), p.mask);
+    k_cells_count<<<ceil_div(n, 256), 256, 0, s>>>(ks, n, prm, ws.at<CellEntry>(p.o_tab), p.mask);
   }
   return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
 }
