@@ -3,11 +3,13 @@
 //
 // Every round of every pair runs as three launches over tiles of kIcpThreads
 // source points (all pairs' tiles together in batched mode):
-//   k_icp_search      p' = R p + t (FP32) and the first stage of the exact
-//                     nearest-neighbour search within the rejection distance
-//                     (the query's cell, then the cells of its 3x3x3 block
-//                     meeting the ball of the best distance so far); queries
-//                     whose ball leaves the block go to a queue;
+//   k_icp_search      p' = R p + t (FP32); a query whose previous neighbour
+//                     is certified unchanged keeps it, the others run the
+//                     first stage of the exact nearest-neighbour search within
+//                     the rejection distance (the query's cell, then the cells
+//                     of its 3x3x3 block meeting the ball of the best distance
+//                     so far); queries whose ball leaves the block go to a
+//                     queue;
 //   k_icp_finish      each queued query is finished by one whole warp: the
 //                     cells of the directory level meeting its ball are looked
 //                     up by the lanes in parallel and their points scanned

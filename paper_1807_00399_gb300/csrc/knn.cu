@@ -4,7 +4,8 @@
 // reference grid (self-queries: the sorted points themselves; external
 // queries: a stable Morton sort of the queries), so the threads of a warp
 // search neighbouring cells and share their loads through L1.  Each thread
-// keeps its k best (squared distance, index) keys sorted in registers.
+// keeps its k best (squared distance, index) keys: sorted in registers for
+// k <= 4, in a max-heap in shared memory above (heap-sorted at the end).
 //
 // Normals (Sec. 3 normal/curvature estimation, Sec. 4 10-NN neighbourhoods):
 // the k neighbours' offsets from the query give their mean, then the centred
