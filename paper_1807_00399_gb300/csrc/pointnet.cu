@@ -274,11 +274,15 @@ __global__ void __launch_bounds__(kEncThreads, 1) k_pn_encode(const float* __res
 // ---------------------------------------------------------------------------
 // encoder forward on the 5th-generation tensor cores (tcgen05 + TMEM)
 // ---------------------------------------------------------------------------
-// 128 threads; thread r owns point row r of a 128-point tile.  Operands live in
-// shared memory as K-major BF16 tiles with the 128-byte swizzle (64-element
-// rows); the two GEMMs accumulate in tensor memory (columns 0..127: layer 2,
-// 128..383: layer 3), issued by one thread and completed through an mbarrier.
-constexpr int kTcThreads = 128;
+// 256 threads in two halves: threads r and r + 128 own point row r of a
+// 128-point tile (warp w reads tensor-memory lanes 32 (w % 4) ..), the first
+// half the low, the second the high half of each layer's channels, so the
+// CUDA-core work between the MMAs (layer 1, the two epilogues) is split over
+// eight warps.  Operands live in shared memory as K-major BF16 tiles with the
+// 128-byte swizzle (64-element rows); the two GEMMs accumulate in tensor
+// memory (columns 0..127: layer 2, 128..383: layer 3), issued by one thread
+// and completed through an mbarrier.
+constexpr int kTcThreads = 256;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kMbarPolls = 1u << 26;  // bounded wait (~seconds)
 
@@ -291,7 +295,7 @@ struct EncTcSmem {
   float b1[kH1];
   float b2[kH2];
   float b3[kH3];
-  float red[4][32][33];          // per-warp transpose for the column max
+  float red[8][32][33];          // per-warp transpose for the column max
   u64 wmax[4][kH3];              // per-warp column maxima of one tile
   uint64_t bar;
   uint32_t tmem_base;
@@ -309,6 +313,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pn_encode_tc(
   const uint32_t raw_s = tc::smem_u32(smem_raw);
   EncTcSmem& S = *reinterpret_cast<EncTcSmem*>(smem_raw + (((raw_s + 1023u) & ~1023u) - raw_s));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int quarter = warp & 3;  // tensor-memory lanes (tile rows) 32 quarter ..
+  const int half = warp >> 2;    // which half of each layer's channels
+  const int row = tid & 127;     // this thread's tile row
   if (warp == 0) {
     tc::tmem_alloc(&S.tmem_base, kTmemCols);
     tc::tmem_relinquish();
@@ -338,7 +345,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pn_encode_tc(
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = S.tmem_base;
-  const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+  const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
   const uint32_t id2 = tc::idesc_bf16_f32(128, kH2);
   const uint32_t id3 = tc::idesc_bf16_f32(128, kH3);
   uint32_t phase = 0;
@@ -348,12 +355,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pn_encode_tc(
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
     const int cloud = t / tiles_per_cloud;
     const int row0 = (t % tiles_per_cloud) * kTileP;
-    // ---- layer 1 (FP32 ALU): row tid, 64 channels -> bf16 A1 ----
+    // ---- layer 1 (FP32 ALU): row `row`, channels 32 half .. + 32 -> bf16 A1 ----
     {
-      const float* xp = X + ((int64_t)cloud * P + row0 + tid) * 3;
+      const float* xp = X + ((int64_t)cloud * P + row0 + row) * 3;
       const float x = xp[0], y = xp[1], z = xp[2];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
+      for (int cc = 0; cc < 4; ++cc) {
+        const int c = 4 * half + cc;
         unsigned w[4];
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
@@ -363,7 +371,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pn_encode_tc(
           const float z1 = fmaf(wr[3], x, fmaf(wr[4], y, fmaf(wr[5], z, S.b1[ch + 1])));
           w[h] = pack_bf16x2(fmaxf(z0, 0.0f), fmaxf(z1, 0.0f));
         }
-        *reinterpret_cast<uint4*>(S.a1 + tc::sw128_offset(tid, 8 * c)) =
+        *reinterpret_cast<uint4*>(S.a1 + tc::sw128_offset(row, 8 * c)) =
             make_uint4(w[0], w[1], w[2], w[3]);
       }
     }
@@ -389,7 +397,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pn_encode_tc(
     tc::tc_fence_after();
     // ---- epilogue 2: bias + relu -> bf16 A2 (two 64-wide k blocks) ----
 #pragma unroll 1
-    for (int j = 0; j < 4; ++j) {
+    for (int jj = 0; jj < 2; ++jj) {
+      const int j = 2 * half + jj;
       float v[32];
       tc::tmem_ld32(tmem + lane_base + 32 * j, v);
       uint8_t* blk = S.a2[j >> 1];
@@ -402,7 +411,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pn_encode_tc(
           w[h] = pack_bf16x2(fmaxf(v[8 * c + 2 * h] + S.b2[col], 0.0f),
                              fmaxf(v[8 * c + 2 * h + 1] + S.b2[col + 1], 0.0f));
         }
-        *reinterpret_cast<uint4*>(blk + tc::sw128_offset(tid, (32 * j + 8 * c) & 63)) =
+        *reinterpret_cast<uint4*>(blk + tc::sw128_offset(row, (32 * j + 8 * c) & 63)) =
             make_uint4(w[0], w[1], w[2], w[3]);
       }
     }
@@ -429,7 +438,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pn_encode_tc(
     tc::tc_fence_after();
     // ---- epilogue 3: bias + relu, column (value, row) max of the tile ----
 #pragma unroll 1
-    for (int j = 0; j < 8; ++j) {
+    for (int jj = 0; jj < 4; ++jj) {
+      const int j = 4 * half + jj;
       float v[32];
       tc::tmem_ld32(tmem + lane_base + kH2 + 32 * j, v);
 #pragma unroll
@@ -444,7 +454,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pn_encode_tc(
           br = rr;
         }
       }
-      S.wmax[warp][32 * j + lane] = feat_pack(best, row0 + 32 * warp + br);
+      S.wmax[quarter][32 * j + lane] = feat_pack(best, row0 + 32 * quarter + br);
       __syncwarp();
     }
     tc::tc_fence_before();
