@@ -274,15 +274,16 @@ __global__ void __launch_bounds__(kEncThreads, 1) k_pn_encode(const float* __res
 // ---------------------------------------------------------------------------
 // encoder forward on the 5th-generation tensor cores (tcgen05 + TMEM)
 // ---------------------------------------------------------------------------
-// 256 threads in two halves: threads r and r + 128 own point row r of a
-// 128-point tile (warp w reads tensor-memory lanes 32 (w % 4) ..), the first
-// half the low, the second the high half of each layer's channels, so the
-// CUDA-core work between the MMAs (layer 1, the two epilogues) is split over
-// eight warps.  Operands live in shared memory as K-major BF16 tiles with the
+// kTcParts x 128 threads: threads r, r + 128, ... own point row r of a
+// 128-point tile (warp w reads tensor-memory lanes 32 (w % 4) ..), part
+// w / 4 one kTcParts-th of each layer's channels, so the CUDA-core work
+// between the MMAs (layer 1, the two epilogues) is split over 4 kTcParts
+// warps.  Operands live in shared memory as K-major BF16 tiles with the
 // 128-byte swizzle (64-element rows); the two GEMMs accumulate in tensor
 // memory (columns 0..127: layer 2, 128..383: layer 3), issued by one thread
 // and completed through an mbarrier.
-constexpr int kTcThreads = 256;
+constexpr int kTcParts = 4;
+constexpr int kTcThreads = 128 * kTcParts;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kMbarPolls = 1u << 26;  // bounded wait (~seconds)
 
@@ -295,7 +296,7 @@ struct EncTcSmem {
   float b1[kH1];
   float b2[kH2];
   float b3[kH3];
-  float red[8][32][33];          // per-warp transpose for the column max
+  float red[4 * kTcParts][32][33];  // per-warp transpose for the column max
   u64 wmax[4][kH3];              // per-warp column maxima of one tile
   uint64_t bar;
   uint32_t tmem_base;
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pn_encode_tc(
   EncTcSmem& S = *reinterpret_cast<EncTcSmem*>(smem_raw + (((raw_s + 1023u) & ~1023u) - raw_s));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int quarter = warp & 3;  // tensor-memory lanes (tile rows) 32 quarter ..
-  const int half = warp >> 2;    // which half of each layer's channels
+  const int half = warp >> 2;    // which part of each layer's channels
   const int row = tid & 127;     // this thread's tile row
   if (warp == 0) {
     tc::tmem_alloc(&S.tmem_base, kTmemCols);
@@ -355,13 +356,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pn_encode_tc(
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
     const int cloud = t / tiles_per_cloud;
     const int row0 = (t % tiles_per_cloud) * kTileP;
-    // ---- layer 1 (FP32 ALU): row `row`, channels 32 half .. + 32 -> bf16 A1 ----
+    // ---- layer 1 (FP32 ALU): row `row`, this part's channels -> bf16 A1 ----
     {
       const float* xp = X + ((int64_t)cloud * P + row0 + row) * 3;
       const float x = xp[0], y = xp[1], z = xp[2];
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) {
-        const int c = 4 * half + cc;
+      for (int cc = 0; cc < 8 / kTcParts; ++cc) {
+        const int c = (8 / kTcParts) * half + cc;
         unsigned w[4];
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
@@ -397,8 +398,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pn_encode_tc(
     tc::tc_fence_after();
     // ---- epilogue 2: bias + relu -> bf16 A2 (two 64-wide k blocks) ----
 #pragma unroll 1
-    for (int jj = 0; jj < 2; ++jj) {
-      const int j = 2 * half + jj;
+    for (int jj = 0; jj < 4 / kTcParts; ++jj) {
+      const int j = (4 / kTcParts) * half + jj;
       float v[32];
       tc::tmem_ld32(tmem + lane_base + 32 * j, v);
       uint8_t* blk = S.a2[j >> 1];
@@ -438,8 +439,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pn_encode_tc(
     tc::tc_fence_after();
     // ---- epilogue 3: bias + relu, column (value, row) max of the tile ----
 #pragma unroll 1
-    for (int jj = 0; jj < 4; ++jj) {
-      const int j = 4 * half + jj;
+    for (int jj = 0; jj < 8 / kTcParts; ++jj) {
+      const int j = (8 / kTcParts) * half + jj;
       float v[32];
       tc::tmem_ld32(tmem + lane_base + kH2 + 32 * j, v);
 #pragma unroll
