@@ -375,6 +375,9 @@ def run_ours(args):
     queries = None
     if not args.no_queries:
         queries = run_queries(args, rank)
+    paper_icp = None
+    if not args.no_queries:
+        paper_icp = run_paper_icp(args, rank)
 
     # ---- CPU baseline (oracle, rank 0, N = 1 only) ----
     cpu = None
@@ -414,6 +417,7 @@ def run_ours(args):
             "icp_variants": variants,
             "smooth_segmentation": segmentation,
             "queries": queries,
+            "paper_icp_pipeline": paper_icp,
             "gpu_launches": int(n1 - n0),
             "clocks": clocks,
         }
@@ -569,6 +573,9 @@ def run_queries(args, rank: int, reps: int = 10):
             ("surface 10k, knn k=10", surf, "knn", 10, "k_knn"),
             ("depth frame, knn k=10", depth, "knn", 10, "k_knn"),
             ("depth frame, normals k=10", depth, "normals", 10, "k_normals"),
+            ("depth frame, normals r=1 cm", depth, "normals_r", 0.01, "k_normals_radius"),
+            ("depth frame, knn k=10 within 1 cm", depth, "hybrid", 10, "k_knn_hybrid"),
+            ("depth frame, voxel grid 1 cm", depth, "voxel", 0.01, "voxel_downsample"),
             ("lidar sweep, knn k=16", lidar, "knn", 16, "k_knn"),
             ("lidar sweep, radius r=0.5 m", lidar, "radius", 0.5, "k_radius")):
         x = torch.from_numpy(pts).cuda()
@@ -576,6 +583,12 @@ def run_queries(args, rank: int, reps: int = 10):
             fn = lambda x=x, k=k: cil.knn(x, x, k)  # noqa: E731
         elif op == "normals":
             fn = lambda x=x, k=k: cil.estimate_normals(x, k, (0.0, 0.0, 0.0))  # noqa: E731
+        elif op == "normals_r":
+            fn = lambda x=x, k=k: cil.estimate_normals_radius(x, k, (0.0, 0.0, 0.0))  # noqa: E731
+        elif op == "hybrid":
+            fn = lambda x=x, k=k: cil.knn_hybrid(x, x, k, 0.01)  # noqa: E731
+        elif op == "voxel":
+            fn = lambda x=x, k=k: cil.voxel_downsample(x, k)  # noqa: E731
         else:
             # the capacity from one sizing call, so each timed call is one pass
             cap = int(cil.radius_search(x, x, k)[1].numel())
@@ -605,6 +618,45 @@ def run_queries(args, rank: int, reps: int = 10):
                       "ms_query_kernel": q_ms, "queries_per_s_end_to_end": len(pts) / e2e * 1e3,
                       "queries_per_s_query_only": len(pts) / q_ms * 1e3})
     return cases
+
+
+def run_paper_icp(args, rank: int, reps: int = 10):
+    """Sec. 4's registration benchmark as the paper runs it, on the depth-frame
+    pair: both frames downsampled on a 1 cm voxel grid, 10-NN normals of the
+    target, 15 point-to-plane ICP rounds with a 5 cm rejection distance.
+    Median ms per pair (voxel grids + registration) and the final RMSE."""
+    import torch
+
+    import paper_1807_00399_gb300 as cil
+    from paper_1807_00399_gb300 import synth
+
+    pair = synth.depth_frame_pair(args.seed + rank)
+    src = torch.from_numpy(pair.source).cuda()
+    dst = torch.from_numpy(pair.target).cuda()
+
+    def step():
+        s, _ = cil.voxel_downsample(src, 0.01)
+        d, _ = cil.voxel_downsample(dst, 0.01)
+        return s, d, cil.register_pair(s, d, K_NN, pair.viewpoint, 15, DMAX)
+
+    step()
+    torch.cuda.synchronize()
+    ms = []
+    out = None
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = step()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    s, d, (T, repb, _) = out
+    rep = cil.decode_report(repb)
+    return {"workload": f"depth-frame pair, 1 cm voxel grids ({s.shape[0]} / {d.shape[0]} points), "
+                        "10-NN normals, 15 point-to-plane rounds, d_max 0.05 m",
+            "ms_per_pair": float(np.median(ms)), "pairs_per_s": 1e3 / float(np.median(ms)),
+            "final_rmse": rep["rmse"], "n_inliers": rep["n_inliers"]}
 
 
 def run_segmentation(args, rank: int, reps: int = 3):
@@ -688,7 +740,7 @@ def main():
     ap.add_argument("--no-segmentation", action="store_true",
                     help="skip the apartment-scale smooth-segmentation timing")
     ap.add_argument("--no-queries", action="store_true",
-                    help="skip the standalone k-NN / normals / radius query timings")
+                    help="skip the standalone query timings and the voxel-grid ICP pipeline")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -391,7 +391,8 @@ def register_pair(src, dst, k: int, viewpoint, iters: int, max_corr_dist: float,
                   cell_scale=0.0, block=0, stream=None):
     """Target grid + k-NN normals + ICP in one enqueue (cil_register_pair).
     Everything stays on the device: returns (T (16,) float64 CUDA tensor,
-    report (32-byte uint8 CUDA tensor, decode with decode_report), normals)."""
+    report (cil_icp_report bytes in a uint8 CUDA tensor, decode with
+    decode_report), normals)."""
     torch = _torch()
     src = _points(src, "src")
     dst = _points(dst, "dst")
