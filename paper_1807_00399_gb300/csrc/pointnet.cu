@@ -39,11 +39,6 @@ constexpr int oW1 = 0, oB1 = oW1 + kH1 * kIn, oW2 = oB1 + kH1, oB2 = oW2 + kH2 *
 constexpr int kEncParams = oW4;  // W1..b3 live in the encoder
 
 constexpr int kTileP = 128;      // points per encoder tile
-constexpr int kEncThreads = 256;
-constexpr int kLdA1 = kH1 + 8;   // padded smem row strides (bf16 elements)
-constexpr int kLdA2 = kH2 + 8;
-constexpr int kLdW2 = kH1 + 8;
-constexpr int kLdW3 = kH2 + 8;
 
 struct PnState {
   int max_pairs, P;
@@ -75,201 +70,11 @@ __device__ __forceinline__ unsigned pack_bf16x2(float lo, float hi) {
   return *reinterpret_cast<const unsigned*>(&v);
 }
 
-__device__ __forceinline__ void mma_bf16_16816(float c[4], const unsigned a[4], const unsigned b[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 __device__ __forceinline__ u64 feat_pack(float v, int row) {
   return ((u64)__float_as_uint(v) << 32) | (u64)(0xffffffffu - (unsigned)row);
 }
 __device__ __forceinline__ float feat_val(u64 k) { return __uint_as_float((unsigned)(k >> 32)); }
 __device__ __forceinline__ int feat_row(u64 k) { return (int)(0xffffffffu - (unsigned)(k & 0xffffffffu)); }
-
-// (value, row) max with ties to the smaller row
-__device__ __forceinline__ void vmax(float& v, int& r, float v2, int r2) {
-  if (v2 > v || (v2 == v && r2 < r)) {
-    v = v2;
-    r = r2;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// encoder forward (persistent, tensor cores)
-// ---------------------------------------------------------------------------
-struct EncSmem {
-  __nv_bfloat16 w2[kH2 * kLdW2];
-  __nv_bfloat16 w3[kH3 * kLdW3];
-  __nv_bfloat16 a1[kTileP * kLdA1];
-  __nv_bfloat16 a2[kTileP * kLdA2];
-  float w1[kH1 * kIn];
-  float b1[kH1];
-  float b2[kH2];
-  float b3[kH3];
-  u64 red[4][kH3 / 2];
-};
-
-__global__ void __launch_bounds__(kEncThreads, 1) k_pn_encode(const float* __restrict__ X, int clouds,
-                                                              int P, const float* __restrict__ prm,
-                                                              const __nv_bfloat16* __restrict__ w2b,
-                                                              const __nv_bfloat16* __restrict__ w3b,
-                                                              u64* __restrict__ feat_key) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  EncSmem& S = *reinterpret_cast<EncSmem*>(smem_raw);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int g = lane >> 2, q = lane & 3;
-  // resident weights
-  for (int e = tid; e < kH2 * kH1 / 2; e += kEncThreads) {
-    const int n = e / (kH1 / 2), k2 = e % (kH1 / 2);
-    reinterpret_cast<unsigned*>(S.w2 + n * kLdW2)[k2] =
-        reinterpret_cast<const unsigned*>(w2b + n * kH1)[k2];
-  }
-  for (int e = tid; e < kH3 * kH2 / 2; e += kEncThreads) {
-    const int n = e / (kH2 / 2), k2 = e % (kH2 / 2);
-    reinterpret_cast<unsigned*>(S.w3 + n * kLdW3)[k2] =
-        reinterpret_cast<const unsigned*>(w3b + n * kH2)[k2];
-  }
-  for (int e = tid; e < kH1 * kIn; e += kEncThreads) S.w1[e] = prm[oW1 + e];
-  for (int e = tid; e < kH1; e += kEncThreads) S.b1[e] = prm[oB1 + e];
-  for (int e = tid; e < kH2; e += kEncThreads) S.b2[e] = prm[oB2 + e];
-  for (int e = tid; e < kH3; e += kEncThreads) S.b3[e] = prm[oB3 + e];
-  __syncthreads();
-
-  const int tiles_per_cloud = P / kTileP;
-  const int total = clouds * tiles_per_cloud;
-  const int mrow = (warp & 3) * 32;  // warp's 32 rows of the tile
-  for (int t = blockIdx.x; t < total; t += gridDim.x) {
-    const int cloud = t / tiles_per_cloud;
-    const int row0 = (t % tiles_per_cloud) * kTileP;
-    const float* xc = X + ((int64_t)cloud * P + row0) * 3;
-    // ---- layer 1 (FP32 ALU): thread -> point tid/2, 32 channels ----
-    {
-      const int p = tid >> 1, c0 = (tid & 1) * 32;
-      const float x = xc[3 * p], y = xc[3 * p + 1], z = xc[3 * p + 2];
-      unsigned* dst = reinterpret_cast<unsigned*>(S.a1 + p * kLdA1 + c0);
-#pragma unroll
-      for (int c = 0; c < 32; c += 2) {
-        const float* w = S.w1 + (c0 + c) * 3;
-        const float z0 = fmaf(w[0], x, fmaf(w[1], y, fmaf(w[2], z, S.b1[c0 + c])));
-        const float z1 = fmaf(w[3], x, fmaf(w[4], y, fmaf(w[5], z, S.b1[c0 + c + 1])));
-        dst[c >> 1] = pack_bf16x2(fmaxf(z0, 0.0f), fmaxf(z1, 0.0f));
-      }
-    }
-    __syncthreads();
-    // ---- layer 2: [128 x 64] x [64 x 128], warp tile 32 x 64 ----
-    {
-      const int n0 = (warp >> 2) * 64;
-      float acc[2][8][4];
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
-#pragma unroll
-      for (int ks = 0; ks < kH1; ks += 16) {
-        unsigned a[2][4], b[8][2];
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          const __nv_bfloat16* ar = S.a1 + (mrow + 16 * i + g) * kLdA1 + ks + 2 * q;
-          a[i][0] = *reinterpret_cast<const unsigned*>(ar);
-          a[i][1] = *reinterpret_cast<const unsigned*>(ar + 8 * kLdA1);
-          a[i][2] = *reinterpret_cast<const unsigned*>(ar + 8);
-          a[i][3] = *reinterpret_cast<const unsigned*>(ar + 8 * kLdA1 + 8);
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const __nv_bfloat16* br = S.w2 + (n0 + 8 * j + g) * kLdW2 + ks + 2 * q;
-          b[j][0] = *reinterpret_cast<const unsigned*>(br);
-          b[j][1] = *reinterpret_cast<const unsigned*>(br + 8);
-        }
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-          for (int j = 0; j < 8; ++j) mma_bf16_16816(acc[i][j], a[i], b[j]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int col = n0 + 8 * j + 2 * q;
-          const int r = mrow + 16 * i + g;
-          const float bb0 = S.b2[col], bb1 = S.b2[col + 1];
-          *reinterpret_cast<unsigned*>(S.a2 + r * kLdA2 + col) =
-              pack_bf16x2(fmaxf(acc[i][j][0] + bb0, 0.0f), fmaxf(acc[i][j][1] + bb1, 0.0f));
-          *reinterpret_cast<unsigned*>(S.a2 + (r + 8) * kLdA2 + col) =
-              pack_bf16x2(fmaxf(acc[i][j][2] + bb0, 0.0f), fmaxf(acc[i][j][3] + bb1, 0.0f));
-        }
-    }
-    __syncthreads();
-    // ---- layer 3 in two column halves: [128 x 128] x [128 x 128] each ----
-#pragma unroll 1
-    for (int half = 0; half < 2; ++half) {
-      const int n0 = half * 128 + (warp >> 2) * 64;
-      float acc[2][8][4];
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
-#pragma unroll
-      for (int ks = 0; ks < kH2; ks += 16) {
-        unsigned a[2][4], b[8][2];
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          const __nv_bfloat16* ar = S.a2 + (mrow + 16 * i + g) * kLdA2 + ks + 2 * q;
-          a[i][0] = *reinterpret_cast<const unsigned*>(ar);
-          a[i][1] = *reinterpret_cast<const unsigned*>(ar + 8 * kLdA2);
-          a[i][2] = *reinterpret_cast<const unsigned*>(ar + 8);
-          a[i][3] = *reinterpret_cast<const unsigned*>(ar + 8 * kLdA2 + 8);
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const __nv_bfloat16* br = S.w3 + (n0 + 8 * j + g) * kLdW3 + ks + 2 * q;
-          b[j][0] = *reinterpret_cast<const unsigned*>(br);
-          b[j][1] = *reinterpret_cast<const unsigned*>(br + 8);
-        }
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-          for (int j = 0; j < 8; ++j) mma_bf16_16816(acc[i][j], a[i], b[j]);
-      }
-      // bias + relu + column max over this warp's 32 rows
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int col = n0 + 8 * j + 2 * q + e;
-          const float bb = S.b3[col];
-          float v = fmaxf(acc[0][j][e] + bb, 0.0f);
-          int r = mrow + g;
-          vmax(v, r, fmaxf(acc[0][j][2 + e] + bb, 0.0f), mrow + g + 8);
-          vmax(v, r, fmaxf(acc[1][j][e] + bb, 0.0f), mrow + 16 + g);
-          vmax(v, r, fmaxf(acc[1][j][2 + e] + bb, 0.0f), mrow + 24 + g);
-#pragma unroll
-          for (int off = 4; off < 32; off <<= 1) {
-            const float v2 = __shfl_xor_sync(0xffffffffu, v, off);
-            const int r2 = __shfl_xor_sync(0xffffffffu, r, off);
-            vmax(v, r, v2, r2);
-          }
-          if (g == 0) S.red[warp & 3][col - half * 128] = feat_pack(v, row0 + r);
-        }
-      }
-      __syncthreads();
-      if (tid < 128) {
-        u64 best = S.red[0][tid];
-#pragma unroll
-        for (int w = 1; w < 4; ++w) best = max(best, S.red[w][tid]);
-        atomicMax(feat_key + (int64_t)cloud * kH3 + half * 128 + tid, best);
-      }
-      __syncthreads();
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------
 // encoder forward on the 5th-generation tensor cores (tcgen05 + TMEM)
@@ -815,7 +620,6 @@ __global__ void k_pn_refresh(const float* __restrict__ w, __nv_bfloat16* __restr
   }
 }
 
-static size_t enc_smem() { return sizeof(EncSmem); }
 static size_t enc_bwd_smem() { return sizeof(EncBwdSmem); }
 
 }  // namespace cil
@@ -853,9 +657,7 @@ cil_status cil_pointnet_create(int max_pairs, int n_points, cil_pointnet** out) 
   cil_status st = CIL_OK;
   DeviceCtx* ctx = device_ctx(&st);
   if (!ctx) return st;
-  if (cudaFuncSetAttribute(k_pn_encode, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)enc_smem()) != cudaSuccess ||
-      cudaFuncSetAttribute(k_pn_encode_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(k_pn_encode_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)enc_tc_smem()) != cudaSuccess ||
       cudaFuncSetAttribute(k_pn_encode_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)enc_bwd_smem()) != cudaSuccess)
