@@ -117,6 +117,18 @@ def test_depth_frame_full_size():
     assert rot_angle(Tg[:3, :3], p.T_gt[:3, :3]) < 2e-3
 
 
+def test_lidar_sweep_full_size():
+    """The LiDAR-sweep workload (~1.3e5 returns, 16-NN normals, 30 rounds,
+    1 m rejection) against the oracle's kd-tree route."""
+    p = synth.lidar_sweep_pair(0)
+    on, _, _ = oracle.normals(p.target, 16, p.viewpoint, method="kdtree")
+    nrm = on.astype(np.float32)
+    Tg, rg = _gpu_icp(p.source, p.target, nrm, iters=30, max_corr_dist=1.0)
+    o = oracle.icp(p.source, p.target, nrm, iters=30, max_corr_dist=1.0, method="kdtree")
+    _assert_same(Tg, o["T"], p.target)
+    assert abs(rg["n_inliers"] - o["n_inliers"]) <= 5
+
+
 def test_register_pair_equals_separate_calls(surface):
     p, _ = surface
     s = torch.from_numpy(p.source).cuda()
