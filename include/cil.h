@@ -427,6 +427,20 @@ void cil_timing_enable(int on);
 cil_status cil_timing_read(const char *name, double *total_ms, int64_t *launches);
 void cil_timing_reset(void);
 
+/* ---------------------------------------------------------------------------
+ * Failure-path checks (tests; no counterpart in the paper).  Faults are made
+ * on the host or with waits that end by themselves, never by faulting the GPU.
+ *   cil_test_fail_next_allocations  the next `count` workspace allocations of
+ *                      any call fail with CIL_ERR_NOMEM (0 clears)
+ *   cil_check_bounded_wait  launches one warp that waits on an mbarrier no one
+ *                      arrives on, bounded by `polls` polls as the encoder's
+ *                      waits are; synchronises `stream` and returns the
+ *                      error word: CIL_ERR_TIMEOUT (the wait gave up and the
+ *                      kernel returned; the context stays usable)
+ */
+void cil_test_fail_next_allocations(int count);
+cil_status cil_check_bounded_wait(unsigned polls, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,9 @@ def lib():
         L.cil_icp_point_to_plane.argtypes = [P, I64, P, P, I64, P, I, F, P, P, P]
         L.cil_icp.argtypes = [P, I64, P, P, I64, P, I, F, P, P, P, P]
         L.cil_segment.argtypes = [P, P, I64, I, F, F, P, P, P]
+        L.cil_test_fail_next_allocations.argtypes = [I]
+        L.cil_test_fail_next_allocations.restype = None
+        L.cil_check_bounded_wait.argtypes = [ctypes.c_uint, P]
         L.cil_smooth_segment.argtypes = [P, I64, I, P, F, F, P, P, P, P]
         L.cil_register_pair.argtypes = [P, I64, P, I64, I, P, P, I, F, P, P, P, P, P]
         L.cil_icp_batch_create.argtypes = [P, P, I, P, P]

@@ -58,9 +58,14 @@ DeviceCtx* device_ctx(cil_status* st) {
   return &c;
 }
 
+// allocations left to fail (cil_test_fail_next_allocations)
+static std::atomic<int> g_fail_allocs{0};
+
 cil_status Workspace::allocate(DeviceCtx* ctx, cudaStream_t s) {
   stream_ = s;
   if (total_ == 0) total_ = 256;
+  for (int f = g_fail_allocs.load(); f > 0; f = g_fail_allocs.load())
+    if (g_fail_allocs.compare_exchange_weak(f, f - 1)) return CIL_ERR_NOMEM;
   if (cudaMallocFromPoolAsync(reinterpret_cast<void**>(&base_), total_, ctx->pool, s) !=
       cudaSuccess) {
     base_ = nullptr;
@@ -164,6 +169,17 @@ const char* cil_status_string(cil_status s) {
 void cil_timing_enable(int on) { g_timing.store(on ? 1 : 0); }
 
 int64_t cil_launch_count(void) { return g_launches.load(); }
+
+void cil_test_fail_next_allocations(int count) { g_fail_allocs.store(count > 0 ? count : 0); }
+
+cil_status cil_check_bounded_wait(unsigned polls, void* stream) {
+  cil_status st = CIL_OK;
+  DeviceCtx* ctx = device_ctx(&st);
+  if (!ctx) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = launch_bounded_wait_check(polls, ctx->err, s)) != CIL_OK) return st;
+  return read_error_word(ctx, s, true);
+}
 
 cil_status cil_timing_read(const char* name, double* total_ms, int64_t* launches) {
   if (!name || !total_ms || !launches) return CIL_ERR_INVALID_ARG;

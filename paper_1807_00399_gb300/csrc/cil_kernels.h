@@ -21,6 +21,9 @@ cil_status launch_knn_hybrid(const GridView& g, const float* qry, int64_t nq, co
 cil_status launch_normals_radius(const GridView& g, int64_t n, float r, const float* vp_host,
                                  float* out_n, float* out_c, int* out_cnt, cudaStream_t s);
 
+// a bounded mbarrier wait that times out (pointnet.cu; failure-path check)
+cil_status launch_bounded_wait_check(uint32_t polls, int* err, cudaStream_t s);
+
 // connected-component segmentation over k-NN edges (segment.cu): labels =
 // smallest index of each component, count = number of components; `sorted`
 // (optional): the grid's sorted points, whose order the union pass follows

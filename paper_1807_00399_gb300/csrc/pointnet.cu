@@ -280,6 +280,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pn_encode_tc(
   }
 }
 
+// A wait on an mbarrier nothing ever arrives on, bounded like the encoder's
+// waits: it gives up after `polls` polls, records CIL_ERR_TIMEOUT in the error
+// word and returns (the failure path of a stalled tensor-core pipeline, made
+// without stalling anything).
+__global__ void k_bounded_wait_check(uint32_t polls, int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !tc::mbar_wait(&bar, 0, polls)) atomicCAS(err, 0, (int)CIL_ERR_TIMEOUT);
+}
+
+cil_status launch_bounded_wait_check(uint32_t polls, int* err, cudaStream_t s) {
+  note_launches(1);
+  k_bounded_wait_check<<<1, 32, 0, s>>>(polls, err);
+  return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
+}
+
 // ---------------------------------------------------------------------------
 // head forward (+ transform output), one block per pair
 // ---------------------------------------------------------------------------
