@@ -747,7 +747,7 @@ static void icp_accumulate(icp_ctx *c, int nt, double *H, double *g, double *r2,
 }
 
 /*
- * T_init, T_out: row-major 4x4, source -> target.
+ * T_init (NULL: identity), T_out: row-major 4x4, source -> target.
  * iters: number of correspondence/estimation rounds (fixed, no early stop).
  * After the last update one more association pass gives the final
  * point-to-plane RMSE over the inliers and their count.
@@ -784,7 +784,11 @@ int oracle_icp(const float *src, int64_t n_src, const float *dst, const float *d
   c.r2 = malloc(sizeof(double) * nt);
   c.cnt = malloc(sizeof(int64_t) * nt);
   double T[16];
-  memcpy(T, T_init, sizeof(T));
+  if (T_init) {
+    memcpy(T, T_init, sizeof(T));
+  } else {  /* identity */
+    for (int j = 0; j < 16; ++j) T[j] = (j % 5) == 0 ? 1.0 : 0.0;
+  }
   *status = 0;
   double H[36], g[6], r2;
   int64_t cnt;
