@@ -1,7 +1,9 @@
 """Hybrid query (k nearest within r) and radius-neighbourhood normals:
 libcil against the FP64 oracle, with the kNN and normals bars of
 test_gpu_knn.py / test_gpu_normals.py (points on the ball's boundary,
-|d2 - r^2| <= 1e-6 r^2, may go either way)."""
+|d2 - r^2| <= 1e-6 r^2, may go either way; every other point's membership
+must agree, so a neighbourhood's size may differ from the oracle's only by
+boundary points)."""
 import numpy as np
 import pytest
 import torch
@@ -45,6 +47,26 @@ def test_hybrid_self_query_depth_frame_sampled():
     check_knn_rows(p.target, p.target[rows][keep], gi[keep], gd[keep], oi[keep], od[keep], 10)
 
 
+def _count_bounds(ref, qry, r):
+    """Per query, the neighbourhood sizes the membership rule allows: the
+    oracle's count without its boundary members (lo) up to the count with
+    every boundary point just outside the ball as well (hi); the boundary is
+    |d2 - r^2| <= 1e-6 r^2 in FP64."""
+    r2 = float(np.float32(r)) ** 2
+    # a float32 radius whose square exceeds r^2 (1 + 1e-6): every outside
+    # boundary point is a member of this larger ball
+    r_out = np.nextafter(np.float32(np.float32(r) * np.float32(1 + 1e-6)), np.float32(np.inf))
+    assert float(r_out) ** 2 >= r2 * (1 + 1e-6)
+    off, _, d2 = oracle.radius(ref, qry, float(r_out))
+    row = np.repeat(np.arange(len(qry)), np.diff(off))
+    inside = d2 <= r2
+    bnd = np.abs(d2 - r2) <= 1e-6 * r2
+    n_in = np.bincount(row, weights=inside, minlength=len(qry)).astype(np.int64)
+    n_bnd_in = np.bincount(row, weights=inside & bnd, minlength=len(qry)).astype(np.int64)
+    n_bnd_out = np.bincount(row, weights=~inside & bnd, minlength=len(qry)).astype(np.int64)
+    return n_in, n_in - n_bnd_in, n_in + n_bnd_out
+
+
 @pytest.mark.parametrize("r", [0.04, 0.08])
 def test_radius_normals_match_oracle(r):
     p = synth.surface_pair(1, n=8000)
@@ -54,7 +76,12 @@ def test_radius_normals_match_oracle(r):
     on, oc, oev, ocnt = oracle.normals_radius(p.target, r, p.viewpoint)
     cnt = cnt.cpu().numpy()
     # counts may differ only through boundary points
-    assert np.abs(cnt - ocnt).max() <= 2 and (cnt == ocnt).mean() > 0.99
+    n_in, lo, hi = _count_bounds(p.target, p.target, r)
+    assert np.array_equal(n_in, ocnt)
+    bad = (cnt < lo) | (cnt > hi)
+    assert not bad.any(), f"{bad.sum()} neighbourhood sizes differ beyond the boundary points"
+    print(f"r={r}: sizes differing from the oracle's (boundary points only): "
+          f"{int((cnt != ocnt).sum())} of {len(cnt)}")
     same = (cnt == ocnt) & (ocnt >= 3)
     good = same & ((oev[:, 1] - oev[:, 0]) >= 1e-2 * oev[:, 2])
     gn = gn.cpu().numpy().astype(np.float64)
@@ -74,7 +101,10 @@ def test_radius_normals_depth_frame_1cm_sampled():
     sel = np.random.default_rng(2).choice(len(p.target), 400, replace=False)
     on, oc, oev, ocnt = oracle.normals_radius(p.target, 0.01, p.viewpoint, sel=sel)
     cnt = cnt.cpu().numpy()[sel]
-    assert (cnt == ocnt).mean() > 0.98
+    n_in, lo, hi = _count_bounds(p.target, p.target[sel], 0.01)
+    assert np.array_equal(n_in, ocnt)
+    bad = (cnt < lo) | (cnt > hi)
+    assert not bad.any(), f"{bad.sum()} neighbourhood sizes differ beyond the boundary points"
     same = (cnt == ocnt) & (ocnt >= 3)
     good = same & ((oev[:, 1] - oev[:, 0]) >= 1e-2 * oev[:, 2])
     ang = angle_unsigned(gn.cpu().numpy()[sel][good], on[good])
