@@ -1,14 +1,24 @@
 // radius.cu -- fixed-radius neighbour search (Sec. 3, KDTree radius query).
 //
 // Grid cells are sized to the radius (nearest power-of-two multiple of the
-// fine lattice), so each query visits the few cells its ball touches.
-//   pass 1: count neighbours with d2 <= r*r per query (one thread per query);
-//   scan:   int64 CSR offsets;
-//   pass 2: write (index, d2) of each row in visiting order;
-//   sort:   each row by (d2, index) -- rows up to kRowCap keys in shared
-//           memory, longer rows in place in global memory; both with the
-//           same all-ascending bitonic network, where virtual +inf padding
-//           past the row end never moves.
+// fine lattice), so each query's ball meets at most 4 x 4 x 4 cells.  One
+// warp per query, queries in the grid's Morton order (neighbouring warps read
+// the same cells through L1):
+//   count  the lanes look up the ball's cells in parallel, the cells' points
+//          are concatenated and split over the lanes, and accepted points
+//          (d2 <= r*r, inclusive) are counted with a ballot;
+//   scan   int64 CSR offsets (rows longer than kRowCapW also counted);
+//   fill   the same walk; accepted (d2, index) keys are appended to the
+//          warp's shared-memory row in visiting order, then sorted there by
+//          (d2, index) with a bucket sort: buckets of d2 * NB / r^2 (a
+//          monotone map, so bucket order agrees with key order), a histogram
+//          and scan, a scatter of key positions into bucket order, and each
+//          key's rank = its bucket's start + the keys of its bucket below it.
+//          The sorted row is written to its CSR place.  A row longer than
+//          kRowCapW keys is written unsorted and listed;
+//   sort   listed rows, one block each, with an all-ascending bitonic network
+//          (in shared memory up to kRowCap keys, else in place in global
+//          memory; virtual +inf padding past the row end never moves).
 #include <math.h>
 
 #include "cil_host.h"
@@ -16,51 +26,216 @@
 
 namespace cil {
 
-constexpr int kRowCap = 4096;
+constexpr int kRowCap = 4096;      // block sort: rows up to this many keys in shared memory
 constexpr int kSortThreads = 256;
+constexpr int kRowCapW = 1024;     // warp sort: rows up to this many keys in shared memory
+constexpr int kBucketsMax = 512;   // buckets of the warp sort (a power of two)
+constexpr int kCountWarps = 8;     // warps (queries) per block of the count pass
+constexpr int kFillWarps = 4;      // warps (queries) per block of the fill pass
 
-template <bool kFill>
-__global__ void __launch_bounds__(128) k_radius(GridView g, const float* __restrict__ qry, int64_t nq,
-                                                const int* __restrict__ order, float r,
-                                                long long* __restrict__ off, int* __restrict__ out_idx,
-                                                float* __restrict__ out_d2) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nq) return;
-  const int64_t qi = order ? order[i] : i;
-  const float q[3] = {qry[3 * qi], qry[3 * qi + 1], qry[3 * qi + 2]};
+// Cells of the query's ball: the range [lo, hi] of cells meeting the cube of
+// half-edge r + eps around q, walked 32 at a time (lane c takes cell c of the
+// chunk), each looked up if its box meets the ball.
+struct BallCells {
+  int lo[3], nx, nxy, ncell;
+  __device__ __forceinline__ void init(const CellFrame& f, const GridParams& P, const float q[3],
+                                       float r) {
+    int hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = f.cell_of(q[a] - r - f.eps, a, P.inv_fine);
+      hi[a] = f.cell_of(q[a] + r + f.eps, a, P.inv_fine);
+    }
+    nx = hi[0] - lo[0] + 1;
+    nxy = nx * (hi[1] - lo[1] + 1);
+    ncell = nxy * (hi[2] - lo[2] + 1);
+  }
+  // (start, count) of cell c (0 when outside the range, beyond the ball or empty)
+  __device__ __forceinline__ void cell(const GridView& g, const CellFrame& f, const float q[3],
+                                       float r2, int c, int& s, int& n) const {
+    s = 0;
+    n = 0;
+    if (c >= ncell) return;
+    const int z = c / nxy, rem = c - z * nxy, y = rem / nx, x = rem - y * nx;
+    const int c3[3] = {lo[0] + x, lo[1] + y, lo[2] + z};
+    if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > r2) return;
+    if (!cell_lookup(g, cell_key(f.level, 0, c3[0], c3[1], c3[2]), s, n)) n = 0;
+  }
+};
+
+// Visit every point of the query's ball cells: fn(accept, d2, index) is called
+// by every lane for every group of 32 candidates (accept false on lanes
+// without a candidate), so warp-wide operations inside fn are safe.
+template <class F>
+__device__ __forceinline__ void walk_ball(const GridView& g, const float q[3], float r, int lane,
+                                          int* s_start, int* s_pre, F&& fn) {
   const GridParams& P = g.prm[0];
   CellFrame f;
   f.load(P, 0);
   const float r2 = r * r;
-  int lo[3], hi[3];
+  BallCells bc;
+  bc.init(f, P, q, r);
+  for (int c0 = 0; c0 < bc.ncell; c0 += 32) {
+    int s, n;
+    bc.cell(g, f, q, r2, c0 + lane, s, n);
+    // exclusive prefix of the chunk's cell sizes
+    int incl = n;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    lo[a] = f.cell_of(q[a] - r - f.eps, a, P.inv_fine);
-    hi[a] = f.cell_of(q[a] + r + f.eps, a, P.inv_fine);
-  }
-  long long cnt = 0;
-  long long w = kFill ? off[qi] : 0;
-  for (int z = lo[2]; z <= hi[2]; ++z)
-    for (int y = lo[1]; y <= hi[1]; ++y)
-      for (int x = lo[0]; x <= hi[0]; ++x) {
-        const int c3[3] = {x, y, z};
-        if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > r2) continue;
-        int s, n;
-        if (!cell_lookup(g, cell_key(P.level, 0, x, y, z), s, n)) continue;
-        for_points(g.pts, s, n, [&](const float4& p, int) {
-          const float d2 = sqdist(p.x, p.y, p.z, q[0], q[1], q[2]);
-          if (d2 <= r2) {
-            if (kFill) {
-              out_idx[w] = __float_as_int(p.w);
-              out_d2[w] = d2;
-              ++w;
-            } else {
-              ++cnt;
-            }
-          }
-        });
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    __syncwarp();
+    s_start[lane] = s;
+    s_pre[lane] = incl - n;
+    if (lane == 31) s_pre[32] = total;
+    __syncwarp();
+    // candidate t of the chunk lies in cell ci with s_pre[ci] <= t < s_pre[ci + 1];
+    // each lane's t only grows, so its cell pointer only moves forward
+    int ci = 0;
+    for (int base = 0; base < total; base += 32) {
+      const int t = base + lane;
+      bool acc = false;
+      float d2 = 0.0f;
+      int idx = -1;
+      if (t < total) {
+        while (s_pre[ci + 1] <= t) ++ci;
+        const float4 p = __ldg(g.pts + s_start[ci] + (t - s_pre[ci]));
+        d2 = sqdist(p.x, p.y, p.z, q[0], q[1], q[2]);
+        idx = __float_as_int(p.w);
+        acc = d2 <= r2;
       }
-  if (!kFill) off[qi] = cnt;
+      fn(acc, d2, idx);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kCountWarps * 32) k_radius_count(GridView g,
+                                                                   const float* __restrict__ qry,
+                                                                   int64_t nq,
+                                                                   const int* __restrict__ order,
+                                                                   float r,
+                                                                   long long* __restrict__ off,
+                                                                   unsigned* __restrict__ n_long) {
+  __shared__ int s_start[kCountWarps][32], s_pre[kCountWarps][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * kCountWarps + w;
+  if (i >= nq) return;  // whole warp
+  const int64_t qi = order ? order[i] : i;
+  const float q[3] = {qry[3 * qi], qry[3 * qi + 1], qry[3 * qi + 2]};
+  long long cnt = 0;
+  walk_ball(g, q, r, lane, s_start[w], s_pre[w], [&](bool acc, float, int) {
+    cnt += __popc(__ballot_sync(0xffffffffu, acc));
+  });
+  if (lane == 0) {
+    off[qi] = cnt;
+    if (cnt > kRowCapW) atomicAdd(n_long, 1u);
+  }
+}
+
+// bucket of a squared distance in [0, r^2]: floor(d2 * NB / r^2) clamped to
+// NB - 1 (NaN, from r = 0, also to NB - 1); monotone in d2
+__device__ __forceinline__ int d2_bucket(float d2, float scale, int nb) {
+  return (int)fminf(d2 * scale, (float)(nb - 1));
+}
+
+struct FillSmem {
+  u64 key[kRowCapW];          // the row's keys in visiting order
+  unsigned short pos[kRowCapW];  // positions in `key`, grouped by bucket
+  int cnt[kBucketsMax];       // bucket histogram, then bucket ends
+  int start[32], pre[33];     // the walk's cell chunk
+};
+
+__global__ void __launch_bounds__(kFillWarps * 32) k_radius_fill(GridView g,
+                                                                 const float* __restrict__ qry,
+                                                                 int64_t nq,
+                                                                 const int* __restrict__ order,
+                                                                 float r,
+                                                                 const long long* __restrict__ off,
+                                                                 int* __restrict__ out_idx,
+                                                                 float* __restrict__ out_d2,
+                                                                 int* __restrict__ long_rows,
+                                                                 unsigned* __restrict__ n_long,
+                                                                 unsigned long_cap) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  FillSmem& S = reinterpret_cast<FillSmem*>(smem_raw)[w];
+  const int64_t i = (int64_t)blockIdx.x * kFillWarps + w;
+  if (i >= nq) return;  // whole warp
+  const int64_t qi = order ? order[i] : i;
+  const float q[3] = {qry[3 * qi], qry[3 * qi + 1], qry[3 * qi + 2]};
+  const long long b = off[qi];
+  const int n = (int)(off[qi + 1] - b);
+  if (n == 0) return;
+  const bool in_smem = n <= kRowCapW;
+  int nacc = 0;
+  walk_ball(g, q, r, lane, S.start, S.pre, [&](bool acc, float d2, int idx) {
+    const unsigned m = __ballot_sync(0xffffffffu, acc);
+    if (acc) {
+      // p < n: both passes take the same decisions in the same arithmetic
+      // (the test only keeps a disagreement from writing out of bounds)
+      const int p = nacc + __popc(m & ((1u << lane) - 1u));
+      if (p < n && in_smem) {
+        S.key[p] = pack_key(d2, idx);
+      } else if (p < n) {
+        out_idx[b + p] = idx;
+        out_d2[b + p] = d2;
+      }
+    }
+    nacc += __popc(m);
+  });
+  if (!in_smem) {
+    if (lane == 0) {
+      const unsigned slot = atomicAdd(n_long, 1u);
+      if (slot < long_cap) long_rows[slot] = (int)qi;
+    }
+    return;
+  }
+  // ---- bucket sort of the row in shared memory ----
+  int nb = 32;
+  while (nb < kBucketsMax && 2 * nb < n) nb <<= 1;
+  const float r2 = r * r;
+  const float scale = (float)nb / r2;
+  for (int j = lane; j < nb; j += 32) S.cnt[j] = 0;
+  __syncwarp();
+  for (int j = lane; j < n; j += 32) atomicAdd(&S.cnt[d2_bucket(key_d2(S.key[j]), scale, nb)], 1);
+  __syncwarp();
+  {  // exclusive scan of the histogram: lane l owns buckets [l * per, (l + 1) * per)
+    const int per = nb >> 5;
+    int sum = 0;
+    for (int j = 0; j < per; ++j) sum += S.cnt[lane * per + j];
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    int run = incl - sum;
+    for (int j = 0; j < per; ++j) {
+      const int c = S.cnt[lane * per + j];
+      S.cnt[lane * per + j] = run;
+      run += c;
+    }
+  }
+  __syncwarp();
+  for (int j = lane; j < n; j += 32) {
+    const int bk = d2_bucket(key_d2(S.key[j]), scale, nb);
+    S.pos[atomicAdd(&S.cnt[bk], 1)] = (unsigned short)j;
+  }
+  __syncwarp();
+  // S.cnt[k] is now the end of bucket k; a key's rank = its bucket's start +
+  // the keys of its bucket that are smaller (keys are distinct: the index
+  // fills the low word)
+  for (int p = lane; p < n; p += 32) {
+    const u64 key = S.key[S.pos[p]];
+    const int bk = d2_bucket(key_d2(key), scale, nb);
+    const int beg = bk ? S.cnt[bk - 1] : 0, end = S.cnt[bk];
+    int rank = beg;
+    for (int u = beg; u < end; ++u) rank += S.key[S.pos[u]] < key;
+    out_idx[b + rank] = key_idx(key);
+    out_d2[b + rank] = key_d2(key);
+  }
 }
 
 __device__ __forceinline__ void cmp_swap_keys(u64& a, u64& b) {
@@ -71,15 +246,16 @@ __device__ __forceinline__ void cmp_swap_keys(u64& a, u64& b) {
   }
 }
 
-// all-ascending bitonic sort: for each size, a "flip" compare (i, i^(size-1))
-// then half-cleaners (i, i+stride); the smaller key always goes to the lower
-// index, so entries past n behave as +inf and are never touched
+// all-ascending bitonic sort of the listed rows, one block each: for each
+// size, a "flip" compare (i, i^(size-1)) then half-cleaners (i, i+stride); the
+// smaller key always goes to the lower index, so entries past n behave as
+// +inf and are never touched
 __global__ void __launch_bounds__(kSortThreads) k_sort_rows(const long long* __restrict__ off,
-                                                            int64_t nq, int* __restrict__ idx,
+                                                            const int* __restrict__ rows,
+                                                            int* __restrict__ idx,
                                                             float* __restrict__ d2) {
   __shared__ u64 sk[kRowCap];
-  const int64_t row = blockIdx.x;
-  if (row >= nq) return;
+  const int64_t row = rows[blockIdx.x];
   const long long b = off[row];
   const int n = (int)(off[row + 1] - b);
   if (n <= 1) return;
@@ -176,6 +352,7 @@ extern "C" cil_status cil_radius_search(const float* ref, int64_t n_ref, const f
   order_plan(op, ws, n_qry);
   const size_t o_order = ws.reserve(sizeof(int) * (size_t)n_qry);
   const size_t o_tmp = ws.reserve(sizeof(long long) * (scan_tmp_ints(n_qry + 1) * 2 + 2));
+  const size_t o_long = ws.reserve(sizeof(unsigned) * 2);
   if ((st = ws.allocate(ctx, s)) != CIL_OK) return st;
   GridOptions opt;
   opt.k_est = 10;
@@ -185,38 +362,54 @@ extern "C" cil_status cil_radius_search(const float* ref, int64_t n_ref, const f
   int* order = ws.at<int>(o_order);
   if ((st = order_queries(op, ws, qry, nullptr, 1, g.prm, nullptr, order, s)) != CIL_OK) return st;
   long long* off = reinterpret_cast<long long*>(out_offsets);
-  const int grid = ceil_div(n_qry, 128);
+  unsigned* n_long = ws.at<unsigned>(o_long);  // [0] rows longer than kRowCapW, [1] listed
+  if (cudaMemsetAsync(n_long, 0, sizeof(unsigned) * 2, s) != cudaSuccess) return CIL_ERR_CUDA;
   {
     TimedRegion timer("k_radius", s);
     note_launches(1);
-    k_radius<false><<<grid, 128, 0, s>>>(g, qry, n_qry, order, r, off, nullptr, nullptr);
+    k_radius_count<<<ceil_div(n_qry, kCountWarps), kCountWarps * 32, 0, s>>>(g, qry, n_qry, order, r,
+                                                                            off, n_long);
   }
   if (cudaMemsetAsync(off + n_qry, 0, sizeof(long long), s) != cudaSuccess) return CIL_ERR_CUDA;
   scan_exclusive_i64(off, n_qry + 1, ws.at<long long>(o_tmp), s);
-  long long nnz = 0;
-  if (cudaMemcpyAsync(&nnz, off + n_qry, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+  struct {
+    long long nnz;
+    unsigned n_long;
+  } h = {0, 0};
+  if (cudaMemcpyAsync(&h.nnz, off + n_qry, sizeof(long long), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(&h.n_long, n_long, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return CIL_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return CIL_ERR_CUDA;
-  *out_nnz = nnz;
-  if (nnz > capacity) {
+  *out_nnz = h.nnz;
+  if (h.nnz > capacity) {
     ws.release(s);
     cudaStreamSynchronize(s);
     return CIL_ERR_CAPACITY;
   }
-  if (nnz > 0) {
+  if (h.nnz > 0) {
     if (!out_idx) return CIL_ERR_INVALID_ARG;
     float* d2 = out_d2;
-    void* d2_tmp = nullptr;
-    if (!d2) {
-      if (cudaMallocFromPoolAsync(&d2_tmp, sizeof(float) * (size_t)nnz, ctx->pool, s) != cudaSuccess)
-        return CIL_ERR_NOMEM;
-      d2 = static_cast<float*>(d2_tmp);
-    }
+    void* tmp = nullptr;
+    const size_t d2_bytes = out_d2 ? 0 : sizeof(float) * (size_t)h.nnz;
+    const size_t rows_bytes = sizeof(int) * (size_t)(h.n_long > 0 ? h.n_long : 1);
+    if (cudaMallocFromPoolAsync(&tmp, ((d2_bytes + 255) & ~size_t(255)) + rows_bytes, ctx->pool,
+                                s) != cudaSuccess)
+      return CIL_ERR_NOMEM;
+    if (!d2) d2 = static_cast<float*>(tmp);
+    int* long_rows = reinterpret_cast<int*>(static_cast<char*>(tmp) + ((d2_bytes + 255) & ~size_t(255)));
+    // the fill kernel's shared memory is above the 48 KB default (opt-in,
+    // set on the current device)
+    const int smem = (int)sizeof(FillSmem) * kFillWarps;
+    if (cudaFuncSetAttribute(k_radius_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess)
+      return CIL_ERR_CUDA;
     TimedRegion timer("k_radius", s);
-    note_launches(2);
-    k_radius<true><<<grid, 128, 0, s>>>(g, qry, n_qry, order, r, off, out_idx, d2);
-    k_sort_rows<<<(unsigned)n_qry, kSortThreads, 0, s>>>(off, n_qry, out_idx, d2);
-    if (d2_tmp) cudaFreeAsync(d2_tmp, s);
+    note_launches(h.n_long > 0 ? 2 : 1);
+    k_radius_fill<<<ceil_div(n_qry, kFillWarps), kFillWarps * 32, smem, s>>>(
+        g, qry, n_qry, order, r, off, out_idx, d2, long_rows, n_long + 1, h.n_long);
+    if (h.n_long > 0) k_sort_rows<<<h.n_long, kSortThreads, 0, s>>>(off, long_rows, out_idx, d2);
+    cudaFreeAsync(tmp, s);
   }
   ws.release(s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return CIL_ERR_CUDA;

@@ -86,12 +86,13 @@ def test_lidar_sampled():
     _check(p.target, None, 0.5, rows=rows)
 
 
-@pytest.mark.parametrize("r", [1.0, 2.9, 4.0, 5.0, 6.0])
+@pytest.mark.parametrize("r", [1.0, 2.9, 4.0, 5.0, 6.0, 7.0, 8.5])
 def test_lattice_rows_across_sort_paths(r):
     """Integer lattice (exact distances, many exact ties, so the index order
     inside equal distances is checked bit for bit) with row lengths from a
-    few to about a thousand: rows up to 512 keys take the register sort,
-    longer ones the shared-memory sort."""
+    few to about three thousand: rows up to 1024 keys are sorted by their
+    warp in shared memory (bucket sort), longer ones by a block each (bitonic
+    network in shared memory)."""
     pts = synth.lattice_points((16, 16, 16))
     go, gi, gd = _gpu_radius(pts, None, r)
     oo, oi, od = oracle.radius(pts, pts, r)
@@ -99,3 +100,5 @@ def test_lattice_rows_across_sort_paths(r):
     assert np.array_equal(gd.astype(np.float64), od)
     lengths = np.diff(go)
     assert lengths.max() >= 7
+    if r >= 7.0:
+        assert lengths.max() > 1024
