@@ -87,3 +87,14 @@ def rot_angle(Ra, Rb):
 def extent(pts):
     p = np.asarray(pts, np.float64)
     return float(np.linalg.norm(p.max(0) - p.min(0)))
+
+
+def rmse_tol(pts, rot=0.0, trans=0.0):
+    """Bar on |RMSE_library - RMSE_oracle| (absolute) for point-to-plane ICP.
+    Each FP32 residual r = n.(p' - q) carries the rounding of p' = R p + t,
+    of the difference and of the dot product: |dr| <= ~4 eps32 M, with M the
+    largest coordinate magnitude; the RMSE (a 2-norm over sqrt(n)) moves by
+    at most max |dr|.  Transforms that differ by `rot` rad and `trans` move
+    each residual by at most rot M + trans more."""
+    M = float(np.abs(np.asarray(pts, np.float64)).max())
+    return 4 * 2.0 ** -24 * M + rot * M + trans

@@ -14,7 +14,7 @@ import torch
 import oracle
 import paper_1807_00399_gb300 as cil
 from paper_1807_00399_gb300 import synth
-from parity import extent, rot_angle
+from parity import extent, rmse_tol, rot_angle
 
 pytestmark = pytest.mark.gpu
 
@@ -105,19 +105,22 @@ def test_deterministic(surface):
     assert np.array_equal(a[0], b[0]) and a[1] == b[1]
 
 
-def test_depth_frame_full_size():
+def test_depth_frame_full_size(parity_report):
     p = synth.depth_frame_pair(0)
     on, _, _ = oracle.normals(p.target, 10, p.viewpoint, method="kdtree")
     nrm = on.astype(np.float32)
     Tg, rg = _gpu_icp(p.source, p.target, nrm, iters=30, max_corr_dist=0.05)
     o = oracle.icp(p.source, p.target, nrm, iters=30, max_corr_dist=0.05, method="kdtree")
+    parity_report("ICP, depth frame, oracle normals", rot_rad=rot_angle(Tg[:3, :3], o["T"][:3, :3]),
+                  trans_rel=np.abs(Tg[:3, 3] - o["T"][:3, 3]).max() / extent(p.target),
+                  inliers_diff=int(rg["n_inliers"] - o["n_inliers"]))
     _assert_same(Tg, o["T"], p.target)
     assert abs(rg["n_inliers"] - o["n_inliers"]) <= 5
     # and the registration itself is right: close to the generator transform
     assert rot_angle(Tg[:3, :3], p.T_gt[:3, :3]) < 2e-3
 
 
-def test_lidar_sweep_full_size():
+def test_lidar_sweep_full_size(parity_report):
     """The LiDAR-sweep workload (~1.3e5 returns, 16-NN normals, 30 rounds,
     1 m rejection) against the oracle's kd-tree route."""
     p = synth.lidar_sweep_pair(0)
@@ -125,6 +128,9 @@ def test_lidar_sweep_full_size():
     nrm = on.astype(np.float32)
     Tg, rg = _gpu_icp(p.source, p.target, nrm, iters=30, max_corr_dist=1.0)
     o = oracle.icp(p.source, p.target, nrm, iters=30, max_corr_dist=1.0, method="kdtree")
+    parity_report("ICP, LiDAR sweep, oracle normals", rot_rad=rot_angle(Tg[:3, :3], o["T"][:3, :3]),
+                  trans_rel=np.abs(Tg[:3, 3] - o["T"][:3, 3]).max() / extent(p.target),
+                  inliers_diff=int(rg["n_inliers"] - o["n_inliers"]))
     _assert_same(Tg, o["T"], p.target)
     assert abs(rg["n_inliers"] - o["n_inliers"]) <= 5
 
@@ -197,3 +203,30 @@ def test_association_large_rejection_distance(surface):
     Tg, rg = _gpu_icp(p.source, p.target, nrm, iters=3, max_corr_dist=1.0)
     o = oracle.icp(p.source, p.target, nrm, iters=3, max_corr_dist=1.0)
     _assert_same(Tg, o["T"], p.target)
+
+
+def test_register_pair_chain_depth_frame_matches_oracle_chain(parity_report):
+    """The benchmarked chain end to end: cil_register_pair (the library's grid,
+    10-NN normals and 30 point-to-plane rounds, rejection 0.05 m) against the
+    oracle's chain on the same frame pair (its own normals, then its ICP;
+    kd-tree route).  The normals of the two chains differ by their own parity
+    bar (and freely below its eigen-gap gate), so this shows that those
+    differences leave the registration within the ICP bars; the error is
+    reported."""
+    p = synth.depth_frame_pair(0)
+    s = torch.from_numpy(p.source).cuda()
+    d = torch.from_numpy(p.target).cuda()
+    T, rep, _ = cil.register_pair(s, d, 10, p.viewpoint, 30, 0.05)
+    torch.cuda.synchronize()
+    Tg = T.cpu().numpy().reshape(4, 4)
+    rg = cil.decode_report(rep)
+    on, _, _ = oracle.normals(p.target, 10, p.viewpoint, method="kdtree")
+    o = oracle.icp(p.source, p.target, on.astype(np.float32), iters=30, max_corr_dist=0.05,
+                   method="kdtree")
+    ang = rot_angle(Tg[:3, :3], o["T"][:3, :3])
+    dt = np.abs(Tg[:3, 3] - o["T"][:3, 3]).max() / extent(p.target)
+    parity_report("register_pair chain vs oracle chain, depth frame", rot_rad=ang, trans_rel=dt,
+                  rmse_rel=abs(rg["rmse"] - o["rmse"]) / o["rmse"],
+                  inliers_diff=int(rg["n_inliers"] - o["n_inliers"]))
+    _assert_same(Tg, o["T"], p.target)
+    assert abs(rg["rmse"] - o["rmse"]) <= rmse_tol(p.target, ang, dt * extent(p.target))

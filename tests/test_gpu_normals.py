@@ -34,9 +34,18 @@ def _gpu_normals(pts, k, vp, **kw):
 
 
 def _compare(pts, k, vp, gn, gc, on, oc, oev, sel=None):
+    """Asserts the bars; returns the figures to report: points compared,
+    points below the eigen-gap gate, the largest and 99th-percentile angle
+    above the gate and the largest angle below it (finite normals)."""
     P = pts if sel is None else pts[sel]
     good = (oev[:, 1] - oev[:, 0]) >= GATE * oev[:, 2]
     ang = angle_unsigned(gn, on)
+    fin = np.isfinite(ang)
+    below = ~good & fin
+    figs = {"points": int(len(ang)), "below_gate": int((~good).sum()),
+            "max_rad": float(ang[good].max()) if good.any() else 0.0,
+            "p99_rad": float(np.percentile(ang[good], 99)) if good.any() else 0.0,
+            "max_rad_below_gate": float(ang[below].max()) if below.any() else 0.0}
     assert np.all(ang[good] <= TOL_ANGLE), f"max angle {ang[good].max():.3g} rad"
     np.testing.assert_allclose(gc[good], oc[good], atol=TOL_CURV, rtol=0)
     assert np.allclose(np.linalg.norm(gn[good], axis=1), 1.0, atol=1e-5)
@@ -44,15 +53,16 @@ def _compare(pts, k, vp, gn, gc, on, oc, oev, sel=None):
     s_o = (on * v).sum(1) / np.linalg.norm(v, axis=1)
     clear = good & (np.abs(s_o) > 1e-3)
     assert np.all((gn[clear] * on[clear]).sum(1) > 0), "orientation differs"
-    return int((~good).sum())
+    return figs
 
 
 @pytest.mark.parametrize("k", [3, 10, 16, 32])
-def test_surface_normals(k):
+def test_surface_normals(k, parity_report):
     p = synth.surface_pair(0, n=10_000)
     gn, gc = _gpu_normals(p.target, k, p.viewpoint)
     on, oc, oev = oracle.normals(p.target, k, p.viewpoint)
-    _compare(p.target, k, p.viewpoint, gn, gc, on, oc, oev)
+    parity_report(f"normals, wavy surface 10k, k={k}",
+                  **_compare(p.target, k, p.viewpoint, gn, gc, on, oc, oev))
 
 
 def test_plane_exact_normal():
@@ -77,20 +87,22 @@ def test_degenerate_inputs_give_nan():
     assert np.isnan(gn).all() and np.isnan(gc).all()
 
 
-def test_depth_frame_sampled():
+def test_depth_frame_sampled(parity_report):
     p = synth.depth_frame_pair(0)
     sel = np.random.default_rng(2).choice(len(p.target), 3000, replace=False)
     gn, gc = _gpu_normals(p.target, 10, p.viewpoint)
     on, oc, oev = oracle.normals_subset(p.target, sel, 10, p.viewpoint, method="kdtree")
-    _compare(p.target, 10, p.viewpoint, gn[sel], gc[sel], on, oc, oev, sel)
+    parity_report("normals, depth frame (3000 sampled points), k=10",
+                  **_compare(p.target, 10, p.viewpoint, gn[sel], gc[sel], on, oc, oev, sel))
 
 
-def test_lidar_sampled():
+def test_lidar_sampled(parity_report):
     p = synth.lidar_sweep_pair(0)
     sel = np.random.default_rng(3).choice(len(p.target), 3000, replace=False)
     gn, gc = _gpu_normals(p.target, 16, p.viewpoint)
     on, oc, oev = oracle.normals_subset(p.target, sel, 16, p.viewpoint, method="kdtree")
-    _compare(p.target, 16, p.viewpoint, gn[sel], gc[sel], on, oc, oev, sel)
+    parity_report("normals, LiDAR sweep (3000 sampled points), k=16",
+                  **_compare(p.target, 16, p.viewpoint, gn[sel], gc[sel], on, oc, oev, sel))
 
 
 def test_deterministic():
