@@ -59,19 +59,24 @@ typedef enum {
 
 #define CIL_MAX_K 32
 
-/* Optional tuning knobs (pass NULL for defaults).
+/* Optional tuning knobs (pass NULL for defaults).  None of them changes a
+ * result, only the time it takes.
  *   cell_size   > 0: grid cell edge in input units (rounded to the nearest
  *               power-of-two multiple of the cloud's fine Morton resolution,
  *               max_extent / 1023); 0: chosen from the data.
  *   cell_scale  multiplier applied to the data-driven cell size (the median
  *               distance of sampled points to their k-th neighbour; 0 = 1.5).
  *   block       threads per block of the query kernels (0 = default 128;
- *               64, 128, 256 accepted). */
+ *               64, 128, 256 accepted).
+ *   topk        how the k-NN and normals kernels hold each query's k best:
+ *               0 = by k (sorted register list for k < 8, a binary max-heap
+ *               per thread in shared memory from k = 8 on), 1 = register
+ *               list, 2 = shared-memory heap (k = 1 always uses the list). */
 typedef struct {
   float cell_size;
   float cell_scale;
   int block;
-  int reserved;
+  int topk;
 } cil_params;
 
 /* Human-readable name of a status code (static storage). */
@@ -112,7 +117,9 @@ cil_status cil_knn_ex(const float *ref, int64_t n_ref, const float *qry, int64_t
  *     launched);
  *   - the first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current: make it before any
- *     stream capture;
+ *     stream capture; the address is kept for the life of the process, so
+ *     after a cudaDeviceReset of that device this entry point must not be
+ *     called again;
  *   - every call shares the one array: calls that overlap on the GPU race and
  *     corrupt each other's results; each call resets the state it needs;
  *   - the call synchronises `stream` and returns a device-detected error
@@ -337,6 +344,25 @@ cil_status cil_icp(const float *src, int64_t n_src, const float *dst, const floa
                    int64_t n_dst, const double *T_init, int max_iters, float max_corr_dist,
                    const cil_icp_options *opt, double *T_out, cil_icp_report *rep, void *stream);
 
+/* cil_icp that also returns, for every round, the normal-equation sums the
+ * round's solve used (Sec. 3 point-to-plane estimator: the linearised system
+ * H xi = -g accumulated over the round's correspondences; the paper states
+ * the estimator, not a layout).  Diagnostics and precision checks of the
+ * compensated FP32 sums against an FP64 reference.
+ *   sums_out  host double[max_iters + 1][29], round r at sums_out + 29 r:
+ *             [0, 21)  H, upper triangle row by row (H00 H01 .. H05 H11 .. H55)
+ *             [21, 27) g
+ *             27       sum of r^2 over the inliers
+ *             28       inlier count
+ *             (point-to-plane metric; for the other metrics the first 28 slots
+ *             hold that metric's 28 sums).  Row max_iters is the final
+ *             association pass.  Rounds that never ran hold zeros.
+ * Everything else as cil_icp; CIL_ERR_INVALID_ARG for a null sums_out. */
+cil_status cil_icp_sums(const float *src, int64_t n_src, const float *dst, const float *dst_normals,
+                        int64_t n_dst, const double *T_init, int max_iters, float max_corr_dist,
+                        const cil_icp_options *opt, double *T_out, cil_icp_report *rep,
+                        double *sums_out, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Batched registration of B independent pairs of uneven sizes (no counterpart
  * in the paper, which registers one pair at a time, Sec. 4).  Per pair: the
@@ -375,6 +401,26 @@ cil_status cil_icp_batch_run(cil_batch *h, const float *src_cat, const float *ds
                              const double *T_init, double *T_out, cil_icp_report *rep,
                              float *normals_out, void *stream);
 void cil_icp_batch_destroy(cil_batch *h);
+
+/* Fallback of a warm-started batch (no counterpart in the paper: plain ICP
+ * from the identity stays the fallback of the learned warm start below).
+ * Call after cil_icp_batch_run of the same handle, with the same src_cat,
+ * dst_cat, T_out and rep, on the same stream (it reuses that run's target
+ * grid and normals).  Pairs whose rep[b].rmse is >= rmse_threshold, or NaN
+ * (no inliers), are re-registered from the identity (k-NN association,
+ * point-to-plane, the handle's iterations and rejection distance; only their
+ * source tiles are launched) and keep the result with the smaller final RMSE
+ * (the re-registered one wins over a NaN); T_out and rep are updated in
+ * place.  Every re-registered pair's result is bitwise the result an
+ * identity-started cil_icp_batch_run gives that pair.
+ *   used_out  device int32[B] or NULL: 0 not re-registered, 1 re-registered
+ *             and the first result kept, 2 replaced by the re-registration
+ * Synchronises the stream once (to read how many source tiles to launch);
+ * not for stream capture.  CIL_ERR_INVALID_ARG for a null handle or output,
+ * a negative or NaN threshold, or a handle that has not run. */
+cil_status cil_icp_batch_fallback(cil_batch *h, const float *src_cat, const float *dst_cat,
+                                  double rmse_threshold, double *T_out, cil_icp_report *rep,
+                                  int32_t *used_out, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Learned warm start (no counterpart in the paper; it seeds the Sec. 3 ICP).

@@ -42,9 +42,10 @@ class CilError(RuntimeError):
 
 
 class Params(ctypes.Structure):
-    """cil_params: cell_size (0 = from data), cell_scale (0 = 1.0), block."""
+    """cil_params: cell_size (0 = from data), cell_scale (0 = 1.5), block,
+    topk (0 = by k, 1 = register list, 2 = shared-memory heap)."""
     _fields_ = [("cell_size", ctypes.c_float), ("cell_scale", ctypes.c_float),
-                ("block", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("block", ctypes.c_int), ("topk", ctypes.c_int)]
 
 
 class BatchParams(ctypes.Structure):
@@ -77,6 +78,7 @@ def lib():
         L.cil_estimate_normals_ex.argtypes = [P, I64, I, P, P, P, P, P]
         L.cil_icp_point_to_plane.argtypes = [P, I64, P, P, I64, P, I, F, P, P, P]
         L.cil_icp.argtypes = [P, I64, P, P, I64, P, I, F, P, P, P, P]
+        L.cil_icp_sums.argtypes = [P, I64, P, P, I64, P, I, F, P, P, P, P, P]
         L.cil_segment.argtypes = [P, P, I64, I, F, F, P, P, P]
         L.cil_test_fail_next_allocations.argtypes = [I]
         L.cil_test_fail_next_allocations.restype = None
@@ -86,6 +88,7 @@ def lib():
         L.cil_icp_batch_create.argtypes = [P, P, I, P, P]
         L.cil_icp_batch_run.argtypes = [P, P, P, P, P, P, P, P]
         L.cil_icp_batch_destroy.argtypes = [P]
+        L.cil_icp_batch_fallback.argtypes = [P, P, P, ctypes.c_double, P, P, P, P]
         L.cil_icp_batch_destroy.restype = None
         L.cil_launch_count.restype = I64
         L.cil_knn_hybrid.argtypes = [P, I64, P, I64, I, F, P, P, P]
@@ -150,10 +153,10 @@ def _check(st, where):
         raise CilError(st, where)
 
 
-def _params(cell_size=0.0, cell_scale=0.0, block=0):
-    if not (cell_size or cell_scale or block):
+def _params(cell_size=0.0, cell_scale=0.0, block=0, topk=0):
+    if not (cell_size or cell_scale or block or topk):
         return None
-    return Params(float(cell_size), float(cell_scale), int(block), 0)
+    return Params(float(cell_size), float(cell_scale), int(block), int(topk))
 
 
 # ---------------------------------------------------------------------------
@@ -164,8 +167,8 @@ def sync_status(stream=None) -> int:
     return int(lib().cil_sync_status(_stream(stream)))
 
 
-def knn(ref, qry, k: int, *, cell_size=0.0, cell_scale=0.0, block=0, with_d2=True, stream=None,
-        out_idx=None, out_d2=None):
+def knn(ref, qry, k: int, *, cell_size=0.0, cell_scale=0.0, block=0, topk=0, with_d2=True,
+        stream=None, out_idx=None, out_d2=None):
     """k nearest neighbours (cil_knn): (idx int32 (Nq,k), d2 float32 (Nq,k))."""
     torch = _torch()
     ref = _points(ref, "ref")
@@ -176,7 +179,7 @@ def knn(ref, qry, k: int, *, cell_size=0.0, cell_scale=0.0, block=0, with_d2=Tru
         out_idx = torch.empty((nq, k), dtype=torch.int32, device=qry.device)
     if with_d2 and out_d2 is None:
         out_d2 = torch.empty((nq, k), dtype=torch.float32, device=qry.device)
-    prm = _params(cell_size, cell_scale, block)
+    prm = _params(cell_size, cell_scale, block, topk)
     st = lib().cil_knn_ex(_ptr(ref), ref.shape[0], _ptr(qry), nq, int(k), _ptr(out_idx),
                           _ptr(out_d2) if with_d2 else None,
                           ctypes.byref(prm) if prm is not None else None, _stream(stream))
@@ -256,7 +259,7 @@ def radius_search(ref, qry, r: float, capacity: int | None = None, stream=None):
     return off, idx[:n], d2[:n]
 
 
-def estimate_normals(xyz, k: int, viewpoint, *, cell_size=0.0, cell_scale=0.0, block=0,
+def estimate_normals(xyz, k: int, viewpoint, *, cell_size=0.0, cell_scale=0.0, block=0, topk=0,
                      stream=None, out_normals=None, out_curvature=None, with_curvature=True):
     """PCA normals + curvature (cil_estimate_normals)."""
     torch = _torch()
@@ -267,7 +270,7 @@ def estimate_normals(xyz, k: int, viewpoint, *, cell_size=0.0, cell_scale=0.0, b
     if with_curvature and out_curvature is None:
         out_curvature = torch.empty(n, dtype=torch.float32, device=xyz.device)
     vp = (ctypes.c_float * 3)(*[float(v) for v in np.asarray(viewpoint, np.float64).reshape(3)])
-    prm = _params(cell_size, cell_scale, block)
+    prm = _params(cell_size, cell_scale, block, topk)
     st = lib().cil_estimate_normals_ex(_ptr(xyz), n, int(k), vp, _ptr(out_normals),
                                        _ptr(out_curvature) if with_curvature else None,
                                        ctypes.byref(prm) if prm is not None else None,
@@ -313,12 +316,15 @@ ASSOCIATIONS = {"nearest": 0, "projective": 1}
 
 def icp(src, dst, dst_normals=None, T_init=None, iters: int = 20, max_corr_dist: float = 0.1, *,
         metric: str = "point_to_plane", w_point: float = 0.0, w_plane: float = 1.0,
-        association: str = "nearest", pixel_map=None, intrinsics=None, stream=None):
+        association: str = "nearest", pixel_map=None, intrinsics=None, with_sums: bool = False,
+        stream=None):
     """Rigid ICP with a chosen metric and correspondence search (cil_icp).
     metric: point_to_plane | point_to_point | combined (weights w_point,
     w_plane); association: nearest | projective (pixel_map: int32 CUDA tensor
     (height, width) of target point indices or -1; intrinsics (fx, fy, cx,
-    cy)).  Returns (T 4x4 float64 numpy, report dict)."""
+    cy)).  Returns (T 4x4 float64 numpy, report dict); with_sums=True
+    (cil_icp_sums) adds report['sums'], float64 (iters + 1, 29): each round's
+    H upper triangle (21), g (6), sum r^2 and inlier count."""
     src = _points(src, "src")
     dst = _points(dst, "dst")
     nrm = None
@@ -346,13 +352,22 @@ def icp(src, dst, dst_normals=None, T_init=None, iters: int = 20, max_corr_dist:
         T0 = (ctypes.c_double * 16)(*np.asarray(T_init, np.float64).reshape(16).tolist())
     Tout = (ctypes.c_double * 16)()
     rep = IcpReport()
-    st = lib().cil_icp(_ptr(src), src.shape[0], _ptr(dst), _ptr(nrm) if nrm is not None else None,
-                       dst.shape[0], T0, int(iters), float(max_corr_dist), ctypes.byref(o), Tout,
-                       ctypes.byref(rep), _stream(stream))
-    _check(st, "cil_icp")
-    return np.array(Tout[:], np.float64).reshape(4, 4), {
-        "rmse": rep.rmse, "n_inliers": int(rep.n_inliers), "iters_done": rep.iters_done,
-        "status": rep.status}
+    args = (_ptr(src), src.shape[0], _ptr(dst), _ptr(nrm) if nrm is not None else None,
+            dst.shape[0], T0, int(iters), float(max_corr_dist), ctypes.byref(o), Tout,
+            ctypes.byref(rep))
+    sums = None
+    if with_sums:
+        sums = np.zeros((int(iters) + 1, 29), np.float64)
+        st = lib().cil_icp_sums(*args, sums.ctypes.data_as(ctypes.c_void_p), _stream(stream))
+        _check(st, "cil_icp_sums")
+    else:
+        st = lib().cil_icp(*args, _stream(stream))
+        _check(st, "cil_icp")
+    out = {"rmse": rep.rmse, "n_inliers": int(rep.n_inliers), "iters_done": rep.iters_done,
+           "status": rep.status}
+    if sums is not None:
+        out["sums"] = sums
+    return np.array(Tout[:], np.float64).reshape(4, 4), out
 
 
 def segment(xyz, normals, k: int = 30, theta: float = 2.8, radius: float = 0.0, stream=None):
@@ -391,7 +406,7 @@ def smooth_segment(xyz, k: int = 30, viewpoint=(0.0, 0.0, 0.0), theta: float = 2
 
 def register_pair(src, dst, k: int, viewpoint, iters: int, max_corr_dist: float, *,
                   T_init=None, out_normals=None, out_T=None, out_report=None, cell_size=0.0,
-                  cell_scale=0.0, block=0, stream=None):
+                  cell_scale=0.0, block=0, topk=0, stream=None):
     """Target grid + k-NN normals + ICP in one enqueue (cil_register_pair).
     Everything stays on the device: returns (T (16,) float64 CUDA tensor,
     report (cil_icp_report bytes in a uint8 CUDA tensor, decode with
@@ -405,7 +420,7 @@ def register_pair(src, dst, k: int, viewpoint, iters: int, max_corr_dist: float,
     if out_report is None:
         out_report = torch.empty(ctypes.sizeof(IcpReport), dtype=torch.uint8, device=dev)
     vp = (ctypes.c_float * 3)(*[float(v) for v in np.asarray(viewpoint, np.float64).reshape(3)])
-    prm = _params(cell_size, cell_scale, block)
+    prm = _params(cell_size, cell_scale, block, topk)
     st = lib().cil_register_pair(_ptr(src), src.shape[0], _ptr(dst), dst.shape[0], int(k), vp,
                                  _ptr(T_init) if T_init is not None else None, int(iters),
                                  float(max_corr_dist), _ptr(out_normals), _ptr(out_T),
@@ -439,7 +454,7 @@ class Batch:
     one graph launch per run.  Inputs are the pairs' clouds concatenated."""
 
     def __init__(self, n_src, n_dst, *, k: int = 10, iters: int = 30, max_corr_dist: float = 0.1,
-                 viewpoint=(0.0, 0.0, 10.0), cell_size=0.0, cell_scale=0.0, block=0):
+                 viewpoint=(0.0, 0.0, 10.0), cell_size=0.0, cell_scale=0.0, block=0, topk=0):
         self.n_src = np.ascontiguousarray(n_src, np.int64)
         self.n_dst = np.ascontiguousarray(n_dst, np.int64)
         if self.n_src.shape != self.n_dst.shape or self.n_src.ndim != 1:
@@ -447,7 +462,8 @@ class Batch:
         self.B = int(self.n_src.shape[0])
         self.params = BatchParams(int(k), int(iters), float(max_corr_dist),
                                   (ctypes.c_float * 3)(*[float(v) for v in viewpoint]),
-                                  Params(float(cell_size), float(cell_scale), int(block), 0))
+                                  Params(float(cell_size), float(cell_scale), int(block),
+                                         int(topk)))
         h = ctypes.c_void_p()
         st = lib().cil_icp_batch_create(self.n_src.ctypes.data_as(ctypes.c_void_p),
                                         self.n_dst.ctypes.data_as(ctypes.c_void_p), self.B,
@@ -472,6 +488,24 @@ class Batch:
                                      _ptr(rep), _ptr(normals_out), _stream(stream))
         _check(st, "cil_icp_batch_run")
         return T_out, rep
+
+    def fallback(self, src_cat, dst_cat, T_out, rep, rmse_threshold: float = 0.005,
+                 used_out=None, stream=None):
+        """After run(..., T_init=warm start): re-register from the identity
+        the pairs whose final RMSE is >= rmse_threshold (or NaN) and keep the
+        better result in T_out / rep (cil_icp_batch_fallback).  Returns the
+        int32 CUDA tensor `used` (0 kept, 1 re-registered but kept, 2
+        replaced)."""
+        torch = _torch()
+        src_cat = _points(src_cat, "src_cat")
+        dst_cat = _points(dst_cat, "dst_cat")
+        if used_out is None:
+            used_out = torch.empty(self.B, dtype=torch.int32, device=dst_cat.device)
+        st = lib().cil_icp_batch_fallback(self._h, _ptr(src_cat), _ptr(dst_cat),
+                                          float(rmse_threshold), _ptr(T_out), _ptr(rep),
+                                          _ptr(used_out), _stream(stream))
+        _check(st, "cil_icp_batch_fallback")
+        return used_out
 
     def close(self):
         if getattr(self, "_h", None):

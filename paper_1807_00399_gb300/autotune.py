@@ -1,12 +1,20 @@
 """Autotuner for batched registration (cil_icp_batch_*).
 
-Searches the grid cell-size multiplier (the cell edge is the nearest
-power-of-two multiple of each cloud's fine lattice to scale x the data-driven
-neighbourhood radius, so scales 1 / 1.5 / 2 select the estimate's level or
-the one above, depending on where the estimate falls between two levels; 1.5
-is the library default) and the query-kernel block size, timing whole batch
-runs with CUDA events.  The winner is cached as JSON keyed by GPU name
-and a size bucket (pairs rounded up to a power of two, mean cloud size to the
+Three knobs, none of which changes a result (the searches are exact whatever
+the cell size, block shape or top-k layout; tests check the transforms are
+bitwise equal across every configuration tried):
+  cell_scale  multiplier on the data-driven cell edge (each cloud's cell is
+              the nearest power-of-two multiple of its fine lattice to scale x
+              the median k-th neighbour distance of sampled points);
+  block       threads per block of the normals kernel (64, 128, 256);
+  topk        how each query keeps its k best keys: 1 = sorted register list,
+              2 = binary max-heap in shared memory (0 = by k).
+The search is coordinate descent on whole timed batch runs (CUDA events):
+the cell scale over SCALES at the default block and layout, extended by
+factors of 1.5 past either end while the best scale sits on that end (so the
+winner is bracketed), then the block size, then the top-k layout, each at the
+best values found so far.  The winner is cached as JSON keyed by GPU name and
+a size bucket (pairs rounded up to a power of two, mean cloud size to the
 nearest power of two, k, rounds), in $CIL_TUNE_CACHE or
 ~/.cache/cil_gb300/tuning.json.
 """
@@ -18,8 +26,10 @@ import os
 
 import numpy as np
 
-SCALES = (1.0, 1.5, 2.0)
+SCALES = (0.5, 0.75, 1.0, 1.5, 2.0, 3.0, 4.0)
 BLOCKS = (64, 128, 256)
+TOPK = (1, 2)
+SCALE_LIMITS = (0.125, 16.0)  # the range extension stops here
 
 
 def cache_path() -> str:
@@ -74,11 +84,51 @@ def time_batch(h, src, dst, reps: int = 3, warmup: int = 1) -> float:
     return float(np.median(ts))
 
 
+def coordinate_descent(time_fn, scales=SCALES, blocks=BLOCKS, topks=TOPK,
+                       limits=SCALE_LIMITS, default_block: int = 128, default_topk: int = 0):
+    """The search itself, on any cost function time_fn(cell_scale, block,
+    topk) -> ms.  Returns (best (scale, block, topk), table of every timed
+    configuration in the order tried, whether the best scale is interior to
+    the scales tried)."""
+    table, seen = [], {}
+
+    def timed(sc, bl, tk):
+        cfg = (float(sc), int(bl), int(tk))
+        if cfg not in seen:
+            seen[cfg] = float(time_fn(*cfg))
+            table.append({"cell_scale": cfg[0], "block": cfg[1], "topk": cfg[2], "ms": seen[cfg]})
+        return seen[cfg]
+
+    bl0, tk0 = default_block, default_topk
+    sc_list = sorted(float(v) for v in scales)
+    for sc in sc_list:
+        timed(sc, bl0, tk0)
+    while True:  # extend past an edge winner until the best scale is bracketed
+        best_sc = min(sc_list, key=lambda v: seen[(v, bl0, tk0)])
+        if best_sc == sc_list[-1] and sc_list[-1] * 1.5 <= limits[1]:
+            sc_list.append(sc_list[-1] * 1.5)
+            timed(sc_list[-1], bl0, tk0)
+        elif best_sc == sc_list[0] and sc_list[0] / 1.5 >= limits[0]:
+            sc_list.insert(0, sc_list[0] / 1.5)
+            timed(sc_list[0], bl0, tk0)
+        else:
+            break
+    best_bl = min(blocks, key=lambda b: timed(best_sc, b, tk0))
+    if seen[(best_sc, bl0, tk0)] <= seen[(best_sc, best_bl, tk0)]:
+        best_bl = bl0
+    best_tk = min(topks, key=lambda t: timed(best_sc, best_bl, t))
+    if seen[(best_sc, best_bl, tk0)] <= seen[(best_sc, best_bl, best_tk)]:
+        best_tk = tk0
+    return (best_sc, best_bl, best_tk), table, sc_list[0] < best_sc < sc_list[-1]
+
+
 def tune_batch(src_cat, dst_cat, n_src, n_dst, *, k: int = 10, iters: int = 30,
                max_corr_dist: float = 0.1, viewpoint=(0.0, 0.0, 10.0), reps: int = 3,
-               use_cache: bool = True, scales=SCALES, blocks=BLOCKS) -> dict:
-    """Return {"cell_scale", "block", "ms", "key", "table", "cached"} for the
-    fastest configuration of this batch shape."""
+               use_cache: bool = True, scales=SCALES, blocks=BLOCKS, topks=TOPK) -> dict:
+    """Return {"cell_scale", "block", "topk", "ms", "scale_interior", "key",
+    "table", "cached"} for the fastest configuration of this batch shape
+    found by coordinate descent (module docstring); "table" lists every
+    configuration timed, in the order tried."""
     import torch
 
     from . import Batch
@@ -92,16 +142,17 @@ def tune_batch(src_cat, dst_cat, n_src, n_dst, *, k: int = 10, iters: int = 30,
         out["cached"] = True
         out["key"] = key
         return out
-    table = []
-    for sc in scales:
-        for bl in blocks:
-            h = Batch(n_src, n_dst, k=k, iters=iters, max_corr_dist=max_corr_dist,
-                      viewpoint=viewpoint, cell_scale=sc, block=bl)
-            ms = time_batch(h, src_cat, dst_cat, reps=reps)
-            h.close()
-            table.append({"cell_scale": sc, "block": bl, "ms": ms})
-    best = min(table, key=lambda r: r["ms"])
-    out = {"cell_scale": best["cell_scale"], "block": best["block"], "ms": best["ms"],
+
+    def time_fn(sc, bl, tk):
+        h = Batch(n_src, n_dst, k=k, iters=iters, max_corr_dist=max_corr_dist,
+                  viewpoint=viewpoint, cell_scale=sc, block=bl, topk=tk)
+        ms = time_batch(h, src_cat, dst_cat, reps=reps)
+        h.close()
+        return ms
+
+    (sc, bl, tk), table, interior = coordinate_descent(time_fn, scales, blocks, topks)
+    best_ms = min(r["ms"] for r in table if (r["cell_scale"], r["block"], r["topk"]) == (sc, bl, tk))
+    out = {"cell_scale": sc, "block": bl, "topk": tk, "ms": best_ms, "scale_interior": interior,
            "table": table}
     if use_cache:
         data[key] = out

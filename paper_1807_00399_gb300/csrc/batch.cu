@@ -8,6 +8,12 @@
 //   tiles, see icp.cu) with the final RMSE pass.
 // The sequence is captured once per set of buffer pointers into a CUDA graph
 // and replayed with a single cudaGraphLaunch on the caller's stream.
+//
+// Fallback after a warm-started run (the learned warm start keeps plain ICP
+// from the identity as its fallback): the pairs whose final RMSE is at or
+// above a threshold (or undefined) are marked on the device, re-registered
+// from the identity over the same target grid and normals (only their tiles
+// are launched), and each keeps the better of its two results.
 #include <stdlib.h>
 
 #include <vector>
@@ -26,7 +32,8 @@ struct BatchHandle {
   Workspace ws;
   GridPlan gp;
   IcpPlan ip;
-  size_t o_src_start = 0, o_dst_start = 0, o_nrm = 0;
+  size_t o_src_start = 0, o_dst_start = 0, o_nrm = 0, o_active = 0, o_fb_tiles = 0;
+  const float* last_normals = nullptr;  // normals of the last run (null: o_nrm)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
@@ -49,13 +56,56 @@ static cil_status enqueue_batch(BatchHandle* h, const float* src, const float* d
   if (st != CIL_OK) return st;
   const GridView g = grid_view(h->gp, h->ws);
   const int block = h->prm.tune.block ? h->prm.tune.block : 128;
+  const int topk = h->prm.tune.topk >= 0 && h->prm.tune.topk <= 2 ? h->prm.tune.topk : 0;
   if ((st = launch_normals(g, h->B, h->tot_dst, h->prm.k, nullptr, h->prm.viewpoint, dst, nrm,
-                           nullptr, block, s)) != CIL_OK)
+                           nullptr, block, s, nullptr, topk)) != CIL_OK)
     return st;
   if ((st = icp_run(h->ip, h->ws, g, src, src_start, dst, nrm, T_init, nullptr, h->prm.iters, nullptr,
                     h->prm.max_corr_dist, h->ctx, s)) != CIL_OK)
     return st;
   return icp_export(h->ip, h->ws, T_out, rep, s);
+}
+
+// Pairs to re-register: final RMSE not below `thr` (NaN included); counts
+// their tiles.  One block.
+__global__ void k_fallback_select(const cil_icp_report* __restrict__ rep, int B, double thr,
+                                  const int* __restrict__ src_start, int* __restrict__ active,
+                                  unsigned* __restrict__ n_tiles) {
+  unsigned t = 0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const bool redo = !(rep[b].rmse < thr);
+    active[b] = redo ? 1 : 0;
+    if (redo) t += (unsigned)((src_start[b + 1] - src_start[b] + kIcpThreads - 1) / kIcpThreads);
+  }
+  atomicAdd(n_tiles, t);
+}
+
+// Keep the better result of each re-registered pair: the identity-started
+// one replaces the first when its RMSE is smaller, or when the first has none.
+// used[b]: 0 not re-registered, 1 re-registered and the first result kept,
+// 2 replaced.
+__global__ void k_fallback_merge(const IcpPairState* __restrict__ st, int B,
+                                 const int* __restrict__ active, double* __restrict__ T_out,
+                                 cil_icp_report* __restrict__ rep, int* __restrict__ used) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  int u = 0;
+  if (active[b]) {
+    const IcpPairState& S = st[b];
+    const double r0 = rep[b].rmse, r1 = S.rmse;
+    const bool better = (r1 < r0) || (isnan(r0) && !isnan(r1));
+    u = better ? 2 : 1;
+    if (better) {
+      for (int j = 0; j < 16; ++j) T_out[16 * b + j] = S.T[j];
+      cil_icp_report r;
+      r.rmse = S.rmse;
+      r.n_inliers = S.n_inl;
+      r.iters_done = S.iters;
+      r.status = S.status;
+      rep[b] = r;
+    }
+  }
+  if (used) used[b] = u;
 }
 
 }  // namespace cil
@@ -99,6 +149,8 @@ cil_status cil_icp_batch_create(const int64_t* n_src, const int64_t* n_dst, int 
   h->o_src_start = h->ws.reserve(sizeof(int) * (B + 1));
   h->o_dst_start = h->ws.reserve(sizeof(int) * (B + 1));
   h->o_nrm = h->ws.reserve(sizeof(float) * 3 * (size_t)(td > 0 ? td : 1));
+  h->o_active = h->ws.reserve(sizeof(int) * B);
+  h->o_fb_tiles = h->ws.reserve(sizeof(unsigned));
   if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     delete hb;
     return CIL_ERR_CUDA;
@@ -171,7 +223,43 @@ cil_status cil_icp_batch_run(cil_batch* hb, const float* src_cat, const float* d
   }
   if (cudaGraphLaunch(h->exec, s) != cudaSuccess) return CIL_ERR_CUDA;
   note_launches(h->launches_per_run);
+  h->last_normals = normals_out;
   return CIL_OK;
+}
+
+cil_status cil_icp_batch_fallback(cil_batch* hb, const float* src_cat, const float* dst_cat,
+                                  double rmse_threshold, double* T_out, cil_icp_report* rep,
+                                  int32_t* used_out, void* stream) {
+  if (!hb || !T_out || !rep || (hb->h.tot_src > 0 && !src_cat) || (hb->h.tot_dst > 0 && !dst_cat) ||
+      !(rmse_threshold >= 0.0))
+    return CIL_ERR_INVALID_ARG;
+  BatchHandle* h = &hb->h;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != h->device) return CIL_ERR_INVALID_ARG;
+  if (!h->exec) return CIL_ERR_INVALID_ARG;  // no run to fall back from
+  cudaStream_t s = (cudaStream_t)stream;
+  int* active = h->ws.at<int>(h->o_active);
+  unsigned* fb_tiles = h->ws.at<unsigned>(h->o_fb_tiles);
+  const int* src_start = h->ws.at<int>(h->o_src_start);
+  if (cudaMemsetAsync(fb_tiles, 0, sizeof(unsigned), s) != cudaSuccess) return CIL_ERR_CUDA;
+  note_launches(1);
+  k_fallback_select<<<1, 1024, 0, s>>>(rep, h->B, rmse_threshold, src_start, active, fb_tiles);
+  unsigned n_tiles = 0;
+  if (cudaMemcpyAsync(&n_tiles, fb_tiles, sizeof(unsigned), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return CIL_ERR_CUDA;
+  if (n_tiles > 0) {
+    const float* nrm = h->last_normals ? h->last_normals : h->ws.at<float>(h->o_nrm);
+    cil_status st = icp_run(h->ip, h->ws, grid_view(h->gp, h->ws), src_cat, src_start, dst_cat,
+                            nrm, nullptr, nullptr, h->prm.iters, nullptr, h->prm.max_corr_dist,
+                            h->ctx, s, nullptr, active, (int)n_tiles);
+    if (st != CIL_OK) return st;
+  }
+  note_launches(1);
+  k_fallback_merge<<<ceil_div(h->B, 128), 128, 0, s>>>(icp_state(h->ip, h->ws), h->B, active, T_out,
+                                                      rep, used_out);
+  return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
 }
 
 void cil_icp_batch_destroy(cil_batch* hb) {

@@ -145,6 +145,9 @@ static GridOptions grid_options(const cil_params* prm, int k) {
 }
 
 static int block_of(const cil_params* prm) { return prm && prm->block ? prm->block : 128; }
+static int topk_of(const cil_params* prm) {
+  return prm && prm->topk >= 0 && prm->topk <= 2 ? prm->topk : 0;
+}
 
 }  // namespace cil
 
@@ -243,7 +246,7 @@ cil_status cil_knn_ex(const float* ref, int64_t n_ref, const float* qry, int64_t
     order = ws.at<int>(o_order);
     if ((st = order_queries(op, ws, qry, nullptr, 1, g.prm, nullptr, order, s)) != CIL_OK) return st;
   }
-  st = launch_knn(g, qry, n_qry, order, k, out_idx, out_d2, block_of(params), s);
+  st = launch_knn(g, qry, n_qry, order, k, out_idx, out_d2, block_of(params), s, topk_of(params));
   ws.release(s);
   return st;
 }
@@ -269,7 +272,7 @@ cil_status cil_estimate_normals_ex(const float* xyz, int64_t n, int k, const flo
   if ((st = ws.allocate(ctx, s)) != CIL_OK) return st;
   if ((st = grid_build(gp, ws, xyz, nullptr, grid_options(params, k), ctx, s)) != CIL_OK) return st;
   st = launch_normals(grid_view(gp, ws), 1, n, k, nullptr, viewpoint, xyz, out_normals,
-                      out_curvature, block_of(params), s);
+                      out_curvature, block_of(params), s, nullptr, topk_of(params));
   ws.release(s);
   return st;
 }
@@ -337,9 +340,11 @@ cil_status cil_estimate_normals_radius(const float* xyz, int64_t n, float r, con
   return st;
 }
 
-cil_status cil_icp(const float* src, int64_t n_src, const float* dst, const float* dst_normals,
-                   int64_t n_dst, const double* T_init, int max_iters, float max_corr_dist,
-                   const cil_icp_options* opt, double* T_out, cil_icp_report* rep, void* stream) {
+// Shared body of cil_icp and cil_icp_sums (sums_out: host, or null).
+static cil_status icp_impl(const float* src, int64_t n_src, const float* dst,
+                           const float* dst_normals, int64_t n_dst, const double* T_init,
+                           int max_iters, float max_corr_dist, const cil_icp_options* opt,
+                           double* T_out, cil_icp_report* rep, double* sums_out, void* stream) {
   IcpOptions o;
   if (opt) {
     if (opt->metric < CIL_METRIC_POINT_TO_PLANE || opt->metric > CIL_METRIC_COMBINED ||
@@ -385,7 +390,13 @@ cil_status cil_icp(const float* src, int64_t n_src, const float* dst, const floa
   const int64_t counts[1] = {n_src};
   icp_plan(ip, ws, counts, 1);
   const size_t o_out = ws.reserve(sizeof(double) * 16 + sizeof(cil_icp_report));
+  const size_t n_sums = (size_t)(max_iters + 1) * (kIcpQ + 1);
+  const size_t o_sums = sums_out ? ws.reserve(sizeof(double) * n_sums) : 0;
   if ((st = ws.allocate(ctx, s)) != CIL_OK) return st;
+  if (sums_out) {
+    o.sums = ws.at<double>(o_sums);
+    if (cudaMemsetAsync(o.sums, 0, sizeof(double) * n_sums, s) != cudaSuccess) return CIL_ERR_CUDA;
+  }
   GridOptions gopt = grid_options(nullptr, 10);
   if ((st = grid_build(gp, ws, dst, nullptr, gopt, ctx, s)) != CIL_OK) return st;
   if ((st = icp_run(ip, ws, grid_view(gp, ws), src, nullptr, dst, need_normals ? dst_normals : nullptr,
@@ -399,6 +410,9 @@ cil_status cil_icp(const float* src, int64_t n_src, const float* dst, const floa
     cil_icp_report r;
   } h;
   if (cudaMemcpyAsync(&h, Td, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CIL_ERR_CUDA;
+  if (sums_out && cudaMemcpyAsync(sums_out, o.sums, sizeof(double) * n_sums,
+                                  cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return CIL_ERR_CUDA;
   ws.release(s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return CIL_ERR_CUDA;
   for (int j = 0; j < 16; ++j) T_out[j] = h.T[j];
@@ -406,6 +420,22 @@ cil_status cil_icp(const float* src, int64_t n_src, const float* dst, const floa
   cil_status dev = read_error_word(ctx, s, true);
   if (dev != CIL_OK) return dev;
   return CIL_OK;
+}
+
+cil_status cil_icp(const float* src, int64_t n_src, const float* dst, const float* dst_normals,
+                   int64_t n_dst, const double* T_init, int max_iters, float max_corr_dist,
+                   const cil_icp_options* opt, double* T_out, cil_icp_report* rep, void* stream) {
+  return icp_impl(src, n_src, dst, dst_normals, n_dst, T_init, max_iters, max_corr_dist, opt,
+                  T_out, rep, nullptr, stream);
+}
+
+cil_status cil_icp_sums(const float* src, int64_t n_src, const float* dst,
+                        const float* dst_normals, int64_t n_dst, const double* T_init,
+                        int max_iters, float max_corr_dist, const cil_icp_options* opt,
+                        double* T_out, cil_icp_report* rep, double* sums_out, void* stream) {
+  if (!sums_out) return CIL_ERR_INVALID_ARG;
+  return icp_impl(src, n_src, dst, dst_normals, n_dst, T_init, max_iters, max_corr_dist, opt,
+                  T_out, rep, sums_out, stream);
 }
 
 // Shared body of cil_segment (normals given) and cil_smooth_segment (normals
@@ -510,7 +540,7 @@ cil_status cil_register_pair(const float* src, int64_t n_src, const float* dst, 
   if ((st = grid_build(gp, ws, dst, nullptr, gopt, ctx, s)) != CIL_OK) return st;
   const GridView g = grid_view(gp, ws);
   if ((st = launch_normals(g, 1, n_dst, k, nullptr, viewpoint, dst, nrm, nullptr, block_of(params),
-                           s)) != CIL_OK)
+                           s, nullptr, topk_of(params))) != CIL_OK)
     return st;
   if ((st = icp_run(ip, ws, g, src, nullptr, dst, nrm, T_init, nullptr, max_iters, nullptr, max_corr_dist,
                     ctx, s)) != CIL_OK)

@@ -393,6 +393,14 @@ constexpr int topk_smem_per_thread() {
   return KMAX >= kHeapFromK ? KMAX * (int)sizeof(u64) : 0;
 }
 
+// Top-k layout picked at run time (a tuning axis; results do not depend on
+// it): 0 = by k as TopKFor, 1 = register list, 2 = shared-memory heap.
+template <int KMAX, bool HEAP>
+using TopKSel = typename std::conditional<HEAP, TopKHeap<KMAX>, TopK<KMAX>>::type;
+constexpr bool topk_heap(int kmax, int layout) {
+  return layout == 2 || (layout != 1 && kmax >= kHeapFromK);
+}
+
 // Exact k nearest neighbours of q among the points of cloud `cloud`.
 // Rings of cells are searched at the cloud's level; a search that has not
 // proved its k-th distance after kRingCap rings (sparse regions, queries far

@@ -5,8 +5,10 @@
 
 namespace cil {
 
+// topk_layout: 0 = by k, 1 = register list, 2 = shared-memory heap (the
+// results do not depend on it)
 cil_status launch_knn(const GridView& g, const float* qry, int64_t nq, const int* order, int k,
-                      int* out_idx, float* out_d2, int block, cudaStream_t s);
+                      int* out_idx, float* out_d2, int block, cudaStream_t s, int topk_layout = 0);
 
 // viewpoints: vp_dev (device float[3 * clouds]) or, when null, vp_host[3]
 // out_idx (optional, single cloud): the k neighbour indices of every point,
@@ -14,7 +16,8 @@ cil_status launch_knn(const GridView& g, const float* qry, int64_t nq, const int
 // lists the normals used
 cil_status launch_normals(const GridView& g, int clouds, int64_t n, int k, const float* vp_dev,
                           const float* vp_host, const float* xyz, float* out_n, float* out_c,
-                          int block, cudaStream_t s, int* out_idx = nullptr);
+                          int block, cudaStream_t s, int* out_idx = nullptr,
+                          int topk_layout = 0);
 
 cil_status launch_knn_hybrid(const GridView& g, const float* qry, int64_t nq, const int* order,
                              int k, float r, int* out_idx, float* out_d2, cudaStream_t s);
@@ -47,6 +50,8 @@ struct IcpOptions {
   const int* pixel_map = nullptr;  // device int32[height][width]: target index or -1
   int width = 0, height = 0;
   float fx = 0.0f, fy = 0.0f, cx = 0.0f, cy = 0.0f;
+  double* sums = nullptr;  // device [pairs][rounds][kIcpQ + 1]: each round's sums and inlier
+                           // count as the round close sees them, or null (not recorded)
 };
 
 struct IcpPairState {
@@ -89,12 +94,15 @@ void icp_plan(IcpPlan& p, Workspace& ws, const int64_t* src_counts, int pairs);
 // double[16 * pairs], or host double[16] for one pair, or both null =
 // identity) and run all rounds plus the final RMSE pass (three launches per
 // round).  `src_start_dev`: device int[pairs+1] (null for one pair).
+// `active_dev` (device int[pairs], or null = all): pairs with 0 get no tiles;
+// `n_tiles_active` is then the tile count of the active pairs (launch size).
 cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt,
                    const float* src, const int* src_start_dev, const float* dst,
                    const float* dst_normals,
                    const double* T_init_dev, const double* T_init_host, int iters,
                    const float* dmax_dev, float dmax, DeviceCtx* ctx, cudaStream_t s,
-                   const IcpOptions* opt = nullptr);
+                   const IcpOptions* opt = nullptr, const int* active_dev = nullptr,
+                   int n_tiles_active = -1);
 
 IcpPairState* icp_state(const IcpPlan& p, const Workspace& ws);
 

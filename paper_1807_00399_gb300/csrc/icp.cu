@@ -651,7 +651,7 @@ __device__ __noinline__ void close_round(IcpPairState& S, const double* tot, lon
 __global__ void k_icp_setup(IcpPairState* st, int pairs, const int* src_start, int64_t n_src_single,
                             int* tile_off, const double* T_init, Mat4 T_host, int use_host_T,
                             const float* dmax_dev, float dmax, int iters, float* rt_out,
-                            const GridParams* prm, const float* dst) {
+                            const GridParams* prm, const float* dst, const int* active) {
   // single block: tile prefix over pairs
   __shared__ int carry, gcarry;
   __shared__ int tmp[1024], gtmp[1024];
@@ -665,7 +665,8 @@ __global__ void k_icp_setup(IcpPairState* st, int pairs, const int* src_start, i
     int nt = 0;
     if (b < pairs) {
       const int64_t n = src_start ? (int64_t)(src_start[b + 1] - src_start[b]) : n_src_single;
-      nt = (int)((n + kTileSrc - 1) / kTileSrc);
+      // a pair left out of this run (active[b] == 0) gets no tiles
+      nt = (active && !active[b]) ? 0 : (int)((n + kTileSrc - 1) / kTileSrc);
     }
     // serial exclusive prefix of this chunk of pairs (pairs are few)
     const int ng = (nt + kIcpGroup - 1) / kIcpGroup;
@@ -1226,6 +1227,10 @@ __global__ void __launch_bounds__(kIcpThreads, 4) k_icp_accumulate(IcpArgs a, in
     }
   }
   __syncthreads();
+  if (a.opt.sums && tid <= kIcpQ) {
+    double* o = a.opt.sums + ((int64_t)b * a.rounds + round) * (kIcpQ + 1);
+    o[tid] = tid < kIcpQ ? sm_tot[tid] : (double)sm_cnt;
+  }
   if (tid == 0) {
     IcpPairState& S = a.st[b];
     close_round(S, sm_tot, sm_cnt, round == a.rounds - 1, a.opt.metric);
@@ -1309,7 +1314,8 @@ cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt, c
                    const int* src_start_dev, const float* dst, const float* dst_normals,
                    const double* T_init_dev, const double* T_init_host, int iters,
                    const float* dmax_dev, float dmax, DeviceCtx* ctx, cudaStream_t s,
-                   const IcpOptions* opt) {
+                   const IcpOptions* opt, const int* active_dev, int n_tiles_active) {
+  const int n_tiles = n_tiles_active >= 0 ? n_tiles_active : p.n_tiles;
   Mat4 Th;
   for (int j = 0; j < 16; ++j) Th.m[j] = T_init_host ? T_init_host[j] : 0.0;
   IcpPairState* st = ws.at<IcpPairState>(p.o_state);
@@ -1318,7 +1324,8 @@ cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt, c
   unsigned* qc = ws.at<unsigned>(p.o_qc);
   note_launches(1);
   k_icp_setup<<<1, 1024, 0, s>>>(st, p.pairs, src_start_dev, p.n_src, tile_off, T_init_dev, Th,
-                                 T_init_host != nullptr, dmax_dev, dmax, iters, rt, tgt.prm, dst);
+                                 T_init_host != nullptr, dmax_dev, dmax, iters, rt, tgt.prm, dst,
+                                 active_dev);
   if (cudaMemsetAsync(qc, 0, sizeof(unsigned) * 4, s) != cudaSuccess) return CIL_ERR_CUDA;
   if (cudaMemsetAsync(ws.at<int>(p.o_grp_done), 0,
                       sizeof(int) * (size_t)(p.n_groups > 0 ? p.n_groups : 1), s) != cudaSuccess)
@@ -1326,7 +1333,7 @@ cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt, c
   int* order = ws.at<int>(p.o_order);
   cil_status stt = order_queries(p.order, ws, src, src_start_dev, p.pairs, tgt.prm, rt, order, s);
   if (stt != CIL_OK) return stt;
-  if (p.n_tiles == 0) return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
+  if (n_tiles == 0) return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
   IcpArgs a;
   a.g = tgt;
   a.src = src;
@@ -1338,7 +1345,7 @@ cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt, c
   a.src_start = src_start_dev;
   a.n_src1 = (int)p.n_src;
   a.pairs = p.pairs;
-  a.n_tiles = p.n_tiles;
+  a.n_tiles = n_tiles;
   a.rounds = iters + 1;
   a.st = st;
   a.corr = ws.at<int>(p.o_corr);
@@ -1367,12 +1374,12 @@ cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt, c
     for (int r = 0; r < a.rounds; ++r) {
       if (r == timed_round) {
         TimedRegion t1("k_icp_search", s);
-        if (launch_after(k_icp_search, p.n_tiles, s, a, r) != cudaSuccess) return CIL_ERR_CUDA;
-      } else if (launch_after(k_icp_search, p.n_tiles, s, a, r) != cudaSuccess) {
+        if (launch_after(k_icp_search, n_tiles, s, a, r) != cudaSuccess) return CIL_ERR_CUDA;
+      } else if (launch_after(k_icp_search, n_tiles, s, a, r) != cudaSuccess) {
         return CIL_ERR_CUDA;
       }
       if (launch_after(k_icp_finish, grid_f, s, a, r) != cudaSuccess) return CIL_ERR_CUDA;
-      if (launch_after(k_icp_accumulate, p.n_tiles, s, a, r) != cudaSuccess) return CIL_ERR_CUDA;
+      if (launch_after(k_icp_accumulate, n_tiles, s, a, r) != cudaSuccess) return CIL_ERR_CUDA;
     }
   }
   return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;

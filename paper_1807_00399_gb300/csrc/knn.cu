@@ -20,7 +20,7 @@
 
 namespace cil {
 
-template <int KMAX>
+template <int KMAX, bool HEAP>
 __global__ void __launch_bounds__(256) k_knn(GridView g, const float* __restrict__ qry, int64_t nq,
                                              const int* __restrict__ order, int k,
                                              int* __restrict__ out_idx, float* __restrict__ out_d2) {
@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) k_knn(GridView g, const float* __restrict
     q[2] = p.z;
   }
   extern __shared__ u64 s_topk[];
-  TopKFor<KMAX> top;
+  TopKSel<KMAX, HEAP> top;
   top.bind(s_topk + threadIdx.x, blockDim.x);
   top.init(k);
   grid_knn<KMAX>(g, 0, q, top);
@@ -263,7 +263,7 @@ __device__ __forceinline__ void normal_from_topk(const Top& top, int k,
   finish_normal(C, q, vp, out_n, out_c);
 }
 
-template <int KMAX>
+template <int KMAX, bool HEAP>
 __global__ void __launch_bounds__(256) k_normals(GridView g, int cloud_count, int64_t n, int k,
                                                  const float* __restrict__ vp_all, float vx,
                                                  float vy, float vz,
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(256) k_normals(GridView g, int cloud_count, in
   const int64_t local = __float_as_int(p.w);
   const float q[3] = {p.x, p.y, p.z};
   extern __shared__ u64 s_topk[];
-  TopKFor<KMAX> top;
+  TopKSel<KMAX, HEAP> top;
   top.bind(s_topk + threadIdx.x, blockDim.x);
   top.init(k);
   grid_knn<KMAX>(g, cloud, q, top);
@@ -444,48 +444,72 @@ __global__ void __launch_bounds__(128) k_normals_radius(GridView g, int64_t n, f
 // Threads per block for a top-k kind: the heap variants keep KMAX keys per
 // thread in shared memory and run at most 128 threads per block (32 KB at
 // KMAX = 32), so no launch needs the opt-in above 48 KB.
-template <int KM>
+template <int KM, bool HEAP>
 static int topk_block(int block) {
   if (block != 64 && block != 128 && block != 256) block = 128;
-  return KM >= kHeapFromK ? (block < 128 ? block : 128) : block;
+  return HEAP ? (block < 128 ? block : 128) : block;
 }
 
+template <int KM, bool HEAP>
+static void knn_launch_as(const GridView& g, const float* qry, int64_t nq, const int* order, int k,
+                          int* out_idx, float* out_d2, int block, cudaStream_t s) {
+  const int b = topk_block<KM, HEAP>(block);
+  const int smem = HEAP ? KM * (int)sizeof(u64) * b : 0;
+  k_knn<KM, HEAP><<<ceil_div(nq, b), b, smem, s>>>(g, qry, nq, order, k, out_idx, out_d2);
+}
+
+// layout: 0 = by k, 1 = register list, 2 = shared-memory heap (k = 1 always
+// takes the register list)
 template <int KM>
 static void knn_launch(const GridView& g, const float* qry, int64_t nq, const int* order, int k,
-                       int* out_idx, float* out_d2, int block, cudaStream_t s) {
-  const int b = topk_block<KM>(block);
-  k_knn<KM><<<ceil_div(nq, b), b, topk_smem_per_thread<KM>() * b, s>>>(g, qry, nq, order, k,
-                                                                       out_idx, out_d2);
+                       int* out_idx, float* out_d2, int block, int layout, cudaStream_t s) {
+  if (KM > 1 && topk_heap(KM, layout))
+    knn_launch_as<KM, (KM > 1)>(g, qry, nq, order, k, out_idx, out_d2, block, s);
+  else
+    knn_launch_as<KM, false>(g, qry, nq, order, k, out_idx, out_d2, block, s);
+}
+
+template <int KM, bool HEAP>
+static void normals_launch_as(const GridView& g, int clouds, int64_t n, int k, const float* vp_dev,
+                              float vx, float vy, float vz, const float* xyz, float* out_n,
+                              float* out_c, int* out_idx, int block, cudaStream_t s) {
+  const int b = topk_block<KM, HEAP>(block);
+  const int smem = HEAP ? KM * (int)sizeof(u64) * b : 0;
+  k_normals<KM, HEAP><<<ceil_div(n, b), b, smem, s>>>(g, clouds, n, k, vp_dev, vx, vy, vz, xyz,
+                                                      out_n, out_c, out_idx);
 }
 
 template <int KM>
 static void normals_launch(const GridView& g, int clouds, int64_t n, int k, const float* vp_dev,
                            float vx, float vy, float vz, const float* xyz, float* out_n,
-                           float* out_c, int* out_idx, int block, cudaStream_t s) {
-  const int b = topk_block<KM>(block);
-  k_normals<KM><<<ceil_div(n, b), b, topk_smem_per_thread<KM>() * b, s>>>(
-      g, clouds, n, k, vp_dev, vx, vy, vz, xyz, out_n, out_c, out_idx);
+                           float* out_c, int* out_idx, int block, int layout, cudaStream_t s) {
+  if (KM > 1 && topk_heap(KM, layout))
+    normals_launch_as<KM, (KM > 1)>(g, clouds, n, k, vp_dev, vx, vy, vz, xyz, out_n, out_c,
+                                    out_idx, block, s);
+  else
+    normals_launch_as<KM, false>(g, clouds, n, k, vp_dev, vx, vy, vz, xyz, out_n, out_c, out_idx,
+                                 block, s);
 }
 
 cil_status launch_knn(const GridView& g, const float* qry, int64_t nq, const int* order, int k,
-                      int* out_idx, float* out_d2, int block, cudaStream_t s) {
+                      int* out_idx, float* out_d2, int block, cudaStream_t s, int topk_layout) {
   if (nq <= 0) return CIL_OK;
   TimedRegion timer("k_knn", s);
   note_launches(1);
-  CIL_FOR_K(k, (knn_launch<KM>(g, qry, nq, order, k, out_idx, out_d2, block, s)));
+  CIL_FOR_K(k, (knn_launch<KM>(g, qry, nq, order, k, out_idx, out_d2, block, topk_layout, s)));
   return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
 }
 
 cil_status launch_normals(const GridView& g, int clouds, int64_t n, int k, const float* vp_dev,
                           const float* vp_host, const float* xyz, float* out_n, float* out_c,
-                          int block, cudaStream_t s, int* out_idx) {
+                          int block, cudaStream_t s, int* out_idx, int topk_layout) {
   if (n <= 0) return CIL_OK;
   TimedRegion timer("k_normals", s);
   note_launches(1);
   const float vx = vp_host ? vp_host[0] : 0.0f, vy = vp_host ? vp_host[1] : 0.0f,
               vz = vp_host ? vp_host[2] : 0.0f;
   CIL_FOR_K(k, (normals_launch<KM>(g, clouds, n, k, vp_dev, vx, vy, vz, xyz, out_n, out_c, out_idx,
-                                   block, s)));
+                                   block, topk_layout, s)));
   return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
 }
 

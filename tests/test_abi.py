@@ -56,6 +56,11 @@ def test_argument_errors_need_no_gpu():
     assert L.cil_knn(None, -1, None, 10, 5, None, None, None) == 1
     assert L.cil_estimate_normals(None, 10, 0, None, None, None, None) == 1
     assert L.cil_icp_point_to_plane(None, -5, None, None, 10, None, 1, 0.1, None, None, None) == 1
+    L.cil_icp_sums.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_float,
+                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_void_p]
+    assert L.cil_icp_sums(None, 0, None, None, 0, None, 1, 0.1, None, None, None, None, None) == 1
 
 
 def test_package_fails_loudly_without_library(monkeypatch, tmp_path):

@@ -22,3 +22,21 @@ def test_cache_roundtrip(tmp_path, monkeypatch):
     assert json.loads(path.read_text())["k"]["block"] == 128
     path.write_text("not json")
     assert autotune._load(str(path)) == {}
+
+
+def test_descent_brackets_the_best_scale_and_picks_each_axis():
+    # cost minimal at scale 6 (beyond the listed range), block 64, heap layout
+    def cost(sc, bl, tk):
+        return (np.log(sc / 6.0)) ** 2 + (0.0 if bl == 64 else 0.1) + (0.0 if tk == 2 else 0.05)
+    (sc, bl, tk), table, interior = autotune.coordinate_descent(cost)
+    assert interior and bl == 64 and tk == 2
+    assert abs(np.log(sc / 6.0)) <= np.log(1.5) / 2 + 1e-12  # nearest tried point to 6
+    assert max(r["cell_scale"] for r in table) > 4.0        # the range was extended
+    assert len({(r["cell_scale"], r["block"], r["topk"]) for r in table}) == len(table)
+    # minimum below the range: extended downwards
+    (sc, _, _), table, interior = autotune.coordinate_descent(
+        lambda s, b, t: abs(np.log(s / 0.3)))
+    assert interior and min(r["cell_scale"] for r in table) < 0.5 and abs(sc - 1 / 3) < 1e-9
+    # a flat cost keeps the defaults (block 128, layout by k) and the first scale tried
+    (sc, bl, tk), _, interior = autotune.coordinate_descent(lambda s, b, t: 1.0)
+    assert (bl, tk) == (128, 0) and not interior

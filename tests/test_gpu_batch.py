@@ -9,7 +9,7 @@ import torch
 import oracle
 import paper_1807_00399_gb300 as cil
 from paper_1807_00399_gb300 import synth
-from parity import extent, rot_angle
+from parity import extent, rmse_tol, rot_angle
 
 pytestmark = pytest.mark.gpu
 
@@ -91,3 +91,114 @@ def test_batch_with_initial_transforms_and_empty_pair():
     torch.cuda.synchronize()
     assert np.array_equal(T.cpu().numpy()[2], T2.cpu().numpy())
     h.close()
+
+
+def test_full_batch_workload_sampled_pairs_match_oracle(parity_report):
+    """The 256-pair batch workload as benchmarked (sizes log-uniform in
+    [2e3, 2e5], k = 10, 30 rounds, rejection 0.1) in one graph launch; on 8
+    of its pairs -- the smallest, the largest and six at the size quantiles
+    between -- (a) the oracle's ICP fed the batch's own normals must match the
+    batch transform at the ICP bars, and (b) the oracle's whole chain (its own
+    normals, then its ICP, kd-tree route) is compared as well: the normals
+    differ by their own parity bar, so the chain is held to the same ICP
+    bars and its error is reported."""
+    sizes = synth.batch_sizes(0, 256)
+    src, dst, T_gt = synth.surface_batch_torch(1000, sizes)
+    h = cil.Batch(sizes, sizes, k=10, iters=30, max_corr_dist=0.1, viewpoint=(0, 0, 10))
+    nrm = torch.empty_like(dst)
+    T, rep = h.run(src, dst, normals_out=nrm)
+    torch.cuda.synchronize()
+    reps = cil.decode_reports(rep, len(sizes))
+    T = T.cpu().numpy().reshape(-1, 4, 4)
+    order = np.argsort(sizes, kind="stable")
+    picks = sorted({int(order[int(round(q * (len(sizes) - 1)))]) for q in np.linspace(0, 1, 8)})
+    assert len(picks) == 8 and sizes[picks].min() == sizes.min() and sizes[picks].max() == sizes.max()
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    S, D, N = src.cpu().numpy(), dst.cpu().numpy(), nrm.cpu().numpy()
+    worst = {"rot_rad": 0.0, "trans_rel": 0.0, "chain_rot_rad": 0.0, "chain_trans_rel": 0.0}
+    for b in picks:
+        s0, s1 = int(off[b]), int(off[b + 1])
+        ps, pd = S[s0:s1], D[s0:s1]
+        ext = extent(pd)
+        o = oracle.icp(ps, pd, N[s0:s1], iters=30, max_corr_dist=0.1, method="kdtree")
+        ang = rot_angle(T[b][:3, :3], o["T"][:3, :3])
+        dt = np.abs(T[b][:3, 3] - o["T"][:3, 3]).max() / ext
+        assert ang <= 1e-5 and dt <= 1e-6, f"pair {b} (n={sizes[b]}): {ang:.3g} rad, {dt:.3g}"
+        assert abs(reps[b]["rmse"] - o["rmse"]) <= rmse_tol(pd, ang, dt * ext)
+        on, _, _ = oracle.normals(pd, 10, (0, 0, 10), method="kdtree")
+        oc = oracle.icp(ps, pd, on.astype(np.float32), iters=30, max_corr_dist=0.1,
+                        method="kdtree")
+        cang = rot_angle(T[b][:3, :3], oc["T"][:3, :3])
+        cdt = np.abs(T[b][:3, 3] - oc["T"][:3, 3]).max() / ext
+        assert cang <= 1e-5 and cdt <= 1e-6, f"chain, pair {b}: {cang:.3g} rad, {cdt:.3g}"
+        worst = {"rot_rad": max(worst["rot_rad"], ang), "trans_rel": max(worst["trans_rel"], dt),
+                 "chain_rot_rad": max(worst["chain_rot_rad"], cang),
+                 "chain_trans_rel": max(worst["chain_trans_rel"], cdt)}
+    parity_report(f"batch of 256 pairs, 8 sampled (n {sizes[picks].min()}..{sizes[picks].max()})",
+                  **worst)
+    h.close()
+
+
+def test_fallback_reregisters_failed_pairs_from_identity():
+    """cil_icp_batch_fallback after a warm-started run: pairs whose final RMSE
+    is >= 0.005 (or NaN) are re-registered from the identity and keep the
+    better result.  Warm starts here: the generator's label for even pairs,
+    the label moved 3 units along x for odd ones (no target point within the
+    rejection distance, so no inliers and a NaN RMSE: they fail).  Every
+    re-registered pair must then hold, bit for bit, what an identity-started
+    run of the same batch gives it (or its first result, when that was
+    better); the others are untouched."""
+    pairs, _, _ = synth.warm_start_pairs(4242, 24, n=6000)
+    sizes = [len(p.source) for p in pairs]
+    src = torch.from_numpy(np.concatenate([p.source for p in pairs])).cuda()
+    dst = torch.from_numpy(np.concatenate([p.target for p in pairs])).cuda()
+    T0 = np.stack([p.T_gt for p in pairs]).copy()
+    T0[1::2, 0, 3] += 3.0
+    T0d = torch.from_numpy(T0.reshape(-1, 16)).cuda()
+    kw = dict(k=10, iters=30, max_corr_dist=0.1, viewpoint=(0, 0, 10))
+    h_id = cil.Batch(sizes, sizes, **kw)
+    T_i, rep_i = h_id.run(src, dst)
+    h = cil.Batch(sizes, sizes, **kw)
+    T_l, rep_l = h.run(src, dst, T_init=T0d)
+    torch.cuda.synchronize()
+    T_first, rep_first = T_l.clone(), rep_l.clone()
+    used = h.fallback(src, dst, T_l, rep_l, rmse_threshold=0.005)
+    torch.cuda.synchronize()
+    used = used.cpu().numpy()
+    r_first = cil.decode_reports(rep_first, len(sizes))
+    r_id = cil.decode_reports(rep_i, len(sizes))
+    r_fin = cil.decode_reports(rep_l, len(sizes))
+    Tf, Ti, T1 = T_l.cpu().numpy(), T_i.cpu().numpy(), T_first.cpu().numpy()
+
+    def same(ra, rb):  # reports equal, NaN RMSEs included
+        return all((ra[k] == rb[k]) or (k == "rmse" and np.isnan(ra[k]) and np.isnan(rb[k]))
+                   for k in ra)
+
+    n_redo = 0
+    for b in range(len(sizes)):
+        bad = not (r_first[b]["rmse"] < 0.005)
+        assert (used[b] > 0) == bad, f"pair {b}"
+        if used[b] == 2:
+            assert np.array_equal(Tf[b], Ti[b]) and same(r_fin[b], r_id[b]), f"pair {b}"
+            assert r_id[b]["rmse"] < r_first[b]["rmse"] or np.isnan(r_first[b]["rmse"])
+        else:
+            assert np.array_equal(Tf[b], T1[b]) and same(r_fin[b], r_first[b]), f"pair {b}"
+            if used[b] == 1:
+                assert not (r_id[b]["rmse"] < r_first[b]["rmse"])
+        n_redo += int(used[b] > 0)
+    assert n_redo >= 12  # every shifted start fails
+    assert (used[1::2] > 0).all()
+    # the fallback is never worse than either start alone
+    fin = np.array([r["rmse"] for r in r_fin])
+    ok_fin = np.nan_to_num(fin, nan=1.0) < 0.005
+    ok_id = np.nan_to_num(np.array([r["rmse"] for r in r_id]), nan=1.0) < 0.005
+    ok_first = np.nan_to_num(np.array([r["rmse"] for r in r_first]), nan=1.0) < 0.005
+    assert np.all(ok_fin >= ok_id) and np.all(ok_fin >= ok_first)
+    # a second call on the already merged results re-registers the same
+    # still-failing pairs and changes nothing
+    T_keep = T_l.clone()
+    h.fallback(src, dst, T_l, rep_l, rmse_threshold=0.005)
+    torch.cuda.synchronize()
+    assert torch.equal(T_l, T_keep)
+    h.close()
+    h_id.close()

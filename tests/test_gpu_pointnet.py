@@ -105,10 +105,10 @@ def test_short_training_beats_identity_on_held_out_pairs():
     net = cil.PointNet(256, 4096, params=opn.flatten(opn.init_params(4)).astype(np.float32))
     learned.train(net, 400, B=128, lr=1e-3, seed=4)
     pairs, s_sub, d_sub = synth.warm_start_pairs(12345, 32, n=10_000)
-    res = learned.evaluate(net, pairs, s_sub, d_sub, iters=30, max_corr_dist=0.1)
+    res = learned.evaluate(net, pairs, s_sub, d_sub, iters=30, max_corr_dist=0.1, runs=2)
     assert res["warm_start_rot_err_deg_median"] < res["identity_rot_err_deg_median"]
-    assert res["success_learned_with_fallback"] >= res["success_identity"]
-    assert res["success_learned_with_fallback"] > res["success_identity"] or \
+    assert res["success_learned_fallback"] >= res["success_identity"]
+    assert res["success_learned_fallback"] > res["success_identity"] or \
         res["success_identity"] == 1.0
     net.close()
 
@@ -120,8 +120,9 @@ def test_committed_checkpoint_beats_identity_start():
     net = cil.PointNet(64, 4096)
     learned.load_checkpoint(net, learned.CHECKPOINT)
     pairs, s_sub, d_sub = synth.warm_start_pairs(4242, 64, n=10_000)
-    res = learned.evaluate(net, pairs, s_sub, d_sub, iters=30, max_corr_dist=0.1)
+    res = learned.evaluate(net, pairs, s_sub, d_sub, iters=30, max_corr_dist=0.1, runs=2)
     net.close()
     assert res["warm_start_rot_err_deg_median"] < 0.5 * res["identity_rot_err_deg_median"]
-    assert res["success_learned"] > res["success_identity"]
-    assert res["success_learned_with_fallback"] >= res["success_learned"]
+    assert res["success_learned_before_fallback"] > res["success_identity"]
+    assert res["success_learned_fallback"] >= res["success_learned_before_fallback"]
+    assert res["success_learned_fallback"] >= res["success_identity"]
