@@ -54,10 +54,19 @@ WORKLOAD = ("depth-frame pair 640x480 (pinhole 525/319.5/239.5, ground + 20 boxe
             "PCA normals of every target point + 30 point-to-plane ICP rounds (d_max 0.05 m) + "
             "final RMSE pass")
 
-# DRAM traffic per k_icp_search launch measured by ncu on this workload
-# (bytes), with the hash of the kernel sources it was measured on; reported
-# only while the sources are unchanged.
-ICP_TRAFFIC = {"bytes": 22089472, "src_sha": "bea1834c24c98794"}
+# DRAM traffic (read + write bytes) per launch measured by ncu, per kernel,
+# with the hash of the sources the kernel is built from; a figure is reported
+# only while those sources are unchanged.
+TRAFFIC = {
+    "k_icp_search": {"bytes": None, "src_sha": None},
+    "k_knn": {"bytes": None, "src_sha": None},
+    "k_radius": {"bytes": None, "src_sha": None},
+}
+KERNEL_SOURCES = {
+    "k_icp_search": ("icp.cu",),
+    "k_knn": ("knn.cu",),
+    "k_radius": ("radius.cu",),
+}
 
 
 def _peaks():
@@ -68,15 +77,23 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def _src_sha():
-    """Hash of the sources the dominant kernel (k_icp_search) is built from."""
+def src_sha(kernel: str) -> str:
+    """Hash of the sources `kernel` is built from (its .cu file and the shared
+    device headers)."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1807_00399_gb300", "csrc")
-    for f in ("cil_dev.cuh", "cil_host.h", "cil_kernels.h", "icp.cu"):
+    for f in ("cil_dev.cuh", "cil_host.h", "cil_kernels.h") + KERNEL_SOURCES[kernel]:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def traffic_of(kernel: str):
+    rec = TRAFFIC.get(kernel) or {}
+    if rec.get("bytes") and rec.get("src_sha") == src_sha(kernel):
+        return rec["bytes"]
+    return None
 
 
 class ClockSampler:
@@ -187,12 +204,13 @@ def _barrier(ws: int):
 # ---------------------------------------------------------------------------
 # oracle pipeline (reference arm and CPU baseline)
 # ---------------------------------------------------------------------------
-def oracle_step(pair, frac: float, rng_seed: int = 0, full_normals=None):
+def oracle_step(pair, frac: float, rng_seed: int = 0, full_normals=None, keep=None):
     """The oracle's pipeline on a sample: normals of frac * N_t target points
     (neighbourhoods searched in the full cloud) and 30-round ICP of frac * N_s
     source points against the full target.  With frac < 1 the ICP uses normals
     of every target point, computed once outside the timing (`full_normals`).
-    Returns (target queries, seconds, final rmse)."""
+    Returns (target queries, seconds, final rmse); with frac == 1 and a dict
+    `keep`, the oracle's normals, eigenvalues and ICP result are stored in it."""
     import oracle
     rng = np.random.default_rng(rng_seed)
     nt, ns = len(pair.target), len(pair.source)
@@ -207,14 +225,59 @@ def oracle_step(pair, frac: float, rng_seed: int = 0, full_normals=None):
         nrm = full_normals
         src = pair.source[sel_s]
     else:
-        on, _, _ = oracle.normals(pair.target, K_NN, pair.viewpoint, method="kdtree")
+        on, _, oev = oracle.normals(pair.target, K_NN, pair.viewpoint, method="kdtree")
         t_norm = time.perf_counter() - t0
         nrm = on.astype(np.float32)
         src = pair.source
     t1 = time.perf_counter()
     out = oracle.icp(src, pair.target, nrm, iters=ICP_ITERS, max_corr_dist=DMAX, method="kdtree")
     t_icp = time.perf_counter() - t1
+    if keep is not None and m_t == nt:
+        keep.update(normals=on, evals=oev, icp=out)
     return m_t, t_norm + t_icp, out["rmse"]
+
+
+def precision_vs_oracle(pair, T_gpu, rep_gpu, nrm_gpu, knn_gpu, keep, knn_rows: int = 2000,
+                        seed: int = 0):
+    """Error of the library's results on the bench frame pair against the FP64
+    oracle on the same inputs: the registration (the library's chain against
+    the oracle's chain: its normals, then its ICP), the normals (angle above
+    the eigen-gap gate (l1 - l0) / l2 >= 1e-2, and how many points fall below
+    it), and the 10-NN lists of a seeded sample of rows (indices that differ
+    outside FP32 distance ties, largest relative d2 error)."""
+    import oracle
+    T_o = keep["icp"]["T"]
+    M = T_gpu[:3, :3] @ T_o[:3, :3].T
+    w = np.array([M[2, 1] - M[1, 2], M[0, 2] - M[2, 0], M[1, 0] - M[0, 1]]) / 2
+    rot = float(np.arctan2(np.linalg.norm(w), (np.trace(M) - 1) / 2))
+    tgt = pair.target.astype(np.float64)
+    ext = float(np.linalg.norm(tgt.max(0) - tgt.min(0)))
+    trans = float(np.abs(T_gpu[:3, 3] - T_o[:3, 3]).max() / ext)
+    on, oev = keep["normals"], keep["evals"]
+    g = nrm_gpu.astype(np.float64)
+    ang = np.arctan2(np.linalg.norm(np.cross(g, on), axis=1), np.abs((g * on).sum(1)))
+    good = (oev[:, 1] - oev[:, 0]) >= 1e-2 * oev[:, 2]
+    rows = np.sort(np.random.default_rng(seed).choice(len(pair.target), knn_rows, replace=False))
+    oi, od = oracle.knn(pair.target, pair.target[rows], K_NN + 1)
+    gi, gd = knn_gpu[0][rows], knn_gpu[1][rows].astype(np.float64)
+    rel = lambda a, b: np.abs(a - b) <= 1e-6 * np.maximum(np.abs(b), 1e-30)  # noqa: E731
+    tie = np.zeros((knn_rows, K_NN), bool)
+    for c in range(K_NN):
+        for nb in (c - 1, c + 1):
+            if 0 <= nb <= K_NN:
+                tie[:, c] |= rel(od[:, nb], od[:, c])
+    mism = (gi != oi[:, :K_NN]) & ~tie
+    d2_err = np.abs(gd - od[:, :K_NN]) / np.maximum(od[:, :K_NN], 1e-30)
+    return {"icp_chain_rot_rad": rot, "icp_chain_trans_rel_extent": trans,
+            "rmse_rel": abs(rep_gpu["rmse"] - keep["icp"]["rmse"]) / keep["icp"]["rmse"],
+            "inliers_diff": int(rep_gpu["n_inliers"] - keep["icp"]["n_inliers"]),
+            "normals_points_gated": int(good.sum()),
+            "normals_max_rad": float(ang[good].max()),
+            "normals_p99_rad": float(np.percentile(ang[good], 99)),
+            "normals_below_gate": int((~good).sum()),
+            "knn_rows": knn_rows, "knn_index_mismatch_outside_ties": int(mism.sum()),
+            "knn_rows_with_ties": int(tie.any(1).sum()),
+            "knn_d2_max_rel_err": float(np.where(od[:, :K_NN] > 0, d2_err, 0).max())}
 
 
 def run_reference(args):
@@ -373,15 +436,13 @@ def run_ours(args):
     # the dominant kernel by the ncu launch list is k_icp_search (one launch
     # per ICP round; the ICP loop "k_icp" is 93 launches of three kernels)
     dom = "k_icp_search"
-    alg = {  # algorithmic bytes per launch (roofline section)
+    alg = {  # algorithmic bytes per launch: what the step must move, per kernel
         "k_icp_search": 20 * ns + 16 * nt,
         "k_normals": 40 * nt,
         "grid_build": 52 * nt + 16 * (1 << math.ceil(math.log2(2 * nt))),
         "order_queries": 52 * ns,
     }
-    traffic = None
-    if ICP_TRAFFIC["bytes"] and ICP_TRAFFIC["src_sha"] == _src_sha():
-        traffic = ICP_TRAFFIC["bytes"]
+    traffic = traffic_of(dom)
     achieved = alg[dom] / (per_launch_ms[dom] / 1e3) / 1e9
     roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
@@ -402,25 +463,34 @@ def run_ours(args):
     if not args.no_segmentation:
         segmentation = run_segmentation(args, rank)
     queries = None
+    query_rooflines = None
     if not args.no_queries:
-        queries = run_queries(args, rank)
+        queries, query_rooflines = run_queries(args, rank, peaks, peak_kind)
     paper_icp = None
     if not args.no_queries:
         paper_icp = run_paper_icp(args, rank)
 
-    # ---- CPU baseline (oracle, rank 0, N = 1 only) ----
+    # ---- CPU baseline (oracle, rank 0, N = 1 only) and the error of every
+    # result against it ----
     cpu = None
+    precision = None
     if ws == 1 and not args.no_cpu_baseline:
         import oracle
+        T_gpu = T.cpu().numpy().reshape(4, 4)
+        nrm_gpu = nrm.cpu().numpy()
+        gi, gd = cil.knn(dst, dst, K_NN)
+        knn_gpu = (gi.cpu().numpy(), gd.cpu().numpy())
+        keep = {}
         q_tot, t_tot = 0, 0.0
         while t_tot < 10.0:
-            q, t, _ = oracle_step(pair, 1.0)
+            q, t, _ = oracle_step(pair, 1.0, keep=keep)
             q_tot += q
             t_tot += t
         cpu = {"value": q_tot / t_tot, "unit": "queries/s", "cores": oracle.default_threads(),
                "kind": "oracle",
                "sample": f"full frame pair, oracle kd-tree route, {q_tot // nt} step(s), "
                          f"{t_tot:.1f} s"}
+        precision = precision_vs_oracle(pair, T_gpu, rep_h, nrm_gpu, knn_gpu, keep)
 
     if rank == 0:
         line = {
@@ -432,29 +502,50 @@ def run_ours(args):
                        "icp_iters": ICP_ITERS, "max_corr_dist": DMAX, "seed": args.seed,
                        "parallelism": f"replicas x{ws} (independent frame pairs)",
                        "l2": "flushed between timed steps (256 MiB write outside the events)"},
-            "pairs_per_s": ws * args.steps / (tot_max / 1e3),
-            "final_rmse": rep_h["rmse"], "final_inliers": rep_h["n_inliers"],
-            "icp_status": rep_h["status"],
             "e2e": {"value": e2e_value, "unit": "queries/s",
                     "h2d_bytes_per_step": int(src.numel() * 4 + dst.numel() * 4),
                     "d2h_bytes_per_step": int(T_h.numel() * 8 + rep_h_buf.numel())},
             "roofline": roofline,
-            "kernels_ms_per_launch": per_launch_ms,
             "cpu_baseline": cpu,
-            "batched": batched,
-            "learned": learned_res,
-            "icp_variants": variants,
-            "smooth_segmentation": segmentation,
-            "queries": queries,
-            "paper_icp_pipeline": paper_icp,
             "gpu_launches": int(n1 - n0),
             "clocks": clocks,
+            # full records of the other measurements
+            "kernels_ms_per_launch": per_launch_ms,
+            "queries": queries,
+            "icp_variants": variants,
+            "smooth_segmentation": segmentation,
+            "paper_icp_pipeline": paper_icp,
+            "batched_detail": batched,
+            "learned_detail": learned_res,
+            # compact summaries last
+            "pairs_per_s": ws * args.steps / (tot_max / 1e3),
+            "final_rmse": rep_h["rmse"], "final_inliers": rep_h["n_inliers"],
+            "icp_status": rep_h["status"],
+            "rooflines": query_rooflines,
+            "batched": _summary(batched, ("pairs", "pairs_per_s_batched", "pairs_per_s_plain",
+                                          "speedup", "max_abs_rmse_diff",
+                                          "T_bitwise_equal_batched_vs_plain",
+                                          "success_rate_rmse_lt_0.005", "tuned")),
+            "learned": _summary(learned_res, LEARNED_SUMMARY),
+            "precision": precision,
         }
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+LEARNED_SUMMARY = ("pairs", "pairs_per_s_learned_fallback", "pairs_per_s_identity",
+                   "success_learned_fallback", "success_identity",
+                   "median_rmse_success_learned_fallback", "median_rmse_success_identity",
+                   "pairs_reregistered", "runs")
+
+
+def _summary(rec, keys):
+    if rec is None:
+        return None
+    return {k: (round(rec[k], 6) if isinstance(rec[k], float) else rec[k]) for k in keys if k in rec}
 
 
 def run_batched(args, rank: int, B: int = 256, runs: int = 5):
@@ -479,7 +570,7 @@ def run_batched(args, rank: int, B: int = 256, runs: int = 5):
                                 max_corr_dist=0.1, reps=1)
     h = cil.Batch(sizes, sizes, k=K_NN, iters=ICP_ITERS, max_corr_dist=0.1,
                   viewpoint=(0.0, 0.0, 10.0), cell_scale=tuned["cell_scale"],
-                  block=tuned["block"])
+                  block=tuned["block"], topk=tuned.get("topk", 0))
     RS = ctypes.sizeof(cil.IcpReport)
     T = torch.empty((B, 16), dtype=torch.float64, device="cuda")
     rep = torch.empty((B, RS), dtype=torch.uint8, device="cuda")
@@ -525,9 +616,10 @@ def run_batched(args, rank: int, B: int = 256, runs: int = 5):
     rot_err = np.degrees(np.arccos(np.clip((np.trace(M, axis1=1, axis2=2) - 1) / 2, -1, 1)))
     return {"pairs": B, "points_per_side": int(sizes.sum()),
             "autotune": {"cell_scale": tuned["cell_scale"], "block": tuned["block"],
+                         "topk": tuned.get("topk"), "scale_interior": tuned.get("scale_interior"),
                          "cached": tuned["cached"],
-                         "table_ms": {f'{r["cell_scale"]}/{r["block"]}': round(r["ms"], 3)
-                                      for r in tuned.get("table", [])}},
+                         "table_ms": {f'{r["cell_scale"]:g}/{r["block"]}/{r["topk"]}':
+                                      round(r["ms"], 3) for r in tuned.get("table", [])}},
             "ms_batched_graph": ms_b, "pairs_per_s_batched": B / (ms_b / 1e3),
             "ms_sequential_plain": ms_s, "pairs_per_s_plain": B / (ms_s / 1e3),
             "speedup": ms_s / ms_b,
@@ -535,7 +627,9 @@ def run_batched(args, rank: int, B: int = 256, runs: int = 5):
             "T_bitwise_equal_batched_vs_plain": same_T,
             "median_rmse": float(np.nanmedian(rb)),
             "success_rate_rmse_lt_0.005": float(np.mean(np.nan_to_num(rb, nan=1.0) < 0.005)),
-            "median_rot_err_deg_vs_generator": float(np.median(rot_err))}
+            "median_rot_err_deg_vs_generator": float(np.median(rot_err)),
+            "tuned": f'scale {tuned["cell_scale"]:g}, block {tuned["block"]}, '
+                     f'topk {tuned.get("topk", 0)}, interior {tuned.get("scale_interior")}'}
 
 
 def run_variants(args, rank: int, reps: int = 5):
@@ -581,11 +675,15 @@ def run_variants(args, rank: int, reps: int = 5):
     return out
 
 
-def run_queries(args, rank: int, reps: int = 10):
+def run_queries(args, rank: int, peaks=None, peak_kind="fallback", reps: int = 10):
     """Standalone self-queries of the whole cloud on each workload (Sec. 3
     k-NN, radius and normal queries): median ms per call through the C ABI
     (grid build + query, end to end) and the query kernel's own time from the
-    library's CUDA events (grid prebuilt), as queries/s."""
+    library's CUDA events (grid prebuilt), as queries/s.  Also returns the
+    HBM roofline of the k-NN kernel (depth frame, k = 10: 12 B query + 12 B
+    reference + 8 k B output per query) and of the radius search (LiDAR
+    sweep, r = 0.5 m: per call 12 + 12 B read and 8 B offsets per query and
+    8 B per neighbour written)."""
     import ctypes
 
     import torch
@@ -595,6 +693,7 @@ def run_queries(args, rank: int, reps: int = 10):
 
     L = cil.lib()
     cases = []
+    rooflines = {}
     surf = synth.surface_pair(args.seed + rank, n=10_000).target
     depth = synth.depth_frame_pair(args.seed + rank).target
     lidar = synth.lidar_sweep_pair(args.seed + rank).target
@@ -621,6 +720,7 @@ def run_queries(args, rank: int, reps: int = 10):
         else:
             # the capacity from one sizing call, so each timed call is one pass
             cap = int(cil.radius_search(x, x, k)[1].numel())
+            nnz = cap
             fn = lambda x=x, k=k, cap=cap: cil.radius_search(x, x, k, capacity=cap)  # noqa: E731
         fn()
         torch.cuda.synchronize()
@@ -646,7 +746,20 @@ def run_queries(args, rank: int, reps: int = 10):
         cases.append({"case": name, "n": len(pts), "ms_end_to_end": e2e, "ms_grid_build": g_ms,
                       "ms_query_kernel": q_ms, "queries_per_s_end_to_end": len(pts) / e2e * 1e3,
                       "queries_per_s_query_only": len(pts) / q_ms * 1e3})
-    return cases
+        n = len(pts)
+        alg = None
+        if name == "depth frame, knn k=10":
+            alg, rk = (24 + 8 * k) * n, "k_knn"
+        elif op == "radius":
+            alg, rk = 32 * n + 8 * nnz, "k_radius"
+        if alg is not None and peaks is not None:
+            ach = alg / (q_ms / 1e3) / 1e9
+            rooflines[rk] = {"case": name, "bound": "hbm", "achieved": round(ach, 2),
+                             "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                             "frac": round(ach / peaks["hbm_gbs"], 5), "traffic": traffic_of(rk),
+                             "algorithmic_bytes_per_call": int(alg),
+                             "ms_per_call": round(q_ms, 5), "peak_kind": peak_kind}
+    return cases, rooflines
 
 
 def run_paper_icp(args, rank: int, reps: int = 10):

@@ -29,11 +29,23 @@ def test_clock_rows_empty():
     assert c == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
 
 
-def test_traffic_record_keyed_to_the_search_kernel_sources():
-    # the key is a hash of the files the kernel is built from: stable across calls
-    assert bench._src_sha() == bench._src_sha()
-    assert len(bench._src_sha()) == 16
-    assert set(bench.ICP_TRAFFIC) == {"bytes", "src_sha"}
+def test_traffic_records_keyed_to_each_kernels_sources(monkeypatch):
+    # the key is a hash of the files the kernel is built from: stable across
+    # calls, different per kernel; a record is reported only while it matches
+    for k in bench.TRAFFIC:
+        assert bench.src_sha(k) == bench.src_sha(k) and len(bench.src_sha(k)) == 16
+        assert set(bench.TRAFFIC[k]) == {"bytes", "src_sha"}
+    assert len({bench.src_sha(k) for k in bench.TRAFFIC}) == len(bench.TRAFFIC)
+    monkeypatch.setitem(bench.TRAFFIC, "k_knn", {"bytes": 123, "src_sha": bench.src_sha("k_knn")})
+    assert bench.traffic_of("k_knn") == 123
+    monkeypatch.setitem(bench.TRAFFIC, "k_knn", {"bytes": 123, "src_sha": "0" * 16})
+    assert bench.traffic_of("k_knn") is None
+
+
+def test_summary_keeps_listed_keys_in_order():
+    rec = {"a": 1.23456789, "b": 2, "c": "x"}
+    assert bench._summary(rec, ("c", "a", "missing")) == {"c": "x", "a": 1.234568}
+    assert bench._summary(None, ("a",)) is None
 
 
 def test_clock_rejection_rule():
