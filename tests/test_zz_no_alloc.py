@@ -65,3 +65,44 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     assert st == CAPACITY
     st, _, _ = _noalloc(small, big, 4)
     assert st == CAPACITY
+
+
+def test_noalloc_largest_case_and_empty_reference():
+    # the case that reserves the most scratch: both sets at the limit, k at
+    # its maximum, queries distinct from the reference points
+    ref = torch.from_numpy(synth.surface_pair(24, n=MAX_POINTS).target).cuda()
+    qry = torch.from_numpy(synth.surface_pair(25, n=MAX_POINTS).source).cuda()
+    for _ in range(2):
+        st, idx, d2 = _noalloc(ref, qry, 32)
+        assert st == 0, cil.STATUS.get(st, st)
+        ref_idx, ref_d2 = cil.knn(ref, qry, 32)
+        torch.cuda.synchronize()
+        assert torch.equal(idx, ref_idx)
+        np.testing.assert_allclose(d2.cpu().numpy(), ref_d2.cpu().numpy(), rtol=1e-6, atol=0)
+    # no reference points: every row is padding (-1, +inf), as cil_knn gives
+    empty = torch.zeros((0, 3), dtype=torch.float32, device="cuda")
+    st, idx, d2 = _noalloc(empty, qry[:100], 5)
+    assert st == 0
+    ref_idx, ref_d2 = cil.knn(empty, qry[:100], 5)
+    torch.cuda.synchronize()
+    assert torch.equal(idx, ref_idx) and torch.equal(d2, ref_d2)
+    assert bool((idx == -1).all()) and bool(torch.isinf(d2).all())
+
+
+def test_noalloc_takes_no_workspace_allocation():
+    """An armed allocation failure stays pending across the call: it takes
+    no memory from the library's pool (the next allocating call fails)."""
+    L = cil.lib()
+    ref = torch.from_numpy(synth.surface_pair(26, n=4_000).target).cuda()
+    try:
+        L.cil_test_fail_next_allocations(1)
+        st, idx, _ = _noalloc(ref, ref, 8)
+        assert st == 0
+        with pytest.raises(cil.CilError) as e:
+            cil.knn(ref, ref, 8)
+        assert e.value.status == 7  # CIL_ERR_NOMEM: the armed failure was still pending
+    finally:
+        L.cil_test_fail_next_allocations(0)
+    ref_idx, _ = cil.knn(ref, ref, 8)
+    torch.cuda.synchronize()
+    assert torch.equal(idx, ref_idx)
