@@ -68,10 +68,15 @@ typedef enum {
  *               distance of sampled points to their k-th neighbour; 0 = 1.5).
  *   block       threads per block of the query kernels (0 = default 128;
  *               64, 128, 256 accepted).
- *   topk        how the k-NN and normals kernels hold each query's k best:
- *               0 = by k (sorted register list for k < 8, a binary max-heap
- *               per thread in shared memory from k = 8 on), 1 = register
- *               list, 2 = shared-memory heap (k = 1 always uses the list). */
+ *   topk        how the k-NN and normals kernels search: 0 = the default;
+ *               1 = one thread per query, its k best in a sorted register
+ *               list; 2 = one thread per query, a binary max-heap in shared
+ *               memory (k = 1 always uses the list; the default picks the list
+ *               for k < 8, the heap from 8 on); 3 = warp-staged: the 32
+ *               Morton-adjacent queries of a warp scan one shared set of
+ *               points (their cells and one ring around them, staged in
+ *               shared memory), a query whose k-th distance is not proven
+ *               inside that set continuing with the per-query search. */
 typedef struct {
   float cell_size;
   float cell_scale;
@@ -142,6 +147,14 @@ cil_status cil_knn_noalloc(const float *ref, int64_t n_ref, const float *qry, in
 cil_status cil_radius_search(const float *ref, int64_t n_ref, const float *qry, int64_t n_qry,
                              float r, int64_t *out_offsets, int32_t *out_idx, float *out_d2,
                              int64_t capacity, int64_t *out_nnz, void *stream);
+/* The same with tuning knobs (NULL = defaults): the search cells' edge is r,
+ * or params->cell_size when > 0, or r * params->cell_scale when > 0 (rounded
+ * to a power-of-two multiple of the fine lattice); block and topk unused.
+ * Results do not depend on them. */
+cil_status cil_radius_search_ex(const float *ref, int64_t n_ref, const float *qry, int64_t n_qry,
+                                float r, int64_t *out_offsets, int32_t *out_idx, float *out_d2,
+                                int64_t capacity, int64_t *out_nnz, const cil_params *params,
+                                void *stream);
 
 /* ---------------------------------------------------------------------------
  * Hybrid query (Sec. 3, KDTree "hybrid" queries): for every query the k

@@ -43,7 +43,8 @@ class CilError(RuntimeError):
 
 class Params(ctypes.Structure):
     """cil_params: cell_size (0 = from data), cell_scale (0 = 1.5), block,
-    topk (0 = by k, 1 = register list, 2 = shared-memory heap)."""
+    topk (0 = default, 1 = register list, 2 = shared-memory heap, 3 =
+    warp-staged)."""
     _fields_ = [("cell_size", ctypes.c_float), ("cell_scale", ctypes.c_float),
                 ("block", ctypes.c_int), ("topk", ctypes.c_int)]
 
@@ -74,6 +75,7 @@ def lib():
         L.cil_knn.argtypes = [P, I64, P, I64, I, P, P, P]
         L.cil_knn_ex.argtypes = [P, I64, P, I64, I, P, P, P, P]
         L.cil_radius_search.argtypes = [P, I64, P, I64, F, P, P, P, I64, P, P]
+        L.cil_radius_search_ex.argtypes = [P, I64, P, I64, F, P, P, P, I64, P, P, P]
         L.cil_estimate_normals.argtypes = [P, I64, I, P, P, P, P]
         L.cil_estimate_normals_ex.argtypes = [P, I64, I, P, P, P, P, P]
         L.cil_icp_point_to_plane.argtypes = [P, I64, P, P, I64, P, I, F, P, P, P]
@@ -232,10 +234,12 @@ def voxel_downsample(xyz, voxel: float, stream=None):
     return out[:m.value], cnt[:m.value]
 
 
-def radius_search(ref, qry, r: float, capacity: int | None = None, stream=None):
-    """All neighbours within r (cil_radius_search): CSR (offsets int64, idx
+def radius_search(ref, qry, r: float, capacity: int | None = None, *, cell_size=0.0,
+                  cell_scale=0.0, stream=None):
+    """All neighbours within r (cil_radius_search_ex): CSR (offsets int64, idx
     int32, d2 float32).  With capacity=None the call is made twice if needed:
-    first to learn the size, then to fill."""
+    first to learn the size, then to fill.  cell_size / cell_scale: the
+    search cells' edge (default r; results do not depend on it)."""
     torch = _torch()
     ref = _points(ref, "ref")
     qry = ref if qry is ref else _points(qry, "qry")
@@ -246,14 +250,17 @@ def radius_search(ref, qry, r: float, capacity: int | None = None, stream=None):
     d2 = torch.empty(max(cap, 1), dtype=torch.float32, device=qry.device)
     nnz = ctypes.c_int64(0)
     L = lib()
-    st = L.cil_radius_search(_ptr(ref), ref.shape[0], _ptr(qry), nq, float(r), _ptr(off), _ptr(idx),
-                             _ptr(d2), cap, ctypes.byref(nnz), _stream(stream))
+    prm = _params(cell_size, cell_scale)
+    pp = ctypes.byref(prm) if prm is not None else None
+    st = L.cil_radius_search_ex(_ptr(ref), ref.shape[0], _ptr(qry), nq, float(r), _ptr(off),
+                                _ptr(idx), _ptr(d2), cap, ctypes.byref(nnz), pp, _stream(stream))
     if st == 4 and capacity is None:
         cap = int(nnz.value)
         idx = torch.empty(max(cap, 1), dtype=torch.int32, device=qry.device)
         d2 = torch.empty(max(cap, 1), dtype=torch.float32, device=qry.device)
-        st = L.cil_radius_search(_ptr(ref), ref.shape[0], _ptr(qry), nq, float(r), _ptr(off),
-                                 _ptr(idx), _ptr(d2), cap, ctypes.byref(nnz), _stream(stream))
+        st = L.cil_radius_search_ex(_ptr(ref), ref.shape[0], _ptr(qry), nq, float(r), _ptr(off),
+                                    _ptr(idx), _ptr(d2), cap, ctypes.byref(nnz), pp,
+                                    _stream(stream))
     _check(st, "cil_radius_search")
     n = int(nnz.value)
     return off, idx[:n], d2[:n]

@@ -7,8 +7,10 @@ bitwise equal across every configuration tried):
               the nearest power-of-two multiple of its fine lattice to scale x
               the median k-th neighbour distance of sampled points);
   block       threads per block of the normals kernel (64, 128, 256);
-  topk        how each query keeps its k best keys: 1 = sorted register list,
-              2 = binary max-heap in shared memory (0 = by k).
+  topk        how the k-NN search runs: 1 = per query, k best in a sorted
+              register list; 2 = per query, binary max-heap in shared memory;
+              3 = warp-staged (32 queries scan one shared set of points);
+              0 = the library's default.
 The search is coordinate descent on whole timed batch runs (CUDA events):
 the cell scale over SCALES at the default block and layout, extended by
 factors of 1.5 past either end while the best scale sits on that end (so the
@@ -28,7 +30,7 @@ import numpy as np
 
 SCALES = (0.5, 0.75, 1.0, 1.5, 2.0, 3.0, 4.0)
 BLOCKS = (64, 128, 256)
-TOPK = (1, 2)
+TOPK = (1, 2, 3)
 SCALE_LIMITS = (0.125, 16.0)  # the range extension stops here
 
 

@@ -56,7 +56,7 @@ static cil_status enqueue_batch(BatchHandle* h, const float* src, const float* d
   if (st != CIL_OK) return st;
   const GridView g = grid_view(h->gp, h->ws);
   const int block = h->prm.tune.block ? h->prm.tune.block : 128;
-  const int topk = h->prm.tune.topk >= 0 && h->prm.tune.topk <= 2 ? h->prm.tune.topk : 0;
+  const int topk = h->prm.tune.topk >= 0 && h->prm.tune.topk <= 3 ? h->prm.tune.topk : 0;
   if ((st = launch_normals(g, h->B, h->tot_dst, h->prm.k, nullptr, h->prm.viewpoint, dst, nrm,
                            nullptr, block, s, nullptr, topk)) != CIL_OK)
     return st;

@@ -146,7 +146,7 @@ static GridOptions grid_options(const cil_params* prm, int k) {
 
 static int block_of(const cil_params* prm) { return prm && prm->block ? prm->block : 128; }
 static int topk_of(const cil_params* prm) {
-  return prm && prm->topk >= 0 && prm->topk <= 2 ? prm->topk : 0;
+  return prm && prm->topk >= 0 && prm->topk <= 3 ? prm->topk : 0;
 }
 
 }  // namespace cil

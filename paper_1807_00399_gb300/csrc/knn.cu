@@ -315,6 +315,214 @@ __global__ void __launch_bounds__(256) k_normals(GridView g, int cloud_count, in
 }
 
 // ---------------------------------------------------------------------------
+// warp-staged search: the 32 queries of a warp (consecutive in the grid's
+// Morton order, so neighbours in space) share one staged set of points -- the
+// cells of the box spanned by their own cells plus one ring, looked up once by
+// the lanes and copied to shared memory -- and every lane scans every staged
+// point (one broadcast read per point for the whole warp, no divergence in
+// the distance work, no per-query hash lookups).  A lane's result is kept
+// when its k-th distance is proven: every point outside the box is farther
+// (the padded distance to the grid outside the box); otherwise, or when the
+// box is too large to stage, the lane runs the per-query ring search.  The
+// kept keys are the same (d2, index) set either way, so results are bitwise
+// those of the per-query search.
+// ---------------------------------------------------------------------------
+constexpr int kStageWarps = 4;    // warps (32 queries each) per block
+constexpr int kStagePts = 512;    // staged points per warp at most
+constexpr int kStageCells = 128;  // cells of a warp's box at most
+
+struct StageSmem {
+  float4 pts[kStagePts];
+  int start[32], pre[33];
+};
+
+template <int KMAX, class Top>
+__device__ __forceinline__ bool staged_knn(const GridView& g, int cloud, bool warp_ok,
+                                           const float q[3], bool active, Top& top, StageSmem& S,
+                                           int lane) {
+  const unsigned full = 0xffffffffu;
+  if (!warp_ok) return false;
+  const GridParams& P = g.prm[cloud];
+  CellFrame f;
+  f.load(P, cloud);
+  int lo[3], hi[3], qlo[3], qhi[3];  // the box; the queries' own cells
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int c = f.cell_of(q[a], a, P.inv_fine);
+    qlo[a] = (int)__reduce_min_sync(full, active ? c : 0x7fffffff);
+    qhi[a] = (int)__reduce_max_sync(full, active ? c : -1);
+    lo[a] = max(qlo[a] - 1, 0);
+    hi[a] = min(qhi[a] + 1, f.hi[a]);
+  }
+  const int nx = hi[0] - lo[0] + 1, nxy = nx * (hi[1] - lo[1] + 1);
+  const int ncell = nxy * (hi[2] - lo[2] + 1);
+  if (ncell > kStageCells) return false;
+  const float inv_nx = 1.0f / (float)nx, inv_nxy = 1.0f / (float)nxy;
+  int total = 0;
+  // the queries' own cells are staged first, the ring around them last, so
+  // every lane meets its nearest points early and later pushes are rare
+  for (int pass = 0, c0 = 0; pass < 2; c0 += 32) {
+    if (c0 >= ncell) {
+      ++pass;
+      c0 = -32;
+      continue;
+    }
+    const int c = c0 + lane;
+    int s = 0, n = 0;
+    if (c < ncell) {
+      // c = (z * ny + y) * nx + x (float quotients: exact for c < 2^22)
+      const int z = __float2int_rz(((float)c + 0.5f) * inv_nxy), rem = c - z * nxy;
+      const int y = __float2int_rz(((float)rem + 0.5f) * inv_nx), x = rem - y * nx;
+      const int X = lo[0] + x, Y = lo[1] + y, Z = lo[2] + z;
+      const bool own = X >= qlo[0] && X <= qhi[0] && Y >= qlo[1] && Y <= qhi[1] && Z >= qlo[2] &&
+                       Z <= qhi[2];
+      if (own == (pass == 0) && !cell_lookup(g, cell_key(f.level, cloud, X, Y, Z), s, n)) n = 0;
+    }
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(full, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int chunk = __shfl_sync(full, incl, 31);
+    if (total + chunk > kStagePts) return false;
+    __syncwarp();
+    S.start[lane] = s;
+    S.pre[lane] = incl - n;
+    if (lane == 31) S.pre[32] = chunk;
+    __syncwarp();
+    int ci = 0, cs = S.start[0], cp = 0, cn = S.pre[1];
+    for (int t = lane; t < chunk; t += 32) {
+      while (t >= cn) {
+        ++ci;
+        cp = cn;
+        cs = S.start[ci];
+        cn = S.pre[ci + 1];
+      }
+      S.pts[total + t] = __ldg(g.pts + cs + (t - cp));
+    }
+    total += chunk;
+  }
+  __syncwarp();
+  top.init(top.k);
+  if (active) {
+    for (int j = 0; j < total; ++j) {
+      const float4 p = S.pts[j];
+      top.push(pack_key(sqdist(p.x, p.y, p.z, q[0], q[1], q[2]), __float_as_int(p.w)));
+    }
+  }
+  __syncwarp();  // S is reused by the next call
+  const float bound = f.unexplored_d2(q, lo, hi);
+  if (top.full()) return top.thr_d2() < bound * (1.0f - 1e-6f);
+  return !(bound < __int_as_float(0x7f800000));  // the whole cloud was staged
+}
+
+template <int KMAX, bool HEAP>
+__global__ void __launch_bounds__(kStageWarps * 32) k_knn_staged(GridView g,
+                                                                 const float* __restrict__ qry,
+                                                                 int64_t nq,
+                                                                 const int* __restrict__ order,
+                                                                 int k, int* __restrict__ out_idx,
+                                                                 float* __restrict__ out_d2) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  StageSmem& S = reinterpret_cast<StageSmem*>(smem_raw)[w];
+  u64* s_topk = reinterpret_cast<u64*>(smem_raw + sizeof(StageSmem) * kStageWarps);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + 32 * w;
+  if (i0 >= nq) return;  // whole warp
+  const bool active = i < nq;
+  const int64_t ii = active ? i : i0;
+  int64_t qi;
+  float q[3];
+  if (order) {
+    qi = order[ii];
+    q[0] = qry[3 * qi];
+    q[1] = qry[3 * qi + 1];
+    q[2] = qry[3 * qi + 2];
+  } else {
+    const float4 p = g.pts[ii];
+    qi = __float_as_int(p.w);
+    q[0] = p.x;
+    q[1] = p.y;
+    q[2] = p.z;
+  }
+  TopKSel<KMAX, HEAP> top;
+  top.bind(s_topk + threadIdx.x, blockDim.x);
+  top.init(k);
+  const bool ok = staged_knn<KMAX>(g, 0, true, q, active, top, S, lane);
+  if (!active) return;
+  if (!ok) grid_knn<KMAX>(g, 0, q, top);
+  top.finish();
+  int* oi = out_idx + qi * k;
+  float* od = out_d2 ? out_d2 + qi * k : nullptr;
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    if (j < k) {
+      const u64 key = top.key_at(j);
+      const bool none = key == kEmptyKey;
+      oi[j] = none ? -1 : key_idx(key);
+      if (od) od[j] = none ? __int_as_float(0x7f800000) : key_d2(key);
+    }
+  }
+}
+
+template <int KMAX, bool HEAP>
+__global__ void __launch_bounds__(kStageWarps * 32) k_normals_staged(
+    GridView g, int cloud_count, int64_t n, int k, const float* __restrict__ vp_all, float vx,
+    float vy, float vz, const float* __restrict__ xyz, float* __restrict__ out_n,
+    float* __restrict__ out_c, int* __restrict__ out_idx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  StageSmem& S = reinterpret_cast<StageSmem*>(smem_raw)[w];
+  u64* s_topk = reinterpret_cast<u64*>(smem_raw + sizeof(StageSmem) * kStageWarps);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + 32 * w;
+  if (i0 >= n) return;  // whole warp
+  const bool active = i < n;
+  const float4 p = g.pts[active ? i : i0];
+  // the sorted array is grouped by cloud; find this point's cloud
+  int cloud = 0;
+  if (cloud_count > 1) {
+    int lo = 0, hi = cloud_count;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if ((int64_t)g.prm[mid].start <= (active ? i : i0)) lo = mid;
+      else hi = mid;
+    }
+    cloud = lo;
+  }
+  const bool same = __all_sync(0xffffffffu, cloud == __shfl_sync(0xffffffffu, cloud, 0));
+  const int start = g.prm[cloud].start;
+  const int64_t local = __float_as_int(p.w);
+  const float q[3] = {p.x, p.y, p.z};
+  TopKSel<KMAX, HEAP> top;
+  top.bind(s_topk + threadIdx.x, blockDim.x);
+  top.init(k);
+  const bool ok = staged_knn<KMAX>(g, cloud, same, q, active, top, S, lane);
+  if (!active) return;
+  if (!ok) grid_knn<KMAX>(g, cloud, q, top);
+  top.finish();
+  const float vp[3] = {vp_all ? vp_all[3 * cloud] : vx, vp_all ? vp_all[3 * cloud + 1] : vy,
+                       vp_all ? vp_all[3 * cloud + 2] : vz};
+  float nv[3], c;
+  normal_from_topk<KMAX>(top, k, xyz + 3 * (int64_t)start, q, vp, nv, c);
+  const int64_t gi = start + local;
+  out_n[3 * gi] = nv[0];
+  out_n[3 * gi + 1] = nv[1];
+  out_n[3 * gi + 2] = nv[2];
+  if (out_c) out_c[gi] = c;
+  if (out_idx) {
+    int* oi = out_idx + gi * k;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+      const u64 key = top.key_at(j);
+      if (j < k) oi[j] = key == kEmptyKey ? -1 : key_idx(key);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // hybrid query (k nearest within r) and radius-neighbourhood normals
 // (Sec. 3 hybrid queries and radius normals; Sec. 4 uses 1 cm balls)
 // ---------------------------------------------------------------------------
@@ -460,9 +668,30 @@ static void knn_launch_as(const GridView& g, const float* qry, int64_t nq, const
 
 // layout: 0 = by k, 1 = register list, 2 = shared-memory heap (k = 1 always
 // takes the register list)
+template <int KM, bool HEAP>
+static int staged_smem() {
+  return (int)sizeof(StageSmem) * kStageWarps + (HEAP ? KM * (int)sizeof(u64) * kStageWarps * 32 : 0);
+}
+
+template <int KM, bool HEAP>
+static void knn_staged_as(const GridView& g, const float* qry, int64_t nq, const int* order, int k,
+                          int* out_idx, float* out_d2, cudaStream_t s) {
+  const int smem = staged_smem<KM, HEAP>();
+  cudaFuncSetAttribute(k_knn_staged<KM, HEAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_knn_staged<KM, HEAP><<<ceil_div(nq, kStageWarps * 32), kStageWarps * 32, smem, s>>>(
+      g, qry, nq, order, k, out_idx, out_d2);
+}
+
 template <int KM>
 static void knn_launch(const GridView& g, const float* qry, int64_t nq, const int* order, int k,
                        int* out_idx, float* out_d2, int block, int layout, cudaStream_t s) {
+  if (layout == 3) {
+    if (KM > 1 && topk_heap(KM, 0))
+      knn_staged_as<KM, (KM > 1)>(g, qry, nq, order, k, out_idx, out_d2, s);
+    else
+      knn_staged_as<KM, false>(g, qry, nq, order, k, out_idx, out_d2, s);
+    return;
+  }
   if (KM > 1 && topk_heap(KM, layout))
     knn_launch_as<KM, (KM > 1)>(g, qry, nq, order, k, out_idx, out_d2, block, s);
   else
@@ -479,10 +708,30 @@ static void normals_launch_as(const GridView& g, int clouds, int64_t n, int k, c
                                                       out_n, out_c, out_idx);
 }
 
+template <int KM, bool HEAP>
+static void normals_staged_as(const GridView& g, int clouds, int64_t n, int k, const float* vp_dev,
+                              float vx, float vy, float vz, const float* xyz, float* out_n,
+                              float* out_c, int* out_idx, cudaStream_t s) {
+  const int smem = staged_smem<KM, HEAP>();
+  cudaFuncSetAttribute(k_normals_staged<KM, HEAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       smem);
+  k_normals_staged<KM, HEAP><<<ceil_div(n, kStageWarps * 32), kStageWarps * 32, smem, s>>>(
+      g, clouds, n, k, vp_dev, vx, vy, vz, xyz, out_n, out_c, out_idx);
+}
+
 template <int KM>
 static void normals_launch(const GridView& g, int clouds, int64_t n, int k, const float* vp_dev,
                            float vx, float vy, float vz, const float* xyz, float* out_n,
                            float* out_c, int* out_idx, int block, int layout, cudaStream_t s) {
+  if (layout == 3) {
+    if (KM > 1 && topk_heap(KM, 0))
+      normals_staged_as<KM, (KM > 1)>(g, clouds, n, k, vp_dev, vx, vy, vz, xyz, out_n, out_c,
+                                      out_idx, s);
+    else
+      normals_staged_as<KM, false>(g, clouds, n, k, vp_dev, vx, vy, vz, xyz, out_n, out_c, out_idx,
+                                   s);
+    return;
+  }
   if (KM > 1 && topk_heap(KM, layout))
     normals_launch_as<KM, (KM > 1)>(g, clouds, n, k, vp_dev, vx, vy, vz, xyz, out_n, out_c,
                                     out_idx, block, s);

@@ -7,18 +7,19 @@
 //   count  the lanes look up the ball's cells in parallel, the cells' points
 //          are concatenated and split over the lanes, and accepted points
 //          (d2 <= r*r, inclusive) are counted with a ballot;
-//   scan   int64 CSR offsets (rows longer than kRowCapW also counted);
-//   fill   the same walk; accepted (d2, index) keys are appended to the
-//          warp's shared-memory row in visiting order, then sorted there by
-//          (d2, index) with a bucket sort: buckets of d2 * NB / r^2 (a
-//          monotone map, so bucket order agrees with key order), a histogram
-//          and scan, a scatter of key positions into bucket order, and each
-//          key's rank = its bucket's start + the keys of its bucket below it.
-//          The sorted row is written to its CSR place.  A row longer than
-//          kRowCapW keys is written unsorted and listed;
-//   sort   listed rows, one block each, with an all-ascending bitonic network
-//          (in shared memory up to kRowCap keys, else in place in global
-//          memory; virtual +inf padding past the row end never moves).
+//   scan   int64 CSR offsets (rows longer than kRowCapW are listed);
+//   fill   the same walk; accepted (index, d2) appended to the query's CSR
+//          row in visiting order (ballot positions: coalesced stores); no
+//          shared memory, so it runs at the count pass's occupancy;
+//   sort   rows up to kRowCapW keys: one warp per row, a bucket sort in
+//          shared memory by (d2, index) -- buckets of d2 * NB / r^2 (a
+//          monotone map, so bucket order agrees with key order), histogram
+//          and scan, the keys scattered into bucket order, each bucket
+//          insertion-sorted by its lane, the row written back coalesced;
+//          longer rows (listed by the count pass): one block each, an
+//          all-ascending bitonic network (in shared memory up to kRowCap
+//          keys, else in place in global memory; virtual +inf padding past
+//          the row end never moves).
 #include <math.h>
 
 #include "cil_host.h"
@@ -31,13 +32,14 @@ constexpr int kSortThreads = 256;
 constexpr int kRowCapW = 1024;     // warp sort: rows up to this many keys in shared memory
 constexpr int kBucketsMax = 512;   // buckets of the warp sort (a power of two)
 constexpr int kCountWarps = 8;     // warps (queries) per block of the count pass
-constexpr int kFillWarps = 4;      // warps (queries) per block of the fill pass
+constexpr int kSortWarps = 4;      // warps (rows) per block of the warp sort
 
 // Cells of the query's ball: the range [lo, hi] of cells meeting the cube of
 // half-edge r + eps around q, walked 32 at a time (lane c takes cell c of the
 // chunk), each looked up if its box meets the ball.
 struct BallCells {
   int lo[3], nx, nxy, ncell;
+  float inv_nx, inv_nxy;
   __device__ __forceinline__ void init(const CellFrame& f, const GridParams& P, const float q[3],
                                        float r) {
     int hi[3];
@@ -49,6 +51,8 @@ struct BallCells {
     nx = hi[0] - lo[0] + 1;
     nxy = nx * (hi[1] - lo[1] + 1);
     ncell = nxy * (hi[2] - lo[2] + 1);
+    inv_nx = 1.0f / (float)nx;
+    inv_nxy = 1.0f / (float)nxy;
   }
   // (start, count) of cell c (0 when outside the range, beyond the ball or empty)
   __device__ __forceinline__ void cell(const GridView& g, const CellFrame& f, const float q[3],
@@ -56,7 +60,11 @@ struct BallCells {
     s = 0;
     n = 0;
     if (c >= ncell) return;
-    const int z = c / nxy, rem = c - z * nxy, y = rem / nx, x = rem - y * nx;
+    // c = (z * ny + y) * nx + x without integer division: (c + 1/2) / m is at
+    // least 1 / (2m) from an integer, above the float rounding of the product
+    // for every c < 2^22 (a ball meets at most 4 x 4 x 4 cells of edge >= r / 2)
+    const int z = __float2int_rz(((float)c + 0.5f) * inv_nxy), rem = c - z * nxy;
+    const int y = __float2int_rz(((float)rem + 0.5f) * inv_nx), x = rem - y * nx;
     const int c3[3] = {lo[0] + x, lo[1] + y, lo[2] + z};
     if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > r2) return;
     if (!cell_lookup(g, cell_key(f.level, 0, c3[0], c3[1], c3[2]), s, n)) n = 0;
@@ -92,16 +100,22 @@ __device__ __forceinline__ void walk_ball(const GridView& g, const float q[3], f
     if (lane == 31) s_pre[32] = total;
     __syncwarp();
     // candidate t of the chunk lies in cell ci with s_pre[ci] <= t < s_pre[ci + 1];
-    // each lane's t only grows, so its cell pointer only moves forward
-    int ci = 0;
+    // each lane's t only grows, so its cell pointer (held in registers: the
+    // cell's start, first and end candidate) only moves forward
+    int ci = 0, cs = s_start[0], cp = 0, cn = s_pre[1];
     for (int base = 0; base < total; base += 32) {
       const int t = base + lane;
       bool acc = false;
       float d2 = 0.0f;
       int idx = -1;
       if (t < total) {
-        while (s_pre[ci + 1] <= t) ++ci;
-        const float4 p = __ldg(g.pts + s_start[ci] + (t - s_pre[ci]));
+        while (t >= cn) {
+          ++ci;
+          cp = cn;
+          cs = s_start[ci];
+          cn = s_pre[ci + 1];
+        }
+        const float4 p = __ldg(g.pts + cs + (t - cp));
         d2 = sqdist(p.x, p.y, p.z, q[0], q[1], q[2]);
         idx = __float_as_int(p.w);
         acc = d2 <= r2;
@@ -117,7 +131,8 @@ __global__ void __launch_bounds__(kCountWarps * 32) k_radius_count(GridView g,
                                                                    const int* __restrict__ order,
                                                                    float r,
                                                                    long long* __restrict__ off,
-                                                                   unsigned* __restrict__ n_long) {
+                                                                   unsigned* __restrict__ n_long,
+                                                                   int* __restrict__ long_rows) {
   __shared__ int s_start[kCountWarps][32], s_pre[kCountWarps][33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t i = (int64_t)blockIdx.x * kCountWarps + w;
@@ -130,7 +145,7 @@ __global__ void __launch_bounds__(kCountWarps * 32) k_radius_count(GridView g,
   });
   if (lane == 0) {
     off[qi] = cnt;
-    if (cnt > kRowCapW) atomicAdd(n_long, 1u);
+    if (cnt > kRowCapW) long_rows[atomicAdd(n_long, 1u)] = (int)qi;  // at most nq rows
   }
 }
 
@@ -140,101 +155,108 @@ __device__ __forceinline__ int d2_bucket(float d2, float scale, int nb) {
   return (int)fminf(d2 * scale, (float)(nb - 1));
 }
 
-struct FillSmem {
-  u64 key[kRowCapW];          // the row's keys in visiting order
-  unsigned short pos[kRowCapW];  // positions in `key`, grouped by bucket
-  int cnt[kBucketsMax];       // bucket histogram, then bucket ends
-  int start[32], pre[33];     // the walk's cell chunk
-};
-
-__global__ void __launch_bounds__(kFillWarps * 32) k_radius_fill(GridView g,
-                                                                 const float* __restrict__ qry,
-                                                                 int64_t nq,
-                                                                 const int* __restrict__ order,
-                                                                 float r,
-                                                                 const long long* __restrict__ off,
-                                                                 int* __restrict__ out_idx,
-                                                                 float* __restrict__ out_d2,
-                                                                 int* __restrict__ long_rows,
-                                                                 unsigned* __restrict__ n_long,
-                                                                 unsigned long_cap) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// fill: the same walk; accepted points appended to the row in visiting order
+// (ballot positions: a warp's stores are consecutive words)
+__global__ void __launch_bounds__(kCountWarps * 32) k_radius_fill(GridView g,
+                                                                  const float* __restrict__ qry,
+                                                                  int64_t nq,
+                                                                  const int* __restrict__ order,
+                                                                  float r,
+                                                                  const long long* __restrict__ off,
+                                                                  int* __restrict__ out_idx,
+                                                                  float* __restrict__ out_d2) {
+  __shared__ int s_start[kCountWarps][32], s_pre[kCountWarps][33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  FillSmem& S = reinterpret_cast<FillSmem*>(smem_raw)[w];
-  const int64_t i = (int64_t)blockIdx.x * kFillWarps + w;
+  const int64_t i = (int64_t)blockIdx.x * kCountWarps + w;
   if (i >= nq) return;  // whole warp
   const int64_t qi = order ? order[i] : i;
   const float q[3] = {qry[3 * qi], qry[3 * qi + 1], qry[3 * qi + 2]};
   const long long b = off[qi];
   const int n = (int)(off[qi + 1] - b);
   if (n == 0) return;
-  const bool in_smem = n <= kRowCapW;
   int nacc = 0;
-  walk_ball(g, q, r, lane, S.start, S.pre, [&](bool acc, float d2, int idx) {
+  walk_ball(g, q, r, lane, s_start[w], s_pre[w], [&](bool acc, float d2, int idx) {
     const unsigned m = __ballot_sync(0xffffffffu, acc);
-    if (acc) {
-      // p < n: both passes take the same decisions in the same arithmetic
-      // (the test only keeps a disagreement from writing out of bounds)
-      const int p = nacc + __popc(m & ((1u << lane) - 1u));
-      if (p < n && in_smem) {
-        S.key[p] = pack_key(d2, idx);
-      } else if (p < n) {
-        out_idx[b + p] = idx;
-        out_d2[b + p] = d2;
-      }
+    // p < n: both passes take the same decisions in the same arithmetic (the
+    // test only keeps a disagreement from writing out of bounds)
+    const int p = nacc + __popc(m & ((1u << lane) - 1u));
+    if (acc && p < n) {
+      out_idx[b + p] = idx;
+      out_d2[b + p] = d2;
     }
     nacc += __popc(m);
   });
-  if (!in_smem) {
-    if (lane == 0) {
-      const unsigned slot = atomicAdd(n_long, 1u);
-      if (slot < long_cap) long_rows[slot] = (int)qi;
-    }
-    return;
-  }
-  // ---- bucket sort of the row in shared memory ----
+}
+
+struct SortSmem {
+  u64 key[kRowCapW];     // the row's keys in bucket order
+  int cnt[kBucketsMax];  // bucket histogram, then bucket starts, then ends
+};
+
+// sort: one warp per row of 2 .. kRowCapW keys, by (d2, index), with a
+// bucket sort: buckets of d2 * NB / r^2 (a monotone map, so bucket order
+// agrees with key order; NB a power of two >= n / 2), a histogram of the row
+// as filled, its scan, a scatter of the keys into bucket order in shared
+// memory, an insertion sort of each bucket by the lane that owns it (buckets
+// hold ~2 keys), and one coalesced write of the sorted row over the filled one
+__global__ void __launch_bounds__(kSortWarps * 32) k_sort_rows_warp(const long long* __restrict__ off,
+                                                                    int64_t nq, float r,
+                                                                    int* __restrict__ idx,
+                                                                    float* __restrict__ d2) {
+  __shared__ SortSmem smem[kSortWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  SortSmem& S = smem[w];
+  const int64_t row = (int64_t)blockIdx.x * kSortWarps + w;
+  if (row >= nq) return;  // whole warp
+  const long long b = off[row];
+  const int n = (int)(off[row + 1] - b);
+  if (n <= 1 || n > kRowCapW) return;  // nothing to sort, or a listed long row
   int nb = 32;
   while (nb < kBucketsMax && 2 * nb < n) nb <<= 1;
   const float r2 = r * r;
   const float scale = (float)nb / r2;
   for (int j = lane; j < nb; j += 32) S.cnt[j] = 0;
   __syncwarp();
-  for (int j = lane; j < n; j += 32) atomicAdd(&S.cnt[d2_bucket(key_d2(S.key[j]), scale, nb)], 1);
+  for (int j = lane; j < n; j += 32) atomicAdd(&S.cnt[d2_bucket(d2[b + j], scale, nb)], 1);
   __syncwarp();
-  {  // exclusive scan of the histogram: lane l owns buckets [l * per, (l + 1) * per)
-    const int per = nb >> 5;
-    int sum = 0;
-    for (int j = 0; j < per; ++j) sum += S.cnt[lane * per + j];
-    int incl = sum;
+  // exclusive scan of the histogram, 32 buckets at a time (conflict free)
+  int carry = 0;
+  for (int c0 = 0; c0 < nb; c0 += 32) {
+    const int v = S.cnt[c0 + lane];
+    int incl = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += v;
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
     }
-    int run = incl - sum;
-    for (int j = 0; j < per; ++j) {
-      const int c = S.cnt[lane * per + j];
-      S.cnt[lane * per + j] = run;
-      run += c;
+    S.cnt[c0 + lane] = carry + incl - v;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  __syncwarp();
+  // keys into bucket order (S.cnt[k] ends as the end of bucket k)
+  for (int j = lane; j < n; j += 32) {
+    const float dd = d2[b + j];
+    S.key[atomicAdd(&S.cnt[d2_bucket(dd, scale, nb)], 1)] = pack_key(dd, idx[b + j]);
+  }
+  __syncwarp();
+  // each lane sorts its buckets in place (bucket k spans [end(k-1), end(k)))
+  for (int k = lane; k < nb; k += 32) {
+    const int beg = k ? S.cnt[k - 1] : 0, end = S.cnt[k];
+    for (int i = beg + 1; i < end; ++i) {
+      const u64 x = S.key[i];
+      int j = i - 1;
+      while (j >= beg && S.key[j] > x) {
+        S.key[j + 1] = S.key[j];
+        --j;
+      }
+      S.key[j + 1] = x;
     }
   }
   __syncwarp();
   for (int j = lane; j < n; j += 32) {
-    const int bk = d2_bucket(key_d2(S.key[j]), scale, nb);
-    S.pos[atomicAdd(&S.cnt[bk], 1)] = (unsigned short)j;
-  }
-  __syncwarp();
-  // S.cnt[k] is now the end of bucket k; a key's rank = its bucket's start +
-  // the keys of its bucket that are smaller (keys are distinct: the index
-  // fills the low word)
-  for (int p = lane; p < n; p += 32) {
-    const u64 key = S.key[S.pos[p]];
-    const int bk = d2_bucket(key_d2(key), scale, nb);
-    const int beg = bk ? S.cnt[bk - 1] : 0, end = S.cnt[bk];
-    int rank = beg;
-    for (int u = beg; u < end; ++u) rank += S.key[S.pos[u]] < key;
-    out_idx[b + rank] = key_idx(key);
-    out_d2[b + rank] = key_d2(key);
+    const u64 key = S.key[j];
+    idx[b + j] = key_idx(key);
+    d2[b + j] = key_d2(key);
   }
 }
 
@@ -325,12 +347,11 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_rows(const long long* __r
 
 using namespace cil;
 
-extern "C" cil_status cil_radius_search(const float* ref, int64_t n_ref, const float* qry,
-                                        int64_t n_qry, float r, int64_t* out_offsets,
-                                        int32_t* out_idx, float* out_d2, int64_t capacity,
-                                        int64_t* out_nnz, void* stream) {
+static cil_status radius_impl(const float* ref, int64_t n_ref, const float* qry, int64_t n_qry,
+                              float r, int64_t* out_offsets, int32_t* out_idx, float* out_d2,
+                              int64_t capacity, int64_t* out_nnz, float cell_edge, void* stream) {
   if (n_ref < 0 || n_qry < 0 || n_ref > 0x7fffffff || n_qry > 0x7fffffff || !(r >= 0.0f) ||
-      !isfinite(r) || capacity < 0 || !out_nnz)
+      !isfinite(r) || capacity < 0 || !out_nnz || !(cell_edge >= 0.0f) || !isfinite(cell_edge))
     return CIL_ERR_INVALID_ARG;
   if (n_qry > 0 && (!qry || !out_offsets)) return CIL_ERR_INVALID_ARG;
   if (n_ref > 0 && !ref) return CIL_ERR_INVALID_ARG;
@@ -353,22 +374,24 @@ extern "C" cil_status cil_radius_search(const float* ref, int64_t n_ref, const f
   const size_t o_order = ws.reserve(sizeof(int) * (size_t)n_qry);
   const size_t o_tmp = ws.reserve(sizeof(long long) * (scan_tmp_ints(n_qry + 1) * 2 + 2));
   const size_t o_long = ws.reserve(sizeof(unsigned) * 2);
+  const size_t o_long_rows = ws.reserve(sizeof(int) * (size_t)n_qry);  // rows over kRowCapW
   if ((st = ws.allocate(ctx, s)) != CIL_OK) return st;
   GridOptions opt;
   opt.k_est = 10;
-  opt.cell_size = r > 0.0f ? r : 0.0f;
+  opt.cell_size = cell_edge;
   if ((st = grid_build(gp, ws, ref, nullptr, opt, ctx, s)) != CIL_OK) return st;
   const GridView g = grid_view(gp, ws);
   int* order = ws.at<int>(o_order);
   if ((st = order_queries(op, ws, qry, nullptr, 1, g.prm, nullptr, order, s)) != CIL_OK) return st;
   long long* off = reinterpret_cast<long long*>(out_offsets);
-  unsigned* n_long = ws.at<unsigned>(o_long);  // [0] rows longer than kRowCapW, [1] listed
-  if (cudaMemsetAsync(n_long, 0, sizeof(unsigned) * 2, s) != cudaSuccess) return CIL_ERR_CUDA;
+  unsigned* n_long = ws.at<unsigned>(o_long);  // rows longer than kRowCapW
+  int* long_rows = ws.at<int>(o_long_rows);     // and their indices
+  if (cudaMemsetAsync(n_long, 0, sizeof(unsigned), s) != cudaSuccess) return CIL_ERR_CUDA;
   {
     TimedRegion timer("k_radius", s);
     note_launches(1);
     k_radius_count<<<ceil_div(n_qry, kCountWarps), kCountWarps * 32, 0, s>>>(g, qry, n_qry, order, r,
-                                                                            off, n_long);
+                                                                            off, n_long, long_rows);
   }
   if (cudaMemsetAsync(off + n_qry, 0, sizeof(long long), s) != cudaSuccess) return CIL_ERR_CUDA;
   scan_exclusive_i64(off, n_qry + 1, ws.at<long long>(o_tmp), s);
@@ -391,25 +414,19 @@ extern "C" cil_status cil_radius_search(const float* ref, int64_t n_ref, const f
     if (!out_idx) return CIL_ERR_INVALID_ARG;
     float* d2 = out_d2;
     void* tmp = nullptr;
-    const size_t d2_bytes = out_d2 ? 0 : sizeof(float) * (size_t)h.nnz;
-    const size_t rows_bytes = sizeof(int) * (size_t)(h.n_long > 0 ? h.n_long : 1);
-    if (cudaMallocFromPoolAsync(&tmp, ((d2_bytes + 255) & ~size_t(255)) + rows_bytes, ctx->pool,
-                                s) != cudaSuccess)
-      return CIL_ERR_NOMEM;
-    if (!d2) d2 = static_cast<float*>(tmp);
-    int* long_rows = reinterpret_cast<int*>(static_cast<char*>(tmp) + ((d2_bytes + 255) & ~size_t(255)));
-    // the fill kernel's shared memory is above the 48 KB default (opt-in,
-    // set on the current device)
-    const int smem = (int)sizeof(FillSmem) * kFillWarps;
-    if (cudaFuncSetAttribute(k_radius_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-        cudaSuccess)
-      return CIL_ERR_CUDA;
+    if (!d2) {
+      if (cudaMallocFromPoolAsync(&tmp, sizeof(float) * (size_t)h.nnz, ctx->pool, s) != cudaSuccess)
+        return CIL_ERR_NOMEM;
+      d2 = static_cast<float*>(tmp);
+    }
     TimedRegion timer("k_radius", s);
-    note_launches(h.n_long > 0 ? 2 : 1);
-    k_radius_fill<<<ceil_div(n_qry, kFillWarps), kFillWarps * 32, smem, s>>>(
-        g, qry, n_qry, order, r, off, out_idx, d2, long_rows, n_long + 1, h.n_long);
+    note_launches(h.n_long > 0 ? 3 : 2);
+    k_radius_fill<<<ceil_div(n_qry, kCountWarps), kCountWarps * 32, 0, s>>>(g, qry, n_qry, order, r,
+                                                                           off, out_idx, d2);
+    k_sort_rows_warp<<<ceil_div(n_qry, kSortWarps), kSortWarps * 32, 0, s>>>(off, n_qry, r,
+                                                                            out_idx, d2);
     if (h.n_long > 0) k_sort_rows<<<h.n_long, kSortThreads, 0, s>>>(off, long_rows, out_idx, d2);
-    cudaFreeAsync(tmp, s);
+    if (tmp) cudaFreeAsync(tmp, s);
   }
   ws.release(s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return CIL_ERR_CUDA;
@@ -421,4 +438,28 @@ extern "C" cil_status cil_radius_search(const float* ref, int64_t n_ref, const f
     return (cil_status)v;
   }
   return CIL_OK;
+}
+
+// The ball's cells: edge r by default (at most 4 x 4 x 4 cells per query);
+// params->cell_size (> 0) sets the edge, else params->cell_scale (> 0)
+// multiplies r.  The edge is rounded to a power-of-two multiple of the fine
+// lattice; it changes the time, not the result.
+extern "C" cil_status cil_radius_search_ex(const float* ref, int64_t n_ref, const float* qry,
+                                           int64_t n_qry, float r, int64_t* out_offsets,
+                                           int32_t* out_idx, float* out_d2, int64_t capacity,
+                                           int64_t* out_nnz, const cil_params* params,
+                                           void* stream) {
+  float edge = r > 0.0f ? r : 0.0f;
+  if (params && params->cell_size > 0.0f) edge = params->cell_size;
+  else if (params && params->cell_scale > 0.0f && r > 0.0f) edge = r * params->cell_scale;
+  return radius_impl(ref, n_ref, qry, n_qry, r, out_offsets, out_idx, out_d2, capacity, out_nnz,
+                     edge, stream);
+}
+
+extern "C" cil_status cil_radius_search(const float* ref, int64_t n_ref, const float* qry,
+                                        int64_t n_qry, float r, int64_t* out_offsets,
+                                        int32_t* out_idx, float* out_d2, int64_t capacity,
+                                        int64_t* out_nnz, void* stream) {
+  return cil_radius_search_ex(ref, n_ref, qry, n_qry, r, out_offsets, out_idx, out_d2, capacity,
+                              out_nnz, nullptr, stream);
 }

@@ -36,6 +36,8 @@ def main(argv=None):
     ap.add_argument("--radius", type=float, default=0.5)
     ap.add_argument("--cell-scale", type=float, default=0.0,
                     help="grid cell-size multiplier (0: the library default)")
+    ap.add_argument("--topk", type=int, default=0,
+                    help="k-NN search layout (0 default, 1 list, 2 heap, 3 warp-staged)")
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--metric", choices=["point_to_plane", "point_to_point", "combined"],
@@ -93,10 +95,11 @@ def main(argv=None):
         fn = {
             "icp": lambda: cil.icp(src, dst, nrm, iters=a.iters, max_corr_dist=dmax, **icp_kw),
             "register": lambda: cil.register_pair(src, dst, k, vp, a.iters, dmax, out_normals=nrm,
-                                                  cell_scale=a.cell_scale),
-            "knn": lambda: cil.knn(dst, dst, k, cell_scale=a.cell_scale),
-            "normals": lambda: cil.estimate_normals(dst, k, vp, cell_scale=a.cell_scale),
-            "radius": lambda: cil.radius_search(dst, dst, a.radius),
+                                                  cell_scale=a.cell_scale, topk=a.topk),
+            "knn": lambda: cil.knn(dst, dst, k, cell_scale=a.cell_scale, topk=a.topk),
+            "normals": lambda: cil.estimate_normals(dst, k, vp, cell_scale=a.cell_scale,
+                                                    topk=a.topk),
+            "radius": lambda: cil.radius_search(dst, dst, a.radius, cell_scale=a.cell_scale),
         }[a.op]
     L = cil.lib()
     fn()

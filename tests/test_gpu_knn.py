@@ -134,3 +134,48 @@ def test_lidar_full_size_sampled():
     p = synth.lidar_sweep_pair(0)
     rows = np.random.default_rng(13).choice(len(p.target), 2000, replace=False)
     _check(p.target, None, 16, self_query=True, rows=rows)
+
+
+@pytest.mark.parametrize("topk", [1, 2, 3])
+def test_topk_layouts_give_bitwise_equal_results(topk):
+    """The top-k layout (per-query register list, per-query shared-memory
+    heap, or the warp-staged search that scans a shared set of points per 32
+    queries and falls back to the per-query search where it cannot prove the
+    k-th distance) changes the speed only: results are bitwise those of the
+    default, on clustered and outlier-heavy clouds, with exact ties."""
+    rng = np.random.default_rng(31)
+    dense = rng.normal(0, 0.01, (6000, 3))
+    sparse = rng.uniform(-50, 50, (300, 3))
+    clouds = [synth.surface_pair(12, n=20_000).target,
+              np.concatenate([dense, sparse]).astype(np.float32),
+              synth.lattice_points((20, 20, 20))]
+    for ref in clouds:
+        qry = np.concatenate([ref[::3] + np.float32(1e-3), ref[:50] + np.float32(70.0)])
+        for k in (1, 4, 10, 16, 32):
+            for q, self_query in ((None, True), (qry, False)):
+                a = _gpu_knn(ref, q, k, self_query)
+                b = _gpu_knn(ref, q, k, self_query, topk=topk)
+                assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), (k, self_query)
+    _check(clouds[0], None, 10, self_query=True, topk=topk)
+    _check(clouds[1], qry, 10, topk=topk)
+
+
+def test_staged_normals_and_batch_bitwise_equal():
+    p = synth.surface_pair(13, n=30_000)
+    x = torch.from_numpy(p.target).cuda()
+    for k in (3, 10, 30):
+        n0, c0 = cil.estimate_normals(x, k, p.viewpoint)
+        n3, c3 = cil.estimate_normals(x, k, p.viewpoint, topk=3)
+        torch.cuda.synchronize()
+        assert torch.equal(n0, n3) and torch.equal(c0, c3)
+    sizes = np.array([2000, 3500, 9000, 700, 12000], np.int64)
+    src, dst, _ = synth.surface_batch_torch(5, sizes)
+    out = []
+    for topk in (0, 3):
+        h = cil.Batch(sizes, sizes, k=10, iters=5, max_corr_dist=0.1, topk=topk)
+        nrm = torch.empty_like(dst)
+        T, _ = h.run(src, dst, normals_out=nrm)
+        torch.cuda.synchronize()
+        out.append((T.clone(), nrm.clone()))
+        h.close()
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])

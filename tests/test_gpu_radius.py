@@ -102,3 +102,15 @@ def test_lattice_rows_across_sort_paths(r):
     assert lengths.max() >= 7
     if r >= 7.0:
         assert lengths.max() > 1024
+
+
+@pytest.mark.parametrize("scale", [0.5, 0.7, 2.0])
+def test_cell_size_does_not_change_results(scale):
+    """The cell edge of the search (r by default) is a speed knob only."""
+    p = synth.lidar_sweep_pair(1)
+    R = torch.from_numpy(p.target).cuda()
+    a = cil.radius_search(R, R, 0.5)
+    b = cil.radius_search(R, R, 0.5, cell_scale=scale)
+    torch.cuda.synchronize()
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
