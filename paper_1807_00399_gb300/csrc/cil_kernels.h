@@ -77,7 +77,7 @@ struct IcpPlan {
   int n_tiles = 0;
   int tile = 0;     // source points per tile
   int n_groups = 0;  // tile groups over all pairs
-  size_t o_state, o_order, o_tile_off, o_rt, o_part_s, o_part_c, o_part_n;
+  size_t o_state, o_order, o_src_sorted, o_tile_off, o_rt, o_part_s, o_part_c, o_part_n;
   size_t o_grp_s, o_grp_c, o_grp_n, o_grp_done;
   size_t o_corr, o_lbd, o_queue, o_qc;
   OrderPlan order;

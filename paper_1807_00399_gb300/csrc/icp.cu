@@ -50,6 +50,7 @@ struct IcpArgs {
   GridView g;
   const float* src;
   const int* order;     // sorted position -> global source index
+  const float4* src_sorted;  // source points in sorted order (x, y, z, unused)
   const float* dst;     // concatenated target points
   const float* dst_n;   // concatenated target normals (null for point-to-point)
   const int* tile_off;  // [pairs + 1] tile prefix
@@ -430,7 +431,7 @@ __device__ bool warp_directory(const GridView& g, int cloud, const float q[3], f
 
 // SO(3) exponential (Rodrigues), FP64.  With t = |w|, s = sin(t/2), c = cos(t/2):
 // sin(t)/t = 2 s c / t and (1 - cos t)/t^2 = 2 s^2 / t^2 (no cancellation).
-__device__ void so3_exp_d(const double w[3], double R[9]) {
+__device__ __forceinline__ void so3_exp_d(const double w[3], double R[9]) {
   const double t2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
   double a, b;  // sin(t)/t and (1 - cos(t))/t^2
   if (t2 < 1e-16) {
@@ -458,32 +459,53 @@ __device__ void so3_exp_d(const double w[3], double R[9]) {
 
 // H x = -g by Cholesky H = L L^T in FP64; false if a pivot <= 1e-12 trace(H).
 // Only the reciprocals of L's diagonal are kept (r_j = 1 / L_jj).
-__device__ bool chol_solve6(const double H[36], const double g[6], double x[6]) {
-  double L[36], r[6];
+// Row-by-row index of the upper-triangle entry (u, v), u <= v, of a 6x6
+// symmetric matrix: the layout of the round's sums.
+__host__ __device__ constexpr int sym6(int u, int v) { return 6 * u - u * (u - 1) / 2 + (v - u); }
+
+// Solve H x = -g by Cholesky (H = L L^T), H given as its 21 upper-triangle
+// sums and g after them (tot[0..20], tot[21..26]).  L is kept packed (lower
+// triangle, row by row) with the reciprocals of its diagonal, every loop has
+// compile-time bounds and is unrolled: the solve stays in registers (it runs
+// on one thread while the rest of the GPU waits for the round to close).
+// False when a pivot is <= 1e-12 trace(H).
+__device__ __forceinline__ bool chol_solve6(const double* tot, double x[6]) {
+  double L[21], r[6];  // L(i, j), j < i, at i (i + 1) / 2 + j; r[j] = 1 / L(j, j)
   double tr = 0.0;
-  for (int a = 0; a < 6; ++a) tr += H[7 * a];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) tr += tot[sym6(a, a)];
   if (!(tr > 0.0)) return false;
   const double piv_min = 1e-12 * tr;
+  bool ok = true;
+#pragma unroll
   for (int j = 0; j < 6; ++j) {
-    double d = H[7 * j];
-    for (int m = 0; m < j; ++m) d = fma(-L[6 * j + m], L[6 * j + m], d);
-    if (!(d > piv_min)) return false;
+    double d = tot[sym6(j, j)];
+#pragma unroll
+    for (int m = 0; m < j; ++m) d = fma(-L[j * (j + 1) / 2 + m], L[j * (j + 1) / 2 + m], d);
+    ok = ok && (d > piv_min);
     r[j] = rsqrt(d);
+#pragma unroll
     for (int i = j + 1; i < 6; ++i) {
-      double v = H[6 * i + j];
-      for (int m = 0; m < j; ++m) v = fma(-L[6 * i + m], L[6 * j + m], v);
-      L[6 * i + j] = v * r[j];
+      double v = tot[sym6(j, i)];
+#pragma unroll
+      for (int m = 0; m < j; ++m) v = fma(-L[i * (i + 1) / 2 + m], L[j * (j + 1) / 2 + m], v);
+      L[i * (i + 1) / 2 + j] = v * r[j];
     }
   }
+  if (!ok) return false;
   double y[6];
+#pragma unroll
   for (int i = 0; i < 6; ++i) {
-    double v = -g[i];
-    for (int m = 0; m < i; ++m) v = fma(-L[6 * i + m], y[m], v);
+    double v = -tot[21 + i];
+#pragma unroll
+    for (int m = 0; m < i; ++m) v = fma(-L[i * (i + 1) / 2 + m], y[m], v);
     y[i] = v * r[i];
   }
+#pragma unroll
   for (int i = 5; i >= 0; --i) {
     double v = y[i];
-    for (int m = i + 1; m < 6; ++m) v = fma(-L[6 * m + i], x[m], v);
+#pragma unroll
+    for (int m = i + 1; m < 6; ++m) v = fma(-L[m * (m + 1) / 2 + i], x[m], v);
     x[i] = v * r[i];
   }
   return true;
@@ -606,6 +628,7 @@ __device__ __noinline__ void close_round(IcpPairState& S, const double* tot, lon
     return;
   }
   // the transform this round's searches used, for the next round's certificates
+#pragma unroll
   for (int j = 0; j < 12; ++j) S.Rt_prev[j] = S.Rt[j];
   S.has_prev = 1;
   double dR[9], dt[3];
@@ -615,16 +638,8 @@ __device__ __noinline__ void close_round(IcpPairState& S, const double* tot, lon
       return;
     }
   } else {
-    double H[36], g[6], xi[6];
-    int q = 0;
-    for (int u = 0; u < 6; ++u)
-      for (int v = u; v < 6; ++v) {
-        H[6 * u + v] = tot[q];
-        H[6 * v + u] = tot[q];
-        ++q;
-      }
-    for (int u = 0; u < 6; ++u) g[u] = tot[21 + u];
-    if (n < 6 || !chol_solve6(H, g, xi)) {
+    double xi[6];
+    if (n < 6 || !chol_solve6(tot, xi)) {
       S.status = CIL_ERR_DEGENERATE;
       return;
     }
@@ -632,8 +647,11 @@ __device__ __noinline__ void close_round(IcpPairState& S, const double* tot, lon
     for (int u = 0; u < 3; ++u) dt[u] = xi[3 + u];
   }
   double T[16], Tn[16];
+#pragma unroll
   for (int j = 0; j < 16; ++j) T[j] = __ldcg(&S.T[j]);
+#pragma unroll
   for (int u = 0; u < 3; ++u) {
+#pragma unroll
     for (int v = 0; v < 4; ++v)
       Tn[4 * u + v] = dR[3 * u] * T[v] + dR[3 * u + 1] * T[4 + v] + dR[3 * u + 2] * T[8 + v];
     Tn[4 * u + 3] += dt[u];
@@ -642,10 +660,142 @@ __device__ __noinline__ void close_round(IcpPairState& S, const double* tot, lon
   Tn[13] = 0.0;
   Tn[14] = 0.0;
   Tn[15] = 1.0;
+#pragma unroll
   for (int j = 0; j < 16; ++j) S.T[j] = Tn[j];
   float Rt[12];
   rt_from_T(Tn, Rt);
+#pragma unroll
   for (int j = 0; j < 12; ++j) S.Rt[j] = Rt[j];
+}
+
+// sin(x)/x and cos(x) for |x| <= 0.1 from their Taylor series in x^2 (the
+// first omitted terms, x^12 / 13! and x^12 / 12!, are below 1e-20)
+__device__ __forceinline__ void sinc_cos_small(double x2, double& sinc, double& c) {
+  sinc = fma(fma(fma(fma(fma(x2, -1.0 / 39916800.0, 1.0 / 362880.0), x2, -1.0 / 5040.0), x2,
+                     1.0 / 120.0), x2, -1.0 / 6.0), x2, 1.0);
+  c = fma(fma(fma(fma(fma(x2, -1.0 / 3628800.0, 1.0 / 40320.0), x2, -1.0 / 720.0), x2,
+                  1.0 / 24.0), x2, -0.5), x2, 1.0);
+}
+
+constexpr unsigned kFull = 0xffffffffu;
+__device__ __forceinline__ int tri6(int i, int k) { return i * (i + 1) / 2 + k; }  // k <= i
+
+// Round close of one pair by a whole warp, for the linearised metrics (the
+// update is the FP64 Cholesky solve of H xi = -g).  FP64 runs at a small
+// fraction of the FP32 rate on this GPU, and a warp instruction costs the
+// same however few lanes it has, so the work is spread over the lanes: lane
+// e < 21 holds entry (i, k), k <= i, of the lower triangle; each Cholesky
+// column is one scaling and one trailing update across the lanes (the same
+// fma sequence per entry as a column-by-column solve), the substitutions
+// update all remaining entries at once, and the rotation entries and the
+// new pose take a lane each.  The final round and the point-to-point closed
+// form go to close_round on lane 0.
+__device__ __noinline__ void close_round_warp(IcpPairState& S, const double* tot, long long n,
+                                              bool final_round, int metric, int lane) {
+  if (final_round || metric == CIL_METRIC_POINT_TO_POINT) {
+    if (lane == 0) close_round(S, tot, n, final_round, metric);
+    return;
+  }
+  // the transform this round's searches used, for the next round's certificates
+  if (lane < 12) S.Rt_prev[lane] = S.Rt[lane];
+  if (lane == 0) S.has_prev = 1;
+  const int e = lane < 21 ? lane : 20;
+  const int i = e >= 15 ? 5 : e >= 10 ? 4 : e >= 6 ? 3 : e >= 3 ? 2 : e >= 1 ? 1 : 0;
+  const int k = e - tri6(i, 0);
+  double a = lane < 21 ? tot[sym6(k, i)] : 0.0;
+  double tr = 0.0;
+#pragma unroll
+  for (int d = 0; d < 6; ++d) tr += tot[sym6(d, d)];
+  bool ok = n >= 6 && tr > 0.0;
+  const double piv_min = 1e-12 * tr;
+  double r_mine = 0.0;  // lane j < 6: 1 / L(j, j)
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const double d = __shfl_sync(kFull, a, tri6(j, j));
+    ok = ok && (d > piv_min);
+    const double rj = rsqrt(d);
+    if (lane == j) r_mine = rj;
+    if (lane < 21 && k == j && i > j) a *= rj;  // column j of L
+    const bool upd = lane < 21 && k > j;        // then i >= k > j
+    const double lij = __shfl_sync(kFull, a, upd ? tri6(i, j) : 0);
+    const double lkj = __shfl_sync(kFull, a, upd ? tri6(k, j) : 0);
+    if (upd) a = fma(-lij, lkj, a);
+  }
+  if (!ok) {
+    if (lane == 0) S.status = CIL_ERR_DEGENERATE;
+    return;
+  }
+  // L y = -g (forward), L^T x = y (backward); lane j < 6 holds entry j
+  double v = lane < 6 ? -tot[21 + lane] : 0.0;
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    const double ym = __shfl_sync(kFull, v, m) * __shfl_sync(kFull, r_mine, m);
+    if (lane == m) v = ym;
+    const bool upd = lane < 6 && lane > m;
+    const double lim = __shfl_sync(kFull, a, upd ? tri6(lane, m) : 0);
+    if (upd) v = fma(-lim, ym, v);
+  }
+#pragma unroll
+  for (int m = 5; m >= 0; --m) {
+    const double xm = __shfl_sync(kFull, v, m) * __shfl_sync(kFull, r_mine, m);
+    if (lane == m) v = xm;
+    const bool upd = lane < m;
+    const double lmi = __shfl_sync(kFull, a, upd ? tri6(m, lane) : 0);
+    if (upd) v = fma(-lmi, xm, v);
+  }
+  // xi = (w, tau): R = I + A [w]x + B [w]x^2, A = sin(t)/t, B = (1 - cos t)/t^2
+  const double w0 = __shfl_sync(kFull, v, 0), w1 = __shfl_sync(kFull, v, 1),
+               w2 = __shfl_sync(kFull, v, 2);
+  const double t2 = w0 * w0 + w1 * w1 + w2 * w2;
+  double A, B;
+  if (t2 <= 0.04) {  // half angle <= 0.1
+    double sinc, c;
+    sinc_cos_small(0.25 * t2, sinc, c);
+    A = sinc * c;            // sin(t)/t = sin(t/2) cos(t/2) / (t/2)
+    B = 0.5 * sinc * sinc;   // (1 - cos t)/t^2 = 2 sin^2(t/2) / t^2
+  } else {
+    const double it = rsqrt(t2);
+    double sn, cs;
+    sincos(0.5 * (t2 * it), &sn, &cs);
+    const double si = sn * it;
+    A = 2.0 * si * cs;
+    B = 2.0 * si * si;
+  }
+  // entry (u, c) of dR on lane 3 u + c (< 9)
+  const int u = lane < 12 ? lane / 4 : 0, col = lane < 12 ? lane % 4 : 0;
+  double dr = 0.0;
+  if (lane < 9) {
+    const int ru = lane / 3, rc = lane % 3;
+    const double wu = ru == 0 ? w0 : ru == 1 ? w1 : w2;
+    const double wc = rc == 0 ? w0 : rc == 1 ? w1 : w2;
+    // [w]x (ru, rc): 0 on the diagonal, else -+ w of the third axis
+    const int third = 3 - ru - rc;
+    const double wt = third == 0 ? w0 : third == 1 ? w1 : w2;
+    const double kx = ru == rc ? 0.0 : (((rc - ru + 3) % 3 == 1) ? -wt : wt);
+    dr = (ru == rc ? 1.0 : 0.0) + B * (wu * wc - (ru == rc ? t2 : 0.0)) + A * kx;
+  }
+  const double d0 = __shfl_sync(kFull, dr, 3 * u), d1 = __shfl_sync(kFull, dr, 3 * u + 1),
+               d2 = __shfl_sync(kFull, dr, 3 * u + 2);
+  const double tau = __shfl_sync(kFull, v, 3 + u);
+  double tn = 0.0;
+  if (lane < 12) {
+    const double T0 = __ldcg(&S.T[col]), T1 = __ldcg(&S.T[4 + col]), T2 = __ldcg(&S.T[8 + col]);
+    tn = d0 * T0 + d1 * T1 + d2 * T2;
+    if (col == 3) tn += tau;
+  }
+  __syncwarp();
+  if (lane < 12) {
+    S.T[lane] = tn;
+    S.Rt[lane] = (float)tn;
+  }
+}
+
+__global__ void k_gather_source(const float* __restrict__ src, const int* __restrict__ order,
+                                int64_t n, float4* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t si = order[i];
+  out[i] = make_float4(src[3 * si], src[3 * si + 1], src[3 * si + 2], 0.0f);
 }
 
 __global__ void k_icp_setup(IcpPairState* st, int pairs, const int* src_start, int64_t n_src_single,
@@ -750,9 +900,8 @@ __device__ __forceinline__ int pair_of(const int* off, int pairs, int v) {
 // operations in every kernel, so every kernel sees the same p')
 __device__ __forceinline__ void transformed_source(const IcpArgs& a, const float* Rt, int pos,
                                                    float p[3]) {
-  const int64_t si = __ldg(a.order + pos);
-  const float x = __ldg(a.src + 3 * si), y = __ldg(a.src + 3 * si + 1),
-              z = __ldg(a.src + 3 * si + 2);
+  const float4 sp = __ldg(a.src_sorted + pos);
+  const float x = sp.x, y = sp.y, z = sp.z;
   p[0] = fmaf(Rt[0], x, fmaf(Rt[1], y, fmaf(Rt[2], z, Rt[3])));
   p[1] = fmaf(Rt[4], x, fmaf(Rt[5], y, fmaf(Rt[6], z, Rt[7])));
   p[2] = fmaf(Rt[8], x, fmaf(Rt[9], y, fmaf(Rt[10], z, Rt[11])));
@@ -829,9 +978,8 @@ __global__ void __launch_bounds__(kIcpThreads, 4) k_icp_search(IcpArgs a, int ro
     const int j = a.corr[pos];
     const float lb = a.lbd[pos];
     {
-      const int64_t si = __ldg(a.order + pos);
-      const float x = __ldg(a.src + 3 * si), y = __ldg(a.src + 3 * si + 1),
-                  z = __ldg(a.src + 3 * si + 2);
+      const float4 sp = __ldg(a.src_sorted + pos);
+      const float x = sp.x, y = sp.y, z = sp.z;
       const float* R = s_Rt;
       const float* R0 = s_Rp;
       // the same operations as transformed_source
@@ -1231,10 +1379,10 @@ __global__ void __launch_bounds__(kIcpThreads, 4) k_icp_accumulate(IcpArgs a, in
     double* o = a.opt.sums + ((int64_t)b * a.rounds + round) * (kIcpQ + 1);
     o[tid] = tid < kIcpQ ? sm_tot[tid] : (double)sm_cnt;
   }
-  if (tid == 0) {
+  if (warp == 0) {
     IcpPairState& S = a.st[b];
-    close_round(S, sm_tot, sm_cnt, round == a.rounds - 1, a.opt.metric);
-    S.tiles_done = 0;
+    close_round_warp(S, sm_tot, sm_cnt, round == a.rounds - 1, a.opt.metric, lane);
+    if (lane == 0) S.tiles_done = 0;
   }
 }
 
@@ -1289,6 +1437,7 @@ void icp_plan(IcpPlan& p, Workspace& ws, const int64_t* src_counts, int pairs) {
   const size_t ns = (size_t)(p.n_src > 0 ? p.n_src : 1);
   p.o_state = ws.reserve(sizeof(IcpPairState) * pairs);
   p.o_order = ws.reserve(sizeof(int) * ns);
+  p.o_src_sorted = ws.reserve(sizeof(float4) * ns);
   p.o_tile_off = ws.reserve(sizeof(int) * (pairs + 1));
   p.o_rt = ws.reserve(sizeof(float) * 12 * pairs);
   p.o_part_s = ws.reserve(sizeof(float) * kIcpQ * nt);
@@ -1333,11 +1482,19 @@ cil_status icp_run(const IcpPlan& p, const Workspace& ws, const GridView& tgt, c
   int* order = ws.at<int>(p.o_order);
   cil_status stt = order_queries(p.order, ws, src, src_start_dev, p.pairs, tgt.prm, rt, order, s);
   if (stt != CIL_OK) return stt;
+  // the source points in that order, once per call (the rounds read them
+  // directly instead of through the order)
+  float4* src_sorted = ws.at<float4>(p.o_src_sorted);
+  if (p.n_src > 0) {
+    note_launches(1);
+    k_gather_source<<<ceil_div(p.n_src, 256), 256, 0, s>>>(src, order, p.n_src, src_sorted);
+  }
   if (n_tiles == 0) return cudaGetLastError() == cudaSuccess ? CIL_OK : CIL_ERR_CUDA;
   IcpArgs a;
   a.g = tgt;
   a.src = src;
   a.order = order;
+  a.src_sorted = src_sorted;
   a.dst = dst;
   a.dst_n = dst_normals;
   a.opt = opt ? *opt : IcpOptions();
