@@ -466,6 +466,16 @@ __global__ void __launch_bounds__(1024) k_choose_level(GridParams* prm, const fl
   constexpr int S = 1024;
   __shared__ float est[S];
   GridParams& P = prm[blockIdx.x];
+  if (cell_size > 0.0f) {  // the edge is given: nothing to estimate
+    if (threadIdx.x == 0) {
+      const float ratio = cell_size / P.fine;
+      int L = ratio <= 1.0f ? 0 : (int)rintf(log2f(ratio));
+      L = max(0, min(L, kFineBits));
+      P.level = L;
+      P.cell = ldexpf(P.fine, L);
+    }
+    return;
+  }
   const int n = P.n, s0 = P.start;
   int k = cloud_k ? cloud_k[blockIdx.x] : k_default;
   k = max(1, min(k, KMAX));
@@ -507,14 +517,9 @@ __global__ void __launch_bounds__(1024) k_choose_level(GridParams* prm, const fl
   }
   if (threadIdx.x == 0) {
     const float fine = P.fine;
-    float target;
-    if (cell_size > 0.0f) {
-      target = cell_size;
-    } else {
-      const float med = ns > 0 ? est[ns / 2] : __int_as_float(0x7f800000);
-      const float R = isfinite(med) ? sqrtf(med) : fine * (float)kFineDim;
-      target = (cell_scale > 0.0f ? cell_scale : kDefaultCellScale) * R;
-    }
+    const float med = ns > 0 ? est[ns / 2] : __int_as_float(0x7f800000);
+    const float R = isfinite(med) ? sqrtf(med) : fine * (float)kFineDim;
+    const float target = (cell_scale > 0.0f ? cell_scale : kDefaultCellScale) * R;
     const float ratio = target / fine;
     int L = ratio <= 1.0f ? 0 : (int)rintf(log2f(ratio));
     L = max(0, min(L, kFineBits));
