@@ -54,13 +54,15 @@ WORKLOAD = ("depth-frame pair 640x480 (pinhole 525/319.5/239.5, ground + 20 boxe
             "PCA normals of every target point + 30 point-to-plane ICP rounds (d_max 0.05 m) + "
             "final RMSE pass")
 
-# DRAM traffic (read + write bytes) per launch measured by ncu, per kernel,
-# with the hash of the sources the kernel is built from; a figure is reported
-# only while those sources are unchanged.
+# DRAM traffic (read + write bytes) measured by ncu (cold caches), per kernel:
+# k_icp_search one launch (round 9 of the depth-frame pair), k_knn the
+# depth-frame 10-NN self-query, k_radius one LiDAR r = 0.5 m call (count,
+# fill and both sorts); with the hash of the sources the kernel is built from,
+# so a figure is reported only while those sources are unchanged.
 TRAFFIC = {
-    "k_icp_search": {"bytes": None, "src_sha": None},
-    "k_knn": {"bytes": None, "src_sha": None},
-    "k_radius": {"bytes": None, "src_sha": None},
+    "k_icp_search": {"bytes": 22089728, "src_sha": "ac094fc57cf5c284"},
+    "k_knn": {"bytes": 17022464, "src_sha": "6c4e152bec122e33"},
+    "k_radius": {"bytes": 804495872, "src_sha": "6ae3802c7b6a1131"},
 }
 KERNEL_SOURCES = {
     "k_icp_search": ("icp.cu",),
