@@ -539,8 +539,9 @@ def run_ours(args):
 
 
 LEARNED_SUMMARY = ("pairs", "pairs_per_s_learned_fallback", "pairs_per_s_identity",
-                   "success_learned_fallback", "success_identity",
-                   "median_rmse_success_learned_fallback", "median_rmse_success_identity",
+                   "pairs_per_s_plain", "success_learned_fallback", "success_identity",
+                   "success_plain", "median_rmse_success_learned_fallback",
+                   "median_rmse_success_identity", "median_rmse_success_plain",
                    "pairs_reregistered", "runs")
 
 

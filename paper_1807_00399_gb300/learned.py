@@ -152,7 +152,8 @@ def rot_err_deg(Ta, Tb):
 def evaluate(net, pairs, src_sub, dst_sub, iters: int = 30, max_corr_dist: float = 0.1,
              k: int = 10, runs: int = 10):
     """Learned warm start + batched ICP + fallback against batched ICP from
-    the identity, on held-out pairs.  The learned arm is the network's
+    the identity and against the plain path (one single-pair call per pair,
+    in sequence, from the identity), on held-out pairs.  The learned arm is the network's
     forward (encoder + head -> T_init), the batch run from T_init, and the
     library's fallback (pairs with final RMSE >= SUCCESS_RMSE re-registered
     from the identity, the better result kept); the identity arm is the batch
@@ -206,6 +207,30 @@ def evaluate(net, pairs, src_sub, dst_sub, iters: int = 30, max_corr_dist: float
             ms[name].append(a.elapsed_time(b))
     ms_learned = float(np.median(ms["learned"]))
     ms_identity = float(np.median(ms["identity"]))
+    # the plain path: one single-pair call (grid, normals, 30 rounds) per pair
+    # from the identity, in sequence
+    from . import register_pair
+    offs = np.concatenate([[0], np.cumsum(n)])
+    T_p = torch.empty((B, 16), dtype=torch.float64, device="cuda")
+    rep_p = torch.empty((B, 24), dtype=torch.uint8, device="cuda")
+    nrm = torch.empty_like(dst)
+
+    def plain_arm():
+        for b in range(B):
+            s0, s1 = int(offs[b]), int(offs[b + 1])
+            register_pair(src[s0:s1], dst[s0:s1], k, (0.0, 0.0, 10.0), iters, max_corr_dist,
+                          out_normals=nrm[s0:s1], out_T=T_p[b], out_report=rep_p[b])
+
+    plain_arm()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    a.record()
+    plain_arm()
+    e.record()
+    torch.cuda.synchronize()
+    ms_plain = a.elapsed_time(e)
+    rp = decode_reports(rep_p, B)
     rl = decode_reports(rep_l, B)
     rw = decode_reports(rep_warm, B)
     ri = decode_reports(rep_i, B)
@@ -219,6 +244,8 @@ def evaluate(net, pairs, src_sub, dst_sub, iters: int = 30, max_corr_dist: float
     ok_l = np.nan_to_num(rm_l, nan=np.inf) < SUCCESS_RMSE
     ok_w = np.nan_to_num(rm_w, nan=np.inf) < SUCCESS_RMSE
     ok_i = np.nan_to_num(rm_i, nan=np.inf) < SUCCESS_RMSE
+    rm_p = np.array([r["rmse"] for r in rp])
+    ok_p = np.nan_to_num(rm_p, nan=np.inf) < SUCCESS_RMSE
     return {
         "pairs": B,
         "runs": runs,
@@ -241,6 +268,11 @@ def evaluate(net, pairs, src_sub, dst_sub, iters: int = 30, max_corr_dist: float
         "pairs_per_s_identity": B / (ms_identity / 1e3),
         "successful_pairs_per_s_learned_fallback": float(ok_l.sum()) / (ms_learned / 1e3),
         "successful_pairs_per_s_identity": float(ok_i.sum()) / (ms_identity / 1e3),
+        "ms_plain_sequential": ms_plain,
+        "pairs_per_s_plain": B / (ms_plain / 1e3),
+        "success_plain": float(ok_p.mean()),
+        "median_rmse_success_plain": float(np.median(rm_p[ok_p])) if ok_p.any() else None,
+        "plain_equals_batched_identity": bool(torch.equal(T_p, T_i)),
     }
 
 
