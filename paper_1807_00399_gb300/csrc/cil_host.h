@@ -66,6 +66,7 @@ struct GridPlan {
   int radix_blocks = 0;
   // workspace offsets
   size_t o_prm, o_pts, o_tab, o_keys0, o_keys1, o_vals0, o_vals1, o_counts, o_scan, o_starts;
+  size_t o_est;         // sampled neighbour distances of the level choice (1024 per cloud)
 };
 
 // Default multiplier on the data-driven cell edge (the median k-th neighbour

@@ -217,15 +217,68 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_hist(const u64* __restrict
   for (int d = threadIdx.x; d < kRadix; d += kRsThreads) counts[(int64_t)d * nblk + blockIdx.x] = h[d];
 }
 
+// Per-digit prefix over the blocks: one warp per digit scans its nblk block
+// counts (digit-major, contiguous) into exclusive prefixes in place and
+// writes the digit's total; the scatter adds the digits' exclusive bases.
+constexpr int kDigitWarps = 8;
+__global__ void __launch_bounds__(kDigitWarps * 32) k_radix_digit_scan(int* __restrict__ counts,
+                                                                       int nblk,
+                                                                       int* __restrict__ totals) {
+  const int lane = threadIdx.x & 31;
+  const int d = blockIdx.x * kDigitWarps + (threadIdx.x >> 5);
+  int* c = counts + (int64_t)d * nblk;
+  int carry = 0;
+  for (int b0 = 0; b0 < nblk; b0 += 32) {
+    const int b = b0 + lane;
+    const int v = b < nblk ? c[b] : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (b < nblk) c[b] = carry + incl - v;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) totals[d] = carry;
+}
+
 // Stable scatter: each warp ranks its 256 items (index order = item j major,
 // lane minor) with match_any; warps are then offset by an exclusive scan of
 // the per-warp digit counts seeded with the block's global digit offsets.
 __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(
     const u64* __restrict__ kin, const int* __restrict__ vin, int64_t n, int shift,
-    const int* __restrict__ offs, int nblk, u64* __restrict__ kout, int* __restrict__ vout) {
+    const int* __restrict__ offs, const int* __restrict__ totals, int nblk,
+    u64* __restrict__ kout, int* __restrict__ vout) {
   __shared__ int wh[kRsWarps][kRadix];
+  __shared__ int dbase[kRadix];  // exclusive scan of the digit totals
+  __shared__ int wsum[kRsWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int e = threadIdx.x; e < kRsWarps * kRadix; e += kRsThreads) (&wh[0][0])[e] = 0;
+  {  // thread t owns digits [t * per, (t + 1) * per)
+    constexpr int per = kRadix / kRsThreads;
+    int v[per], sum = 0;
+#pragma unroll
+    for (int j = 0; j < per; ++j) {
+      v[j] = totals[threadIdx.x * per + j];
+      sum += v[j];
+    }
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int run = incl - sum;
+    for (int w = 0; w < warp; ++w) run += wsum[w];
+#pragma unroll
+    for (int j = 0; j < per; ++j) {
+      dbase[threadIdx.x * per + j] = run;
+      run += v[j];
+    }
+  }
   __syncthreads();
   const unsigned lt = (1u << lane) - 1u;
   const int64_t base = (int64_t)blockIdx.x * kRsTile + warp * (kRsTile / kRsWarps);
@@ -253,7 +306,7 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(
   }
   __syncthreads();
   for (int d = threadIdx.x; d < kRadix; d += kRsThreads) {
-    int acc = offs[(int64_t)d * nblk + blockIdx.x];
+    int acc = dbase[d] + offs[(int64_t)d * nblk + blockIdx.x];
     for (int w = 0; w < kRsWarps; ++w) {
       const int t = wh[w][d];
       wh[w][d] = acc;
@@ -407,17 +460,17 @@ static int radix_passes(int clouds) {
 // sorts (k0, v0) using (k1, v1) as the second buffer; returns which buffer
 // holds the result (0 or 1)
 static int radix_sort(u64* k0, int* v0, u64* k1, int* v1, int64_t n, int passes, int* counts,
-                      int* scan_tmp, int nblk, cudaStream_t s) {
+                      int* totals, int nblk, cudaStream_t s) {
   u64* ka[2] = {k0, k1};
   int* va[2] = {v0, v1};
   int cur = 0;
   for (int p = 0; p < passes; ++p) {
     const int shift = p * kRadixBits;
     k_radix_hist<<<nblk, kRsThreads, 0, s>>>(ka[cur], n, shift, counts, nblk);
-    scan_exclusive(counts, (int64_t)kRadix * nblk, scan_tmp, s);
-    k_radix_scatter<<<nblk, kRsThreads, 0, s>>>(ka[cur], va[cur], n, shift, counts, nblk,
+    k_radix_digit_scan<<<kRadix / kDigitWarps, kDigitWarps * 32, 0, s>>>(counts, nblk, totals);
+    k_radix_scatter<<<nblk, kRsThreads, 0, s>>>(ka[cur], va[cur], n, shift, counts, totals, nblk,
                                                 ka[cur ^ 1], va[cur ^ 1]);
-    note_launches(2);
+    note_launches(3);
     cur ^= 1;
   }
   return cur;
@@ -431,7 +484,7 @@ void radix_sort_plan(RadixPlan& p, Workspace& ws, int64_t n) {
   p.o_vals0 = ws.reserve(sizeof(int) * (size_t)(n > 0 ? n : 1));
   p.o_vals1 = ws.reserve(sizeof(int) * (size_t)(n > 0 ? n : 1));
   p.o_counts = ws.reserve(sizeof(int) * (size_t)kRadix * p.blocks);
-  p.o_scan = ws.reserve(sizeof(int) * scan_tmp_ints((int64_t)kRadix * p.blocks));
+  p.o_scan = ws.reserve(sizeof(int) * kRadix);  // digit totals
 }
 
 int radix_sort_pairs(const RadixPlan& p, const Workspace& ws, int bits, cudaStream_t s) {
@@ -459,72 +512,83 @@ __global__ void k_gather_sorted(const u64* __restrict__ keys, const int* __restr
 // ---------------------------------------------------------------------------
 // 5. level choice
 // ---------------------------------------------------------------------------
+// The level comes from the median, over kLevelSamples points spread evenly
+// over the cloud's sorted order, of each point's k-th nearest distance among
+// its 2k Morton neighbours on either side.  The samples are spread over many
+// blocks (one cloud's estimate on one SM took ~39 us); one block per cloud
+// then sorts them and picks the median.
+constexpr int kLevelSamples = 1024;
+constexpr int kLevelBlock = 128;
+
 template <int KMAX>
-__global__ void __launch_bounds__(1024) k_choose_level(GridParams* prm, const float4* __restrict__ pts,
-                                                       int k_default, const int* cloud_k,
-                                                       float cell_size, float cell_scale) {
-  constexpr int S = 1024;
-  __shared__ float est[S];
-  GridParams& P = prm[blockIdx.x];
-  if (cell_size > 0.0f) {  // the edge is given: nothing to estimate
-    if (threadIdx.x == 0) {
-      const float ratio = cell_size / P.fine;
-      int L = ratio <= 1.0f ? 0 : (int)rintf(log2f(ratio));
-      L = max(0, min(L, kFineBits));
-      P.level = L;
-      P.cell = ldexpf(P.fine, L);
-    }
-    return;
-  }
+__global__ void __launch_bounds__(kLevelBlock) k_level_samples(const GridParams* __restrict__ prm,
+                                                               const float4* __restrict__ pts,
+                                                               int k_default,
+                                                               const int* __restrict__ cloud_k,
+                                                               float* __restrict__ est) {
+  const int cloud = blockIdx.y;
+  const GridParams& P = prm[cloud];
   const int n = P.n, s0 = P.start;
-  int k = cloud_k ? cloud_k[blockIdx.x] : k_default;
+  int k = cloud_k ? cloud_k[cloud] : k_default;
   k = max(1, min(k, KMAX));
-  const int ns = min(S, n);
-  {
-    const int s = threadIdx.x;  // one sample per thread
-    float e = __int_as_float(0x7f800000);
-    if (s < ns) {
-      const int pos = s0 + (int)(((int64_t)s * n) / ns);
-      const float4 q = pts[pos];
-      const int W = 2 * k;
-      TopK<KMAX> top;
-      top.init(k);
-      const int j0 = max(s0, pos - W), j1 = min(s0 + n - 1, pos + W);
-      for (int j = j0; j <= j1; ++j) {
-        const float4 p = pts[j];
-        top.push(pack_key(sqdist(p.x, p.y, p.z, q.x, q.y, q.z), j));
-      }
-      if (top.full()) e = top.thr_d2();
+  const int ns = min(kLevelSamples, n);
+  const int s = blockIdx.x * kLevelBlock + threadIdx.x;  // < kLevelSamples
+  float e = __int_as_float(0x7f800000);
+  if (s < ns) {
+    const int pos = s0 + (int)(((int64_t)s * n) / ns);
+    const float4 q = pts[pos];
+    const int W = 2 * k;
+    TopK<KMAX> top;
+    top.init(k);
+    const int j0 = max(s0, pos - W), j1 = min(s0 + n - 1, pos + W);
+    for (int j = j0; j <= j1; ++j) {
+      const float4 p = pts[j];
+      top.push(pack_key(sqdist(p.x, p.y, p.z, q.x, q.y, q.z), j));
     }
-    est[s] = e;
+    if (top.full()) e = top.thr_d2();
   }
-  __syncthreads();
-  // bitonic sort of est[] ascending
-  for (int size = 2; size <= S; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int t = threadIdx.x; t < S / 2; t += blockDim.x) {
-        const int lo = 2 * t - (t & (stride - 1));
-        const int hi = lo + stride;
-        const bool up = ((lo & size) == 0);
-        const float a = est[lo], b = est[hi];
-        if ((a > b) == up) {
-          est[lo] = b;
-          est[hi] = a;
+  est[(int64_t)cloud * kLevelSamples + s] = e;
+}
+
+// Level of each cloud: cell = fine * 2^level, the power of two nearest to
+// cell_size (> 0) or to cell_scale x the median sampled k-th distance.
+__global__ void __launch_bounds__(kLevelSamples) k_level_pick(GridParams* prm,
+                                                              const float* __restrict__ est,
+                                                              float cell_size, float cell_scale) {
+  __shared__ float e[kLevelSamples];
+  GridParams& P = prm[blockIdx.x];
+  float target = cell_size;
+  if (!(cell_size > 0.0f)) {
+    e[threadIdx.x] = est[(int64_t)blockIdx.x * kLevelSamples + threadIdx.x];
+    __syncthreads();
+    // bitonic sort of e[] ascending
+    for (int size = 2; size <= kLevelSamples; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        const int t = threadIdx.x;
+        if (t < kLevelSamples / 2) {
+          const int lo = 2 * t - (t & (stride - 1));
+          const int hi = lo + stride;
+          const bool up = ((lo & size) == 0);
+          const float a = e[lo], b = e[hi];
+          if ((a > b) == up) {
+            e[lo] = b;
+            e[hi] = a;
+          }
         }
+        __syncthreads();
       }
-      __syncthreads();
     }
+    const int ns = min(kLevelSamples, P.n);
+    const float med = ns > 0 ? e[ns / 2] : __int_as_float(0x7f800000);
+    const float R = isfinite(med) ? sqrtf(med) : P.fine * (float)kFineDim;
+    target = (cell_scale > 0.0f ? cell_scale : kDefaultCellScale) * R;
   }
   if (threadIdx.x == 0) {
-    const float fine = P.fine;
-    const float med = ns > 0 ? est[ns / 2] : __int_as_float(0x7f800000);
-    const float R = isfinite(med) ? sqrtf(med) : fine * (float)kFineDim;
-    const float target = (cell_scale > 0.0f ? cell_scale : kDefaultCellScale) * R;
-    const float ratio = target / fine;
+    const float ratio = target / P.fine;
     int L = ratio <= 1.0f ? 0 : (int)rintf(log2f(ratio));
     L = max(0, min(L, kFineBits));
     P.level = L;
-    P.cell = ldexpf(fine, L);
+    P.cell = ldexpf(P.fine, L);
   }
 }
 
@@ -613,13 +677,14 @@ void grid_plan(GridPlan& p, Workspace& ws, int64_t n, int clouds) {
   p.radix_blocks = ceil_div(n > 0 ? n : 1, kRsTile);
   p.o_prm = ws.reserve(sizeof(GridParams) * clouds);
   p.o_pts = ws.reserve(sizeof(float4) * (size_t)(n > 0 ? n : 1));
+  p.o_est = ws.reserve(sizeof(float) * kLevelSamples * (size_t)clouds);
   p.o_tab = ws.reserve(sizeof(CellEntry) * slots);
   p.o_keys0 = ws.reserve(sizeof(u64) * (size_t)(n > 0 ? n : 1));
   p.o_keys1 = ws.reserve(sizeof(u64) * (size_t)(n > 0 ? n : 1));
   p.o_vals0 = ws.reserve(sizeof(int) * (size_t)(n > 0 ? n : 1));
   p.o_vals1 = ws.reserve(sizeof(int) * (size_t)(n > 0 ? n : 1));
   p.o_counts = ws.reserve(sizeof(int) * (size_t)kRadix * p.radix_blocks);
-  p.o_scan = ws.reserve(sizeof(int) * scan_tmp_ints((int64_t)kRadix * p.radix_blocks));
+  p.o_scan = ws.reserve(sizeof(int) * kRadix);  // digit totals
   p.o_starts = 0;
 }
 
@@ -638,7 +703,7 @@ cil_status grid_build(const GridPlan& p, const Workspace& ws, const float* xyz,
   TimedRegion timer("grid_build", s);
   GridParams* prm = ws.at<GridParams>(p.o_prm);
   const int64_t n = p.n;
-  note_launches(n > 0 ? 8 : 2);  // init, bbox, finalize, keys, gather, level, insert, count
+  note_launches(n > 0 ? 8 : 2);  // init, bbox, finalize, keys, gather, level pick, insert, count
   k_init_params<<<ceil_div(p.clouds, 128), 128, 0, s>>>(prm, p.clouds, cloud_start_dev, n);
   if (n > 0) {
     const int64_t threads = (n + 7) / 8;
@@ -663,8 +728,13 @@ cil_status grid_build(const GridPlan& p, const Workspace& ws, const float* xyz,
     float4* pts = ws.at<float4>(p.o_pts);
     k_gather_sorted<<<ceil_div(n, 256), 256, 0, s>>>(ks, vs, n, xyz, prm, pts);
     const int kk = opt.k_est < 1 ? 1 : (opt.k_est > 32 ? 32 : opt.k_est);
-    CIL_FOR_K(kk, (k_choose_level<KM><<<p.clouds, 1024, 0, s>>>(prm, pts, kk, nullptr, opt.cell_size,
-                                                                opt.cell_scale)));
+    float* est = ws.at<float>(p.o_est);
+    if (!(opt.cell_size > 0.0f)) {
+      note_launches(1);
+      const dim3 grid(kLevelSamples / kLevelBlock, p.clouds);
+      CIL_FOR_K(kk, (k_level_samples<KM><<<grid, kLevelBlock, 0, s>>>(prm, pts, kk, nullptr, est)));
+    }
+    k_level_pick<<<p.clouds, kLevelSamples, 0, s>>>(prm, est, opt.cell_size, opt.cell_scale);
     k_cells_insert<<<ceil_div(n, 256), 256, 0, s>>>(ks, n, prm, ws.at<CellEntry>(p.o_tab), p.mask);
     k_cells_count<<<ceil_div(n, 256), 256, 0, s>>>(ks, n, prm, ws.at<CellEntry>(p.o_tab), p.mask);
   }
@@ -679,7 +749,7 @@ void order_plan(OrderPlan& p, Workspace& ws, int64_t n) {
   p.o_vals0 = ws.reserve(sizeof(int) * (size_t)(n > 0 ? n : 1));
   p.o_vals1 = ws.reserve(sizeof(int) * (size_t)(n > 0 ? n : 1));
   p.o_counts = ws.reserve(sizeof(int) * (size_t)kRadix * p.radix_blocks);
-  p.o_scan = ws.reserve(sizeof(int) * scan_tmp_ints((int64_t)kRadix * p.radix_blocks));
+  p.o_scan = ws.reserve(sizeof(int) * kRadix);  // digit totals
 }
 
 cil_status order_queries(const OrderPlan& p, const Workspace& ws, const float* qry,
