@@ -492,7 +492,8 @@ def run_ours(args):
                "kind": "oracle",
                "sample": f"full frame pair, oracle kd-tree route, {q_tot // nt} step(s), "
                          f"{t_tot:.1f} s"}
-        precision = precision_vs_oracle(pair, T_gpu, rep_h, nrm_gpu, knn_gpu, keep)
+        precision = {k: _sig(v) for k, v in
+                     precision_vs_oracle(pair, T_gpu, rep_h, nrm_gpu, knn_gpu, keep).items()}
 
     if rank == 0:
         line = {
@@ -545,10 +546,17 @@ LEARNED_SUMMARY = ("pairs", "pairs_per_s_learned_fallback", "pairs_per_s_identit
                    "pairs_reregistered", "runs")
 
 
+def _sig(x, digits: int = 4):
+    """x rounded to `digits` significant digits (floats only)."""
+    if not isinstance(x, float) or x == 0.0 or not math.isfinite(x):
+        return x
+    return round(x, digits - 1 - int(math.floor(math.log10(abs(x)))))
+
+
 def _summary(rec, keys):
     if rec is None:
         return None
-    return {k: (round(rec[k], 6) if isinstance(rec[k], float) else rec[k]) for k in keys if k in rec}
+    return {k: _sig(rec[k], 6) for k in keys if k in rec}
 
 
 def run_batched(args, rank: int, B: int = 256, runs: int = 5):

@@ -44,8 +44,10 @@ def test_traffic_records_keyed_to_each_kernels_sources(monkeypatch):
 
 def test_summary_keeps_listed_keys_in_order():
     rec = {"a": 1.23456789, "b": 2, "c": "x"}
-    assert bench._summary(rec, ("c", "a", "missing")) == {"c": "x", "a": 1.234568}
+    assert bench._summary(rec, ("c", "a", "missing")) == {"c": "x", "a": 1.23457}
     assert bench._summary(None, ("a",)) is None
+    assert bench._sig(7.756328758e-08) == 7.756e-08 and bench._sig(12983.3246) == 12980.0
+    assert bench._sig(0.0) == 0.0 and bench._sig(3) == 3
 
 
 def test_clock_rejection_rule():
