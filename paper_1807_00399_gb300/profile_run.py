@@ -10,7 +10,9 @@ surface pairs with sizes log-uniform in [2e3, 2e5]), apartment (7.8M points on
 a furnished flat; op segment only).  Ops: register (grid,
 k-NN normals and point-to-plane ICP), knn (self k-NN), normals, radius
 (radius search), icp (ICP alone on library normals, with --metric and
---association), batch (the batched graph run; workload batch only), segment
+--association), batch (the batched graph run; workload batch only), voxel
+(voxel grid of edge --radius), hybrid (k nearest within --radius),
+normals_r (normals over --radius balls), segment
 (5 mm voxel grid, then k = 30 normals and smooth segments with a 2.8 rad
 angle from one search; workload apartment only).  Each op
 runs --repeat times after one warm-up call; the CUDA-event time per call and
@@ -30,7 +32,8 @@ def main(argv=None):
     ap.add_argument("--workload", choices=["surface", "depth", "lidar", "batch", "apartment"],
                     default="depth")
     ap.add_argument("--op", choices=["register", "knn", "normals", "radius", "batch", "icp",
-                                     "segment"], default="register")
+                                     "segment", "voxel", "hybrid", "normals_r"],
+                    default="register")
     ap.add_argument("--iters", type=int, default=30, help="ICP iterations")
     ap.add_argument("--k", type=int, default=0, help="neighbours (default: 16 lidar, else 10)")
     ap.add_argument("--radius", type=float, default=0.5)
@@ -100,6 +103,9 @@ def main(argv=None):
             "normals": lambda: cil.estimate_normals(dst, k, vp, cell_scale=a.cell_scale,
                                                     topk=a.topk),
             "radius": lambda: cil.radius_search(dst, dst, a.radius, cell_scale=a.cell_scale),
+            "voxel": lambda: cil.voxel_downsample(dst, a.radius),
+            "hybrid": lambda: cil.knn_hybrid(dst, dst, k, a.radius),
+            "normals_r": lambda: cil.estimate_normals_radius(dst, a.radius, vp),
         }[a.op]
     L = cil.lib()
     fn()
@@ -117,7 +123,7 @@ def main(argv=None):
     out = {"workload": a.workload, "op": a.op, "k": k, "iters": a.iters, "repeat": a.repeat,
            "ms_per_call": e0.elapsed_time(e1) / a.repeat}
     for name in ("grid_build", "order_queries", "k_knn", "k_normals", "k_icp", "k_radius",
-                 "voxel_downsample", "segment"):
+                 "voxel_downsample", "segment", "k_knn_hybrid", "k_normals_radius"):
         t, c = ctypes.c_double(), ctypes.c_int64()
         L.cil_timing_read(name.encode(), ctypes.byref(t), ctypes.byref(c))
         if c.value:
