@@ -438,12 +438,9 @@ def run_ours(args):
     # the dominant kernel by the ncu launch list is k_icp_search (one launch
     # per ICP round; the ICP loop "k_icp" is 93 launches of three kernels)
     dom = "k_icp_search"
-    alg = {  # algorithmic bytes per launch: what the step must move, per kernel
-        "k_icp_search": 20 * ns + 16 * nt,
-        "k_normals": 40 * nt,
-        "grid_build": 52 * nt + 16 * (1 << math.ceil(math.log2(2 * nt))),
-        "order_queries": 52 * ns,
-    }
+    # algorithmic bytes per launch: 20 B per source point (xyz, order,
+    # correspondence) + 16 B per target point (sorted float4)
+    alg = {"k_icp_search": 20 * ns + 16 * nt}
     traffic = traffic_of(dom)
     achieved = alg[dom] / (per_launch_ms[dom] / 1e3) / 1e9
     roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
