@@ -2,12 +2,18 @@
 // downsamples to 1 cm voxels before ICP).
 //
 // Point i falls in voxel (floor(x/v), floor(y/v), floor(z/v)) with correctly
-// rounded FP32 division; the 63-bit key (21 bits per axis, offset by 2^20) is
-// stable-radix-sorted with the point index, voxel heads are marked and
-// scanned into output slots, and each voxel's mean is accumulated over its run
-// in index order with compensated FP32 sums (deterministic).  Output voxels
-// ascend by (ix, iy, iz).
+// rounded FP32 division (clamped to 21 bits per axis).  A first pass finds the
+// occupied range of each voxel coordinate; the key packs the coordinates'
+// offsets from the range's low corner in just the bits their spans need
+// (x highest), so it orders voxels by (ix, iy, iz) and the stable radix sort
+// with the point index takes only ceil(bits / 10) passes (3 for a 1 cm grid
+// of a depth frame instead of 7 for the full 63 bits).  Voxel heads are
+// marked and scanned into output slots, and each voxel's mean is accumulated
+// over its run in index order with compensated FP32 sums (deterministic).
+// Output voxels ascend by (ix, iy, iz).
 #include <math.h>
+
+#include <algorithm>
 
 #include "cil_host.h"
 #include "cil_kernels.h"
@@ -16,20 +22,59 @@ namespace cil {
 
 constexpr int kVoxBias = 1 << 20;
 
-__global__ void k_voxel_keys(const float* __restrict__ xyz, int64_t n, float v,
-                             u64* __restrict__ keys, int* __restrict__ vals) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  u64 key = 0;
+// voxel coordinate of x, biased into [0, 2^21)
+__device__ __forceinline__ int voxel_coord(float x, float v) {
+  float f = floorf(__fdiv_rn(x, v));
+  f = fminf(fmaxf(f, -(float)kVoxBias), (float)(kVoxBias - 1));  // NaN -> lower bound
+  return (int)f + kVoxBias;
+}
+
+// Occupied range of the biased coordinates: ext[a] = max (2^21 - 1 - c_a)
+// (the low corner, kept as a maximum) and ext[3 + a] = max c_a; ext starts
+// zeroed, every value is in [0, 2^21).
+__global__ void __launch_bounds__(256) k_voxel_range(const float* __restrict__ xyz, int64_t n,
+                                                     float v, int* __restrict__ ext) {
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int c = voxel_coord(xyz[3 * i + a], v);
+      lo[a] = max(lo[a], (2 * kVoxBias - 1) - c);
+      hi[a] = max(hi[a], c);
+    }
+  }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    float f = floorf(__fdiv_rn(xyz[3 * i + a], v));
-    f = fminf(fmaxf(f, -(float)kVoxBias), (float)(kVoxBias - 1));  // NaN -> lower bound
-    const u64 c = (u64)(long long)((int)f + kVoxBias);
-    key = (key << 21) | c;
+    lo[a] = (int)__reduce_max_sync(0xffffffffu, (unsigned)lo[a]);
+    hi[a] = (int)__reduce_max_sync(0xffffffffu, (unsigned)hi[a]);
   }
-  keys[i] = key;
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      atomicMax(ext + a, lo[a]);
+      atomicMax(ext + 3 + a, hi[a]);
+    }
+  }
+}
+
+// key = (cx - lo_x) << (by + bz) | (cy - lo_y) << bz | (cz - lo_z)
+__global__ void k_voxel_keys(const float* __restrict__ xyz, int64_t n, float v, int lx, int ly,
+                             int lz, int by, int bz, u64* __restrict__ keys, int* __restrict__ vals) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const u64 cx = (u64)(voxel_coord(xyz[3 * i], v) - lx);
+  const u64 cy = (u64)(voxel_coord(xyz[3 * i + 1], v) - ly);
+  const u64 cz = (u64)(voxel_coord(xyz[3 * i + 2], v) - lz);
+  keys[i] = (cx << (by + bz)) | (cy << bz) | cz;
   vals[i] = (int)i;
+}
+
+// bits that hold 0 .. span - 1
+static int span_bits(int span) {
+  int b = 0;
+  while ((1 << b) < span) ++b;
+  return b;
 }
 
 __global__ void k_voxel_heads(const u64* __restrict__ keys, int64_t n, int* __restrict__ head) {
@@ -88,12 +133,27 @@ extern "C" cil_status cil_voxel_downsample(const float* xyz, int64_t n, float vo
   radix_sort_plan(rp, ws, n);
   const size_t o_head = ws.reserve(sizeof(int) * (size_t)(n + 1));
   const size_t o_tmp = ws.reserve(sizeof(int) * scan_tmp_ints(n + 1));
+  const size_t o_ext = ws.reserve(sizeof(int) * 6);
   if ((st = ws.allocate(ctx, s)) != CIL_OK) return st;
   TimedRegion timer("voxel_downsample", s);
-  note_launches(3);
-  k_voxel_keys<<<ceil_div(n, 256), 256, 0, s>>>(xyz, n, voxel, ws.at<u64>(rp.o_keys0),
+  note_launches(4);
+  int* ext = ws.at<int>(o_ext);
+  if (cudaMemsetAsync(ext, 0, sizeof(int) * 6, s) != cudaSuccess) return CIL_ERR_CUDA;
+  const int rblocks = std::max(1, std::min(ceil_div(n, 256), 8 * ctx->num_sms));
+  k_voxel_range<<<rblocks, 256, 0, s>>>(xyz, n, voxel, ext);
+  int e[6];
+  if (cudaMemcpyAsync(e, ext, sizeof(e), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return CIL_ERR_CUDA;
+  int lo[3], bits[3];
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = (2 * kVoxBias - 1) - e[a];
+    bits[a] = span_bits(e[3 + a] - lo[a] + 1);
+  }
+  k_voxel_keys<<<ceil_div(n, 256), 256, 0, s>>>(xyz, n, voxel, lo[0], lo[1], lo[2], bits[1],
+                                                 bits[2], ws.at<u64>(rp.o_keys0),
                                                  ws.at<int>(rp.o_vals0));
-  const int which = radix_sort_pairs(rp, ws, 63, s);
+  const int which = radix_sort_pairs(rp, ws, bits[0] + bits[1] + bits[2], s);
   const u64* keys = ws.at<u64>(which ? rp.o_keys1 : rp.o_keys0);
   const int* vals = ws.at<int>(which ? rp.o_vals1 : rp.o_vals0);
   int* head = ws.at<int>(o_head);

@@ -43,3 +43,18 @@ def test_lattice_and_single_voxel():
     torch.cuda.synchronize()
     assert gc.cpu().tolist() == [64]
     np.testing.assert_allclose(g.cpu().numpy()[0], [0.75, 0.75, 0.75], atol=1e-7)
+
+
+def test_wide_and_flat_spans():
+    """Keys packed in the bits the occupied span needs: x spans the whole
+    21-bit coordinate range, y a small one, z one voxel (no bits)."""
+    rng = np.random.default_rng(11)
+    xs = np.array([-1048575.5, -4.5, 0.5, 7.5, 1048574.5], np.float32)
+    n = 4000
+    pts = np.stack([rng.choice(xs, n), rng.uniform(-100.0, 100.0, n),
+                    np.full(n, 0.25)], axis=1).astype(np.float32)
+    g, gc = cil.voxel_downsample(torch.from_numpy(pts).cuda(), 1.0)
+    torch.cuda.synchronize()
+    o, oc = oracle.voxel_downsample(pts, 1.0)
+    assert np.array_equal(gc.cpu().numpy(), oc)
+    assert np.all(np.abs(g.cpu().numpy() - o) <= 1e-6 * np.abs(pts).max(axis=0))
