@@ -4,16 +4,18 @@
 // Every round of every pair runs as three launches over tiles of kIcpThreads
 // source points (all pairs' tiles together in batched mode):
 //   k_icp_search      p' = R p + t (FP32); a query whose previous neighbour
-//                     is certified unchanged keeps it, the others run the
-//                     first stage of the exact nearest-neighbour search within
-//                     the rejection distance (the query's cell, then the cells
-//                     of its 3x3x3 block meeting the ball of the best distance
-//                     so far); queries whose ball leaves the block go to a
-//                     queue;
-//   k_icp_finish      each queued query is finished by one whole warp: the
-//                     cells of the directory level meeting its ball are looked
-//                     up by the lanes in parallel and their points scanned
-//                     with the lanes splitting them;
+//                     (or lack of one) is certified unchanged keeps it, the
+//                     others run the first stage of the exact nearest-neighbour
+//                     search within the rejection distance (the query's cell,
+//                     then the cells of its 3x3x3 block meeting the ball of the
+//                     best distance so far; in a tile with few such queries, a
+//                     warp per query scanning the block's cells in parallel);
+//                     queries whose ball leaves the block go to a queue;
+//   k_icp_finish      each queued query is finished by one whole warp (one
+//                     lane per query for long queues): the cells of the
+//                     directory level meeting its ball are looked up by the
+//                     lanes in parallel and their points scanned with the
+//                     lanes splitting them;
 //   k_icp_accumulate  for each correspondence n = normal of q, r = n.(p' - q),
 //                     J = [p' x n, n]; the tile's sums H = sum J J^T (21),
 //                     g = sum J r (6), sum r^2 in a fixed compensated order;
@@ -130,23 +132,21 @@ __device__ __forceinline__ void escalate_rings(const GridView& g, int cloud, con
   }
 }
 
-// scan_cell that also keeps the second smallest squared distance within
-// dmax2 (best2)
+// scan_cell that also keeps the smallest squared distance of the other
+// points (best2), within dmax2 or not
 __device__ __forceinline__ void scan_cell2(const GridView& g, int s, int n, const float q[3],
                                            float dmax2, u64& best, int& bj, float& lim,
                                            float& best2) {
   for_points(g.pts, s, n, [&](const float4& p, int j) {
     const float d2 = sqdist(p.x, p.y, p.z, q[0], q[1], q[2]);
-    if (d2 <= dmax2) {
-      const u64 key = pack_key(d2, __float_as_int(p.w));
-      if (key < best) {
-        if (best != kEmptyKey) best2 = fminf(best2, key_d2(best));
-        best = key;
-        bj = j;
-        lim = fminf(lim, d2);
-      } else {
-        best2 = fminf(best2, d2);
-      }
+    const u64 key = pack_key(d2, __float_as_int(p.w));
+    if (d2 <= dmax2 && key < best) {
+      if (best != kEmptyKey) best2 = fminf(best2, key_d2(best));
+      best = key;
+      bj = j;
+      lim = fminf(lim, d2);
+    } else {
+      best2 = fminf(best2, d2);
     }
   });
 }
@@ -159,8 +159,9 @@ __device__ __forceinline__ void scan_cell2(const GridView& g, int s, int n, cons
 // sorted position (-1: none) and min(dmax2, best d^2) of the best point.
 // With kBound, lb2 (when exact): a lower bound on the squared distance from
 // q to every target point but the best -- the second best seen, the cells
-// skipped or outside the searched box (by their padded ranges), the space
-// outside the block and dmax2, whichever is least.
+// skipped or outside the searched box (by their padded ranges) and the space
+// outside the block, whichever is least (not capped at dmax2, so an outlier
+// gets a bound beyond it).
 template <bool kBound>
 __device__ __forceinline__ bool base_search(const GridView& g, int cloud, const float q[3],
                                             float dmax2, u64& best, int& bj, float& lim,
@@ -170,7 +171,7 @@ __device__ __forceinline__ bool base_search(const GridView& g, int cloud, const 
   best = kEmptyKey;
   bj = -1;
   lim = dmax2;
-  lb2 = dmax2;
+  lb2 = __int_as_float(0x7f800000);
   CellFrame f;
   f.load(P, cloud);
   const int c[3] = {f.cell_of(q[0], 0, inv_fine), f.cell_of(q[1], 1, inv_fine),
@@ -217,6 +218,69 @@ __device__ __forceinline__ bool base_search(const GridView& g, int cloud, const 
   const int e1[3] = {c[0] + 1, c[1] + 1, c[2] + 1};
   const float out2 = f.unexplored_d2(q, e0, e1);
   if (kBound) lb2 = fminf(lb2, out2);
+  return out2 * (1.0f - 1e-6f) > lim;
+}
+
+// Warp-wide form of the first stage for one query (all arguments
+// warp-uniform), for tiles with few unsettled queries: the 27 cells of the
+// query's 3x3x3 block are looked up by 27 lanes in parallel and each scanned
+// whole; a cell farther than the rejection distance is not scanned and
+// bounds instead.  best / lim as base_search, and the same return (exact when
+// the block holds every point nearer than the best).  lb2: a lower bound on
+// the squared distance from q to every target point but the best -- the
+// second smallest squared distance in the scanned cells, the ranges of the
+// cells not scanned and the space outside the block, whichever is least.
+// Not capped at the rejection distance, so an outlier gets a bound beyond it.
+__device__ bool warp_block_search(const GridView& g, int cloud, const float q[3], float dmax2,
+                                  int lane, u64& best, float& lim, float& lb2) {
+  const unsigned FULL = 0xffffffffu;
+  const GridParams& P = g.prm[cloud];
+  const float inv_fine = P.inv_fine;
+  CellFrame f;
+  f.load(P, cloud);
+  const int c[3] = {f.cell_of(q[0], 0, inv_fine), f.cell_of(q[1], 1, inv_fine),
+                    f.cell_of(q[2], 2, inv_fine)};
+  u64 mine = kEmptyKey;                   // this lane's nearest within dmax2
+  float sec = __int_as_float(0x7f800000);  // its other points (and skipped range)
+  if (lane < 27) {
+    const int x = c[0] + lane % 3 - 1, y = c[1] + (lane / 3) % 3 - 1, z = c[2] + lane / 9 - 1;
+    if (x >= 0 && x <= f.hi[0] && y >= 0 && y <= f.hi[1] && z >= 0 && z <= f.hi[2]) {
+      const int c3[3] = {x, y, z};
+      const float rd2 = f.range_d2(q, c3, c3);
+      int s, n;
+      if (rd2 * (1.0f - 1e-6f) > dmax2) {
+        sec = rd2;
+      } else if (cell_lookup(g, cell_key(f.level, cloud, x, y, z), s, n)) {
+        for_points(g.pts, s, n, [&](const float4& p, int) {
+          const float d2 = sqdist(p.x, p.y, p.z, q[0], q[1], q[2]);
+          const u64 key = pack_key(d2, __float_as_int(p.w));
+          if (d2 <= dmax2 && key < mine) {
+            if (mine != kEmptyKey) sec = fminf(sec, key_d2(mine));
+            mine = key;
+          } else {
+            sec = fminf(sec, d2);
+          }
+        });
+      }
+    }
+  }
+  u64 w = mine;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const u64 o = ((u64)__shfl_xor_sync(FULL, (unsigned)(w >> 32), off) << 32) |
+                  __shfl_xor_sync(FULL, (unsigned)w, off);
+    w = o < w ? o : w;
+  }
+  // a lane whose nearest lost adds it to the other points
+  float s2 = (mine != kEmptyKey && mine != w) ? fminf(sec, key_d2(mine)) : sec;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s2 = fminf(s2, __shfl_xor_sync(FULL, s2, off));
+  best = w;
+  lim = w == kEmptyKey ? dmax2 : fminf(dmax2, key_d2(w));
+  const int e0[3] = {c[0] - 1, c[1] - 1, c[2] - 1};
+  const int e1[3] = {c[0] + 1, c[1] + 1, c[2] + 1};
+  const float out2 = f.unexplored_d2(q, e0, e1);
+  lb2 = fminf(s2, out2);
   return out2 * (1.0f - 1e-6f) > lim;
 }
 
@@ -935,13 +999,21 @@ __device__ __forceinline__ int projective_match(const IcpArgs& a, int dst_start,
 // delta < lb, delta = |p' - p0| (1 + 1e-5): every other point is at least
 // lb - delta from p', more than |p' - q| by a relative margin far above the
 // FP32 rounding of squared distances, so the exact search would return q
-// too.  Converged rounds move points by micrometres, so most queries are
-// settled that way; the rest are packed onto the block's first threads for
-// the full first stage (whose lanes then do similar work).  The full search
-// records the bound for the next round only for a query that moved less
-// than kCertMove cell edges in this round (one that moves more would rarely
-// certify next round, and the bound costs registers and instructions).
+// too.  A query whose previous round found no point within the rejection
+// distance, with every target point at least lb from p0, keeps none when
+// lb - delta > dmax (1 + 1e-5).  Converged rounds move points by
+// micrometres, so most queries are settled that way; the rest are packed
+// onto the block's first threads for the full first stage (whose lanes then
+// do similar work), or, when few are left, searched a warp per query.  The
+// full search records the bound for the next round only for a query that
+// moved less than kCertMove cell edges in this round (one that moves more
+// would rarely certify next round, and the bound costs registers and
+// instructions).
 constexpr float kCertMove = 0.1f;
+// Tiles with at most this many unsettled queries search them a warp per
+// query (warp_block_search: latency of one cell lookup instead of a chain of
+// them, and a bound from the whole block); more go one per thread.
+constexpr int kWarpStage = 32;
 __global__ void __launch_bounds__(kIcpThreads, 4) k_icp_search(IcpArgs a, int round) {
   __shared__ float s_Rt[12], s_Rp[12];
   __shared__ float s_dmax2, s_move;
@@ -1000,6 +1072,11 @@ __global__ void __launch_bounds__(kIcpThreads, 4) k_icp_search(IcpArgs a, int ro
           a.corr[pos] = in ? j : -1;
           a.lbd[pos] = in ? lb - delta : 0.0f;
         }
+      } else if (j < 0 && lb - delta > sqrtf(dmax2) * (1.0f + 1e-5f)) {
+        // no target point within lb of p0, so none within lb - delta of p',
+        // which is beyond the rejection distance: still no correspondence
+        todo = false;
+        a.lbd[pos] = lb - delta;
       }
     }
   }
@@ -1015,11 +1092,30 @@ __global__ void __launch_bounds__(kIcpThreads, 4) k_icp_search(IcpArgs a, int ro
   }
   if (todo) s_list[off + __popc(m & ((1u << lane) - 1u))] = want_lb ? (pos | (1 << 31)) : pos;
   __syncthreads();
-  bool queued = false;
+  if (cnt <= kWarpStage && a.opt.association != CIL_ASSOC_PROJECTIVE) {
+    // few unsettled queries: a warp per query, the block's cells in parallel
+    for (int t = warp; t < cnt; t += kIcpWarps) {
+      const int e = s_list[t];
+      const int qp = e & 0x7fffffff;
+      float p[3];
+      transformed_source(a, s_Rt, qp, p);
+      u64 best;
+      float lim, lb2;
+      const bool exact = warp_block_search(a.g, b, p, dmax2, lane, best, lim, lb2);
+      if (lane == 0) {
+        const int j = best == kEmptyKey ? -1 : dst_start + key_idx(best);
+        a.corr[qp] = j;
+        a.lbd[qp] = (e < 0 && exact) ? sqrtf(lb2) * (1.0f - 1e-5f) : 0.0f;
+        if (!exact) a.queue[atomicAdd(a.qcount + (round & 1), 1u)] = make_int2(e, b);
+      }
+    }
+    return;
+  }
+  bool queued = false, bound = false;
   int qpos = 0;
   if (tid < cnt) {
     const int e = s_list[tid];
-    const bool bound = e < 0;
+    bound = e < 0;
     qpos = e & 0x7fffffff;
     float p[3];
     transformed_source(a, s_Rt, qpos, p);
@@ -1035,7 +1131,7 @@ __global__ void __launch_bounds__(kIcpThreads, 4) k_icp_search(IcpArgs a, int ro
                      : !base_search<false>(a.g, b, p, dmax2, best, bj, lim, lb2);
       // final, or stage one's best for k_icp_finish
       j = best == kEmptyKey ? -1 : dst_start + key_idx(best);
-      if (bound && !queued && j >= 0) lb = sqrtf(lb2) * (1.0f - 1e-5f);
+      if (bound && !queued) lb = sqrtf(lb2) * (1.0f - 1e-5f);
     }
     a.corr[qpos] = j;
     a.lbd[qpos] = lb;
@@ -1046,15 +1142,30 @@ __global__ void __launch_bounds__(kIcpThreads, 4) k_icp_search(IcpArgs a, int ro
     unsigned base = 0;
     if (lane == __ffs(mq) - 1) base = atomicAdd(a.qcount + (round & 1), (unsigned)__popc(mq));
     base = __shfl_sync(0xffffffffu, base, __ffs(mq) - 1);
-    if (queued) a.queue[base + __popc(mq & ((1u << lane) - 1u))] = make_int2(qpos, b);
+    if (queued)
+      a.queue[base + __popc(mq & ((1u << lane) - 1u))] =
+          make_int2(bound ? (int)((unsigned)qpos | 0x80000000u) : qpos, b);
   }
 }
 
-// Stage one's result for the queued query at sorted source position pos of
-// pair b: p', the best point so far and the query's base-level cell.
-__device__ __forceinline__ void queued_query(const IcpArgs& a, int pos, int b, float q[3],
-                                             float& dmax2, u64& best, int& bj, float& lim,
-                                             int c[3]) {
+// Outlier bound: a queued query that asked for a bound and whose first stage
+// found no point within the rejection distance is searched out to
+// kEmptyGrow times that distance, so that the result (no point, or the
+// nearest one beyond the rejection distance) bounds its distance to every
+// target point with a margin that certifies it as an outlier in the next
+// rounds.
+constexpr float kEmptyGrow2 = 1.5625f;  // 1.25^2
+
+// Stage one's result for the queued query (sorted source position pos of
+// pair b, `bound` as stage one queued it): p', the rejection distance dmax2,
+// the squared search radius ds2, the best point so far and the base-level
+// cell c whose 3x3x3 block stage one searched.  grow: ds2 is the outlier
+// bound's radius; stage one kept no point beyond the rejection distance, so
+// the block is searched again (c lies outside the grid, which no cell skip
+// matches).
+__device__ __forceinline__ void queued_query(const IcpArgs& a, int pos, int b, bool bound,
+                                             float q[3], float& dmax2, float& ds2, u64& best,
+                                             int& bj, float& lim, int c[3], bool& grow) {
   float Rt[12];
 #pragma unroll
   for (int j = 0; j < 12; ++j) Rt[j] = a.st[b].Rt[j];
@@ -1063,7 +1174,9 @@ __device__ __forceinline__ void queued_query(const IcpArgs& a, int pos, int b, f
   const int j = a.corr[pos];
   bj = -1;
   best = kEmptyKey;
-  lim = dmax2;
+  grow = bound && j < 0;
+  ds2 = grow ? dmax2 * kEmptyGrow2 : dmax2;
+  lim = ds2;
   if (j >= 0) {
     lim = sqdist(__ldg(a.dst + 3 * (int64_t)j), __ldg(a.dst + 3 * (int64_t)j + 1),
                  __ldg(a.dst + 3 * (int64_t)j + 2), q[0], q[1], q[2]);
@@ -1072,9 +1185,20 @@ __device__ __forceinline__ void queued_query(const IcpArgs& a, int pos, int b, f
   const GridParams& P = a.g.prm[b];
   CellFrame f;
   f.load(P, b);
-  c[0] = f.cell_of(q[0], 0, P.inv_fine);
-  c[1] = f.cell_of(q[1], 1, P.inv_fine);
-  c[2] = f.cell_of(q[2], 2, P.inv_fine);
+  c[0] = grow ? -2 : f.cell_of(q[0], 0, P.inv_fine);
+  c[1] = grow ? -2 : f.cell_of(q[1], 1, P.inv_fine);
+  c[2] = grow ? -2 : f.cell_of(q[2], 2, P.inv_fine);
+}
+
+// The queued query's correspondence (the best point when within the
+// rejection distance) and, for a grown search that found none, the bound on
+// its distance to every target point: the nearest point found beyond the
+// rejection distance, else the search radius (FP32 margins as in stage one).
+__device__ __forceinline__ void queued_result(const IcpArgs& a, int pos, int b, float dmax2,
+                                              float ds2, u64 best, bool grow) {
+  const bool in = best != kEmptyKey && key_d2(best) <= dmax2;
+  a.corr[pos] = in ? a.g.prm[b].start + key_idx(best) : -1;
+  if (grow && !in) a.lbd[pos] = sqrtf(best == kEmptyKey ? ds2 : key_d2(best)) * (1.0f - 1e-5f);
 }
 
 // Stage two of round `round`.  A short queue (converged rounds: outliers
@@ -1100,13 +1224,15 @@ __global__ void __launch_bounds__(kIcpThreads) k_icp_finish(IcpArgs a, int round
       const unsigned item = base + lane;
       if (item < total) {
         const int2 e = a.queue[item];
-        float q[3], dmax2, lim;
+        const int pos = e.x & 0x7fffffff;
+        float q[3], dmax2, ds2, lim;
         u64 best;
         int bj, c[3];
-        queued_query(a, e.x, e.y, q, dmax2, best, bj, lim, c);
-        if (!lane_directory(a.g, e.y, q, dmax2, c, best, bj, lim))
-          escalate_rings(a.g, e.y, q, dmax2, best, bj, lim);
-        a.corr[e.x] = best == kEmptyKey ? -1 : a.g.prm[e.y].start + key_idx(best);
+        bool grow;
+        queued_query(a, pos, e.y, e.x < 0, q, dmax2, ds2, best, bj, lim, c, grow);
+        if (!lane_directory(a.g, e.y, q, ds2, c, best, bj, lim))
+          escalate_rings(a.g, e.y, q, ds2, best, bj, lim);
+        queued_result(a, pos, e.y, dmax2, ds2, best, grow);
       }
     }
     return;
@@ -1117,16 +1243,18 @@ __global__ void __launch_bounds__(kIcpThreads) k_icp_finish(IcpArgs a, int round
     item = __shfl_sync(FULL, item, 0);
     if (item >= total) break;
     const int2 e = a.queue[item];
-    float q[3], dmax2, lim;
+    const int pos = e.x & 0x7fffffff;
+    float q[3], dmax2, ds2, lim;
     u64 best;
     int bj, c[3];
-    queued_query(a, e.x, e.y, q, dmax2, best, bj, lim, c);
-    if (!warp_directory(a.g, e.y, q, dmax2, c, best, bj, lim, lane, sh_start[warp],
+    bool grow;
+    queued_query(a, pos, e.y, e.x < 0, q, dmax2, ds2, best, bj, lim, c, grow);
+    if (!warp_directory(a.g, e.y, q, ds2, c, best, bj, lim, lane, sh_start[warp],
                         sh_incl[warp])) {
       // a ball spanning many directory cells (large rejection distance)
-      if (lane == 0) escalate_rings(a.g, e.y, q, dmax2, best, bj, lim);
+      if (lane == 0) escalate_rings(a.g, e.y, q, ds2, best, bj, lim);
     }
-    if (lane == 0) a.corr[e.x] = best == kEmptyKey ? -1 : a.g.prm[e.y].start + key_idx(best);
+    if (lane == 0) queued_result(a, pos, e.y, dmax2, ds2, best, grow);
     __syncwarp();
   }
 }
