@@ -340,8 +340,12 @@ __device__ __forceinline__ bool lane_directory(const GridView& g, int cloud, con
 }
 
 // Warp-wide minimum of the lanes' (key, position) candidates merged into the
-// warp-uniform (best, bj, lim).
-__device__ __forceinline__ void warp_merge(u64 mine, int mj, u64& best, int& bj, float& lim) {
+// warp-uniform (best, bj, lim).  With kBound, sec (per lane) also receives
+// every candidate that is not the new best: the lane's own when it lost, and
+// the replaced best.
+template <bool kBound = false>
+__device__ __forceinline__ void warp_merge(u64 mine, int mj, u64& best, int& bj, float& lim,
+                                           float& sec) {
   u64 w = mine;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -350,11 +354,13 @@ __device__ __forceinline__ void warp_merge(u64 mine, int mj, u64& best, int& bj,
     w = o < w ? o : w;
   }
   if (w < best) {
+    if (kBound && best != kEmptyKey) sec = fminf(sec, key_d2(best));
     const unsigned who = __ballot_sync(0xffffffffu, mine == w);
     bj = __shfl_sync(0xffffffffu, mj, __ffs(who) - 1);
     best = w;
     lim = fminf(lim, key_d2(w));
   }
+  if (kBound && mine != kEmptyKey && mine != best) sec = fminf(sec, key_d2(mine));
 }
 
 // Second stage for one query whose ball of radius sqrt(lim) leaves the 3x3x3
@@ -370,9 +376,17 @@ __device__ __forceinline__ void warp_merge(u64 mine, int mj, u64& best, int& bj,
 // more than kDirCells directory cells.  Exact: every cell meeting the ball
 // is searched (the stage's result is the minimum over a superset of the
 // ball's points).
+// kBound: the searched ball has kFinishGrow times the radius (cells are
+// pruned against it), nothing is skipped as searched by the caller, and lb2
+// receives a lower bound on the squared distance from q to every target
+// point but the best: the smallest squared distance of the other points
+// scanned, the ranges of the cells pruned, and the space outside the
+// directory box and outside the base-level box inside large cells.
+constexpr float kFinishGrow = 1.25f;
+template <bool kBound>
 __device__ bool warp_directory(const GridView& g, int cloud, const float q[3], float dmax2,
                                const int c[3], u64& best, int& bj, float& lim, int lane,
-                               int* sh_start, int* sh_incl) {
+                               int* sh_start, int* sh_incl, float& lb2) {
   const unsigned FULL = 0xffffffffu;
   const GridParams& P = g.prm[cloud];
   const float inv_fine = P.inv_fine;
@@ -381,7 +395,8 @@ __device__ bool warp_directory(const GridView& g, int cloud, const float q[3], f
   const int Lc = min(f.level + kDirLevels, kFineBits);
   CellFrame fc;
   fc.load_level(P, cloud, Lc, ldexpf(P.fine, Lc));
-  const float rad = fmaf(sqrtf(lim), 1.0f + 1e-6f, f.eps);
+  const float grow = kBound ? kFinishGrow : 1.0f + 1e-6f;
+  const float rad = fmaf(sqrtf(lim), grow, f.eps);
   int clo[3], chi[3], blo[3], bhi[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -393,6 +408,9 @@ __device__ bool warp_directory(const GridView& g, int cloud, const float q[3], f
   const int dx = chi[0] - clo[0] + 1, dy = chi[1] - clo[1] + 1, dz = chi[2] - clo[2] + 1;
   const int ncell = dx * dy * dz;
   if (ncell > kDirCells) return false;
+  // squared pruning radius for the current lim
+  auto prune2 = [&](float l) { return kBound ? l * (kFinishGrow * kFinishGrow) : l; };
+  float sec = __int_as_float(0x7f800000);  // kBound: this lane's share of lb2
   const int sh = Lc - f.level;
   for (int base = 0; base < ncell; base += 32) {
     const int t = base + lane;
@@ -403,8 +421,10 @@ __device__ bool warp_directory(const GridView& g, int cloud, const float q[3], f
       Y = clo[1] + (t / dx) % dy;
       Z = clo[2] + t / (dx * dy);
       const int C3[3] = {X, Y, Z};
-      if (fc.range_d2(q, C3, C3) * (1.0f - 1e-6f) <= lim &&
-          cell_lookup(g, cell_key(Lc, cloud, X, Y, Z), s, n) && n > 0) {
+      const float cr2 = fc.range_d2(q, C3, C3);
+      if (cr2 * (1.0f - 1e-6f) > prune2(lim)) {
+        if (kBound) sec = fminf(sec, cr2);
+      } else if (cell_lookup(g, cell_key(Lc, cloud, X, Y, Z), s, n) && n > 0) {
         const int nb = (min(((X + 1) << sh) - 1, bhi[0]) - max(X << sh, blo[0]) + 1) *
                        (min(((Y + 1) << sh) - 1, bhi[1]) - max(Y << sh, blo[1]) + 1) *
                        (min(((Z + 1) << sh) - 1, bhi[2]) - max(Z << sh, blo[2]) + 1);
@@ -451,15 +471,19 @@ __device__ bool warp_directory(const GridView& g, int cloud, const float q[3], f
         const float d2 = sqdist(p2[h].x, p2[h].y, p2[h].z, q[0], q[1], q[2]);
         const u64 key = pack_key(d2, __float_as_int(p2[h].w));
         if (d2 <= dmax2 && key < mine) {
+          if (kBound && mine != kEmptyKey) sec = fminf(sec, key_d2(mine));
           mine = key;
           mj = j2[h];
+        } else if (kBound) {
+          sec = fminf(sec, d2);
         }
       }
     }
     __syncwarp();
-    warp_merge(mine, mj, best, bj, lim);
+    warp_merge<kBound>(mine, mj, best, bj, lim, sec);
     // large cells, one after another: their base-level cells meeting the
-    // ball, one per lane (the query's own block was searched in stage one)
+    // ball, one per lane (the query's own block was searched in stage one,
+    // unless c lies outside the grid)
     unsigned m = __ballot_sync(FULL, large);
     while (m) {
       const int src = __ffs(m) - 1;
@@ -477,13 +501,29 @@ __device__ bool warp_directory(const GridView& g, int cloud, const float q[3], f
         const int x = xl + u % nx, y = yl + (u / nx) % ny, z = zl + u / (nx * ny);
         if (abs(x - c[0]) <= 1 && abs(y - c[1]) <= 1 && abs(z - c[2]) <= 1) continue;
         const int c3[3] = {x, y, z};
-        if (f.range_d2(q, c3, c3) * (1.0f - 1e-6f) > mlim) continue;
+        const float br2 = f.range_d2(q, c3, c3);
+        if (br2 * (1.0f - 1e-6f) > prune2(mlim)) {
+          if (kBound) sec = fminf(sec, br2);
+          continue;
+        }
         int s2, n2;
-        if (cell_lookup(g, cell_key(f.level, cloud, x, y, z), s2, n2))
-          scan_cell(g, s2, n2, q, dmax2, mb, mbj, mlim);
+        if (cell_lookup(g, cell_key(f.level, cloud, x, y, z), s2, n2)) {
+          if (kBound) {
+            float b2 = __int_as_float(0x7f800000);
+            scan_cell2(g, s2, n2, q, dmax2, mb, mbj, mlim, b2);
+            sec = fminf(sec, b2);
+          } else {
+            scan_cell(g, s2, n2, q, dmax2, mb, mbj, mlim);
+          }
+        }
       }
-      warp_merge(mb, mbj, best, bj, lim);
+      warp_merge<kBound>(mb, mbj, best, bj, lim, sec);
     }
+  }
+  if (kBound) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sec = fminf(sec, __shfl_xor_sync(FULL, sec, off));
+    lb2 = fminf(sec, fminf(fc.unexplored_d2(q, clo, chi), f.unexplored_d2(q, blo, bhi)));
   }
   return true;
 }
@@ -1148,12 +1188,13 @@ __global__ void __launch_bounds__(kIcpThreads, 4) k_icp_search(IcpArgs a, int ro
   }
 }
 
-// Outlier bound: a queued query that asked for a bound and whose first stage
-// found no point within the rejection distance is searched out to
-// kEmptyGrow times that distance, so that the result (no point, or the
-// nearest one beyond the rejection distance) bounds its distance to every
-// target point with a margin that certifies it as an outlier in the next
-// rounds.
+// Outlier bound of a long queue (one query per lane): a queued query that
+// asked for a bound and whose first stage found no point within the
+// rejection distance is searched out to kEmptyGrow times that distance, so
+// that the result (no point, or the nearest one beyond the rejection
+// distance) bounds its distance to every target point with a margin that
+// certifies it as an outlier in the next rounds.  (A short queue's
+// warp-wide search bounds every query that asked, warp_directory<true>.)
 constexpr float kEmptyGrow2 = 1.5625f;  // 1.25^2
 
 // Stage one's result for the queued query (sorted source position pos of
@@ -1202,11 +1243,13 @@ __device__ __forceinline__ void queued_result(const IcpArgs& a, int pos, int b, 
 }
 
 // Stage two of round `round`.  A short queue (converged rounds: outliers
-// and points far from the surface) is worked by whole warps, one query at a
-// time, which minimises the time until the last query is done.  A queue with
-// more than kLaneQueue queries per warp (the first rounds, large batches)
-// gives each lane its own query, which maximises throughput.
-constexpr int kLaneQueue = 16;
+// and points far from the surface; the first round of a single pair) is
+// worked by whole warps, one query at a time, which minimises the time until
+// the last query is done; a query that asked for a bound gets one, so that
+// it is certified, not queued again, in the next rounds.  A queue with more
+// than kLaneQueue queries per warp (the first rounds of large batches) gives
+// each lane its own query, which maximises throughput.
+constexpr int kLaneQueue = 32;
 __global__ void __launch_bounds__(kIcpThreads) k_icp_finish(IcpArgs a, int round) {
   __shared__ int sh_start[kIcpWarps][32], sh_incl[kIcpWarps][32];
   const unsigned FULL = 0xffffffffu;
@@ -1244,17 +1287,29 @@ __global__ void __launch_bounds__(kIcpThreads) k_icp_finish(IcpArgs a, int round
     if (item >= total) break;
     const int2 e = a.queue[item];
     const int pos = e.x & 0x7fffffff;
-    float q[3], dmax2, ds2, lim;
+    const bool bound = e.x < 0;
+    float q[3], dmax2, ds2, lim, lb2 = 0.0f;
     u64 best;
     int bj, c[3];
     bool grow;
-    queued_query(a, pos, e.y, e.x < 0, q, dmax2, ds2, best, bj, lim, c, grow);
-    if (!warp_directory(a.g, e.y, q, ds2, c, best, bj, lim, lane, sh_start[warp],
-                        sh_incl[warp])) {
+    // a query that asked for a bound gets it from the grown directory search
+    // (the rejection distance unchanged: an outlier's bound then reaches
+    // kFinishGrow times it)
+    queued_query(a, pos, e.y, false, q, dmax2, ds2, best, bj, lim, c, grow);
+    const int c_all[3] = {-2, -2, -2};
+    const bool ok = bound ? warp_directory<true>(a.g, e.y, q, dmax2, c_all, best, bj, lim, lane,
+                                                 sh_start[warp], sh_incl[warp], lb2)
+                          : warp_directory<false>(a.g, e.y, q, dmax2, c, best, bj, lim, lane,
+                                                  sh_start[warp], sh_incl[warp], lb2);
+    if (!ok) {
       // a ball spanning many directory cells (large rejection distance)
-      if (lane == 0) escalate_rings(a.g, e.y, q, ds2, best, bj, lim);
+      if (lane == 0) escalate_rings(a.g, e.y, q, dmax2, best, bj, lim);
     }
-    if (lane == 0) queued_result(a, pos, e.y, dmax2, ds2, best, grow);
+    if (lane == 0) {
+      const bool in = best != kEmptyKey;
+      a.corr[pos] = in ? a.g.prm[e.y].start + key_idx(best) : -1;
+      if (bound && ok) a.lbd[pos] = sqrtf(lb2) * (1.0f - 1e-5f);
+    }
     __syncwarp();
   }
 }
