@@ -1002,13 +1002,15 @@ __device__ __forceinline__ int pair_of(const int* off, int pairs, int v) {
 
 // p' = R p + t of the source point at sorted position pos (FP32; the same
 // operations in every kernel, so every kernel sees the same p')
-__device__ __forceinline__ void transformed_source(const IcpArgs& a, const float* Rt, int pos,
-                                                   float p[3]) {
-  const float4 sp = __ldg(a.src_sorted + pos);
+__device__ __forceinline__ void transform_point(const float* Rt, const float4& sp, float p[3]) {
   const float x = sp.x, y = sp.y, z = sp.z;
   p[0] = fmaf(Rt[0], x, fmaf(Rt[1], y, fmaf(Rt[2], z, Rt[3])));
   p[1] = fmaf(Rt[4], x, fmaf(Rt[5], y, fmaf(Rt[6], z, Rt[7])));
   p[2] = fmaf(Rt[8], x, fmaf(Rt[9], y, fmaf(Rt[10], z, Rt[11])));
+}
+__device__ __forceinline__ void transformed_source(const IcpArgs& a, const float* Rt, int pos,
+                                                   float p[3]) {
+  transform_point(Rt, __ldg(a.src_sorted + pos), p);
 }
 
 // Projective data association (Sec. 3): the target is the organised image of
@@ -1057,40 +1059,44 @@ constexpr int kWarpStage = 32;
 __global__ void __launch_bounds__(kIcpThreads, 4) k_icp_search(IcpArgs a, int round) {
   __shared__ float s_Rt[12], s_Rp[12];
   __shared__ float s_dmax2, s_move;
-  __shared__ int s_pair, s_prev;
+  __shared__ int s_prev;
   __shared__ int s_wn[kIcpWarps];
   __shared__ int s_list[kTileSrc];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tt = blockIdx.x;
   wait_previous_kernel();
   allow_next_kernel();
+  // the tile's pair and sources, and each query's certificate inputs, are
+  // loaded alongside the pair's state (one pair: no lookups)
+  const int b = pair_of(a.tile_off, a.pairs, tt);
   if (tid == 0) {
-    const int b = pair_of(a.tile_off, a.pairs, tt);
-    s_pair = b;
     s_dmax2 = a.st[b].dmax2;
     s_prev = a.st[b].has_prev && a.opt.association != CIL_ASSOC_PROJECTIVE;
     s_move = kCertMove * a.g.prm[b].cell;
   }
   if (tid < 12) {
-    const IcpPairState& S = a.st[pair_of(a.tile_off, a.pairs, tt)];
-    s_Rt[tid] = S.Rt[tid];
-    s_Rp[tid] = S.Rt_prev[tid];
+    s_Rt[tid] = a.st[b].Rt[tid];
+    s_Rp[tid] = a.st[b].Rt_prev[tid];
   }
-  __syncthreads();
-  const int b = s_pair;
-  const int tb = __ldg(a.tile_off + b);
+  const int tb = a.pairs == 1 ? 0 : __ldg(a.tile_off + b);
   const int sb = a.src_start ? __ldg(a.src_start + b) : 0;
   const int se = a.src_start ? __ldg(a.src_start + b + 1) : a.n_src1;
   const int pos = sb + (tt - tb) * kTileSrc + tid;
   const int dst_start = a.g.prm[b].start;
-  const float dmax2 = s_dmax2;
   bool todo = pos < se;
+  int j = -1;
+  float lb = 0.0f;
+  float4 sp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  if (todo) {
+    j = a.corr[pos];
+    lb = a.lbd[pos];
+    sp = __ldg(a.src_sorted + pos);
+  }
+  __syncthreads();
+  const float dmax2 = s_dmax2;
   bool want_lb = false;  // record the bound for the next round
   if (todo && s_prev) {
-    const int j = a.corr[pos];
-    const float lb = a.lbd[pos];
     {
-      const float4 sp = __ldg(a.src_sorted + pos);
       const float x = sp.x, y = sp.y, z = sp.z;
       const float* R = s_Rt;
       const float* R0 = s_Rp;
@@ -1407,11 +1413,29 @@ __device__ __forceinline__ int point_contribution(const IcpArgs& a, int b, const
   return 1;
 }
 
+// Quantities per warp in the group and round reductions.
+constexpr int kQuantPerWarp = (kIcpQ + kIcpWarps - 1) / kIcpWarps;
+
+// Compensated shuffle trees of a warp's quantities (lane 0 ends with each
+// total; lanes merged pairwise by halving offsets, in that order),
+// interleaved so that the trees' latencies overlap.
+__device__ __forceinline__ void merge_trees(KSum (&t)[kQuantPerWarp]) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int h = 0; h < kQuantPerWarp; ++h) {
+      const float s2 = __shfl_down_sync(0xffffffffu, t[h].s, off);
+      const float c2 = __shfl_down_sync(0xffffffffu, t[h].c, off);
+      t[h].merge(s2, c2);
+    }
+  }
+}
+
 // Stage three of round `round` for the tile blockIdx.x: rows, tile sums,
 // group reduction and, in the last block of a pair, the round's solve.
 __global__ void __launch_bounds__(kIcpThreads, 4) k_icp_accumulate(IcpArgs a, int round) {
   __shared__ float s_Rt[12];
-  __shared__ int s_pair, s_last, s_gid, s_g0, s_gsize;
+  __shared__ int s_last, s_gid, s_g0, s_gsize;
   __shared__ float s_c[kIcpQ][kTileSrc + 8];  // contributions per tile point; +8 spreads banks
   __shared__ float s_ps[kIcpQ][kRowChunks], s_pc[kIcpQ][kRowChunks];
   __shared__ double sm_tot[kIcpQ];
@@ -1420,32 +1444,45 @@ __global__ void __launch_bounds__(kIcpThreads, 4) k_icp_accumulate(IcpArgs a, in
   const int tt = blockIdx.x;
   wait_previous_kernel();
   allow_next_kernel();
-  if (tid == 0) {
-    s_pair = pair_of(a.tile_off, a.pairs, tt);
-    if (tt == 0) {
-      // the next round's queue counters (last used two rounds ago, whose
-      // launches have completed)
-      a.qcount[(round + 1) & 1] = 0;
-      a.qhead[(round + 1) & 1] = 0;
-    }
+  if (tid == 0 && tt == 0) {
+    // the next round's queue counters (last used two rounds ago, whose
+    // launches have completed)
+    a.qcount[(round + 1) & 1] = 0;
+    a.qhead[(round + 1) & 1] = 0;
   }
-  __syncthreads();
-  const int b = s_pair;
+  // the tile's pair and sources, each point's correspondence, source point
+  // and target point are loaded alongside the pair's transform (one pair: no
+  // lookups)
+  const int b = pair_of(a.tile_off, a.pairs, tt);
   if (tid < 12) s_Rt[tid] = a.st[b].Rt[tid];
-  __syncthreads();
-  const int tb = __ldg(a.tile_off + b);
+  const int tb = a.pairs == 1 ? 0 : __ldg(a.tile_off + b);
   const int sb = a.src_start ? __ldg(a.src_start + b) : 0;
   const int se = a.src_start ? __ldg(a.src_start + b + 1) : a.n_src1;
   const int pos = sb + (tt - tb) * kTileSrc + tid;
+  const int j = pos < se ? a.corr[pos] : -1;
+  // the tile's group (counted after the tile's partials)
+  const int gl = (tt - tb) / kIcpGroup;
+  int gid = 0, gsize = 0;
+  if (tid == 0) {
+    const int ntiles_b = (a.pairs == 1 ? a.n_tiles : __ldg(a.tile_off + b + 1)) - tb;
+    gid = a.st[b].grp_begin + gl;
+    gsize = min(kIcpGroup, ntiles_b - gl * kIcpGroup);
+  }
+  float4 sp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  float qv[3] = {0.0f, 0.0f, 0.0f};
+  if (j >= 0) {
+    sp = __ldg(a.src_sorted + pos);
+    qv[0] = __ldg(a.dst + 3 * (int64_t)j);
+    qv[1] = __ldg(a.dst + 3 * (int64_t)j + 1);
+    qv[2] = __ldg(a.dst + 3 * (int64_t)j + 2);
+  }
+  __syncthreads();
   // the thread's contribution to the round's 28 sums (zeros where there is
   // no correspondence)
   int cnt = 0;
-  const int j = pos < se ? a.corr[pos] : -1;
   if (j >= 0) {
     float p[3];
-    transformed_source(a, s_Rt, pos, p);
-    const float qv[3] = {__ldg(a.dst + 3 * (int64_t)j), __ldg(a.dst + 3 * (int64_t)j + 1),
-                         __ldg(a.dst + 3 * (int64_t)j + 2)};
+    transform_point(s_Rt, sp, p);
     cnt = point_contribution(a, b, p, qv, j, s_c, tid);
   }
   if (!cnt) {
@@ -1474,13 +1511,10 @@ __global__ void __launch_bounds__(kIcpThreads, 4) k_icp_accumulate(IcpArgs a, in
   } else if (tid == 32) {
     a.part_n[tt] = tile_cnt;
   }
-  __threadfence();
+  // the partials' writers make them visible before the group count
+  if (tid < kIcpQ || tid == 32) __threadfence();
   __syncthreads();
   if (tid == 0) {
-    const int ntiles_b = __ldg(a.tile_off + b + 1) - tb;
-    const int gl = (tt - tb) / kIcpGroup;
-    const int gid = a.st[b].grp_begin + gl;
-    const int gsize = min(kIcpGroup, ntiles_b - gl * kIcpGroup);
     const int old = atomicAdd(a.grp_done + gid, 1);
     s_last = (old == gsize - 1);
     s_gid = gid;
@@ -1495,22 +1529,25 @@ __global__ void __launch_bounds__(kIcpThreads, 4) k_icp_accumulate(IcpArgs a, in
   __threadfence();
   {
     const int gid = s_gid, g0 = s_g0, gs = s_gsize;
-    for (int q = warp; q < kIcpQ; q += kIcpWarps) {
-      KSum t;
-      t.zero();
-      if (lane < gs) {
-        t.s = __ldcg(a.part_s + (int64_t)(g0 + lane) * kIcpQ + q);
-        t.c = __ldcg(a.part_c + (int64_t)(g0 + lane) * kIcpQ + q);
-      }
+    // the warp's quantities q = warp + kIcpWarps h: all loads first, then
+    // the trees side by side (each in its fixed order)
+    KSum t[kQuantPerWarp];
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float s2 = __shfl_down_sync(0xffffffffu, t.s, off);
-        const float c2 = __shfl_down_sync(0xffffffffu, t.c, off);
-        t.merge(s2, c2);
+    for (int h = 0; h < kQuantPerWarp; ++h) {
+      const int q = warp + kIcpWarps * h;
+      t[h].zero();
+      if (q < kIcpQ && lane < gs) {
+        t[h].s = __ldcg(a.part_s + (int64_t)(g0 + lane) * kIcpQ + q);
+        t[h].c = __ldcg(a.part_c + (int64_t)(g0 + lane) * kIcpQ + q);
       }
-      if (lane == 0) {
-        a.grp_s[(int64_t)gid * kIcpQ + q] = t.s;
-        a.grp_c[(int64_t)gid * kIcpQ + q] = t.c;
+    }
+    merge_trees(t);
+#pragma unroll
+    for (int h = 0; h < kQuantPerWarp; ++h) {
+      const int q = warp + kIcpWarps * h;
+      if (lane == 0 && q < kIcpQ) {
+        a.grp_s[(int64_t)gid * kIcpQ + q] = t[h].s;
+        a.grp_c[(int64_t)gid * kIcpQ + q] = t[h].c;
       }
     }
     if (warp == kIcpWarps - 1) {
@@ -1523,7 +1560,7 @@ __global__ void __launch_bounds__(kIcpThreads, 4) k_icp_accumulate(IcpArgs a, in
     // round runs after this launch
     if (tid == 0) a.grp_done[gid] = 0;
   }
-  __threadfence();
+  if (lane == 0) __threadfence();  // the group partials' writers
   __syncthreads();
   if (tid == 0) {
     const int old = atomicAdd(&a.st[b].tiles_done, 1);
@@ -1536,18 +1573,33 @@ __global__ void __launch_bounds__(kIcpThreads, 4) k_icp_accumulate(IcpArgs a, in
   __threadfence();
   {
     const int gb = a.st[b].grp_begin, ge = gb + a.st[b].n_grp;
-    for (int q = warp; q < kIcpQ; q += kIcpWarps) {
-      KSum t;
-      t.zero();
-      for (int u = gb + lane; u < ge; u += 32)
-        t.merge(__ldcg(a.grp_s + (int64_t)u * kIcpQ + q), __ldcg(a.grp_c + (int64_t)u * kIcpQ + q));
+    KSum t[kQuantPerWarp];
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float s2 = __shfl_down_sync(0xffffffffu, t.s, off);
-        const float c2 = __shfl_down_sync(0xffffffffu, t.c, off);
-        t.merge(s2, c2);
-      }
-      if (lane == 0) sm_tot[q] = (double)t.s + (double)t.c;
+    for (int h = 0; h < kQuantPerWarp; ++h) t[h].zero();
+    // two strides of the group partials in flight at a time (a pair has few
+    // groups: 38 for a 640x480 frame)
+    for (int u = gb + lane; u < ge; u += 64) {
+      float ls[2][kQuantPerWarp], lc[2][kQuantPerWarp];
+#pragma unroll
+      for (int v = 0; v < 2; ++v)
+#pragma unroll
+        for (int h = 0; h < kQuantPerWarp; ++h) {
+          const int q = warp + kIcpWarps * h;
+          const int uu = u + 32 * v;
+          ls[v][h] = (q < kIcpQ && uu < ge) ? __ldcg(a.grp_s + (int64_t)uu * kIcpQ + q) : 0.0f;
+          lc[v][h] = (q < kIcpQ && uu < ge) ? __ldcg(a.grp_c + (int64_t)uu * kIcpQ + q) : 0.0f;
+        }
+#pragma unroll
+      for (int v = 0; v < 2; ++v)
+#pragma unroll
+        for (int h = 0; h < kQuantPerWarp; ++h)
+          if (u + 32 * v < ge) t[h].merge(ls[v][h], lc[v][h]);
+    }
+    merge_trees(t);
+#pragma unroll
+    for (int h = 0; h < kQuantPerWarp; ++h) {
+      const int q = warp + kIcpWarps * h;
+      if (lane == 0 && q < kIcpQ) sm_tot[q] = (double)t[h].s + (double)t[h].c;
     }
     if (warp == kIcpWarps - 1) {
       long long n = 0;
