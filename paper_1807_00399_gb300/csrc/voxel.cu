@@ -44,17 +44,23 @@ __global__ void __launch_bounds__(256) k_voxel_range(const float* __restrict__ x
       hi[a] = max(hi[a], c);
     }
   }
+  // warp, then block maxima; one atomic per value and block
+  __shared__ int s_m[6][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     lo[a] = (int)__reduce_max_sync(0xffffffffu, (unsigned)lo[a]);
     hi[a] = (int)__reduce_max_sync(0xffffffffu, (unsigned)hi[a]);
-  }
-  if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      atomicMax(ext + a, lo[a]);
-      atomicMax(ext + 3 + a, hi[a]);
+    if (lane == 0) {
+      s_m[a][warp] = lo[a];
+      s_m[3 + a][warp] = hi[a];
     }
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    int m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, s_m[threadIdx.x][w]);
+    atomicMax(ext + threadIdx.x, m);
   }
 }
 
@@ -139,7 +145,7 @@ extern "C" cil_status cil_voxel_downsample(const float* xyz, int64_t n, float vo
   note_launches(4);
   int* ext = ws.at<int>(o_ext);
   if (cudaMemsetAsync(ext, 0, sizeof(int) * 6, s) != cudaSuccess) return CIL_ERR_CUDA;
-  const int rblocks = std::max(1, std::min(ceil_div(n, 256), 8 * ctx->num_sms));
+  const int rblocks = std::max(1, std::min(ceil_div(n, 256), 2 * ctx->num_sms));
   k_voxel_range<<<rblocks, 256, 0, s>>>(xyz, n, voxel, ext);
   int e[6];
   if (cudaMemcpyAsync(e, ext, sizeof(e), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
