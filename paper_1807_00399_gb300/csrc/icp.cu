@@ -284,8 +284,13 @@ __device__ bool warp_block_search(const GridView& g, int cloud, const float q[3]
   return out2 * (1.0f - 1e-6f) > lim;
 }
 
-// The per-lane form of warp_directory (same cells, same result), for queues
-// long enough to give every lane its own query.
+// The per-lane form of warp_directory (the same result), for queues long
+// enough to give every lane its own query.  The directory cells meeting the
+// ball are visited in shells of growing Chebyshev distance from the query's
+// cell, and the search ends once everything outside the shells walked is
+// beyond the best distance: a first-round query (a long queue, far from its
+// neighbour at the start) finds its neighbour in the first shells and prunes
+// the rest of its ball.
 __device__ __forceinline__ bool lane_directory(const GridView& g, int cloud, const float q[3],
                                                 float dmax2, const int c[3], u64& best, int& bj,
                                                 float& lim) {
@@ -298,19 +303,36 @@ __device__ __forceinline__ bool lane_directory(const GridView& g, int cloud, con
   CellFrame fc;
   fc.load_level(P, cloud, Lc, ldexpf(P.fine, Lc));
   const float rad2 = fmaf(sqrtf(lim), 1.0f + 1e-6f, f.eps);
-  int clo[3], chi[3], blo[3], bhi[3];
+  int clo[3], chi[3], blo[3], bhi[3], cq[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     clo[a] = fc.cell_of(q[a] - rad2, a, inv_fine);
     chi[a] = fc.cell_of(q[a] + rad2, a, inv_fine);
     blo[a] = f.cell_of(q[a] - rad2, a, inv_fine);
     bhi[a] = f.cell_of(q[a] + rad2, a, inv_fine);
+    cq[a] = fc.cell_of(q[a], a, inv_fine);
   }
-  if ((chi[0] - clo[0] + 1) * (chi[1] - clo[1] + 1) * (chi[2] - clo[2] + 1) <= kDirCells) {
-    const int sh = Lc - f.level;
-    for (int Z = clo[2]; Z <= chi[2]; ++Z)
-      for (int Y = clo[1]; Y <= chi[1]; ++Y)
-        for (int X = clo[0]; X <= chi[0]; ++X) {
+  if ((chi[0] - clo[0] + 1) * (chi[1] - clo[1] + 1) * (chi[2] - clo[2] + 1) > kDirCells)
+    return false;
+  const int sh = Lc - f.level;
+  int rmax = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) rmax = max(rmax, max(cq[a] - clo[a], chi[a] - cq[a]));
+  for (int r = 0; r <= rmax; ++r) {
+    if (r > 0) {
+      const int e0[3] = {cq[0] - r + 1, cq[1] - r + 1, cq[2] - r + 1};
+      const int e1[3] = {cq[0] + r - 1, cq[1] + r - 1, cq[2] + r - 1};
+      if (fc.unexplored_d2(q, e0, e1) * (1.0f - 1e-6f) > lim) break;
+    }
+    // the shell's cells inside the box: rows on its z / y faces whole, the
+    // others at their two x ends
+    for (int Z = max(cq[2] - r, clo[2]); Z <= min(cq[2] + r, chi[2]); ++Z)
+      for (int Y = max(cq[1] - r, clo[1]); Y <= min(cq[1] + r, chi[1]); ++Y) {
+        const bool face = Z == cq[2] - r || Z == cq[2] + r || Y == cq[1] - r || Y == cq[1] + r;
+        const int step = face ? 1 : max(2 * r, 1);
+        for (int X = face ? max(cq[0] - r, clo[0]) : cq[0] - r;
+             X <= (face ? min(cq[0] + r, chi[0]) : cq[0] + r); X += step) {
+          if (X < clo[0] || X > chi[0]) continue;
           const int C3[3] = {X, Y, Z};
           if (fc.range_d2(q, C3, C3) * (1.0f - 1e-6f) > lim) continue;
           if (!cell_lookup(g, cell_key(Lc, cloud, X, Y, Z), s, n)) continue;
@@ -334,9 +356,9 @@ __device__ __forceinline__ bool lane_directory(const GridView& g, int cloud, con
                   scan_cell(g, s2, n2, q, dmax2, best, bj, lim);
               }
         }
-    return true;  // every cell meeting the ball was searched
+      }
   }
-  return false;
+  return true;  // every cell meeting the ball was searched or is beyond the best
 }
 
 // Warp-wide minimum of the lanes' (key, position) candidates merged into the
