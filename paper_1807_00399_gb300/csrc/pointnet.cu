@@ -552,16 +552,43 @@ __global__ void __launch_bounds__(256, 1) k_pn_encode_bwd(
     if (z1 > 0.0f) pos1 |= 1ull << k;
     S.a1[c][k] = __float2bfloat16_rn(fmaxf(z1, 0.0f));
   }
-  // Z2 = W2b A1b + b2 ; dW3 row c = g * A2b ; dZ2 = g * W3b[c] * (Z2 > 0)
+  // Z2 = W2b A1b + b2 ; dW3 row c = g * A2b ; dZ2 = g * W3b[c] * (Z2 > 0).
+  // Four outputs at a time (each still summed over k in order): four
+  // independent FMA chains, one shared-memory read of A1 for four of them.
+  constexpr int kOB = 4;
 #pragma unroll 1
-  for (int o = 0; o < kH2; ++o) {
-    float s = prm[oB2 + o];
-#pragma unroll 8
-    for (int k = 0; k < kH1; ++k)
-      s = fmaf(__bfloat162float(w2b[o * kH1 + k]), __bfloat162float(S.a1[c][k]), s);
-    const float a2 = __bfloat162float(__float2bfloat16_rn(fmaxf(s, 0.0f)));
-    out[oW3 + c * kH2 + o] = gch * a2;
-    S.g2[c][o] = s > 0.0f ? gch * __bfloat162float(w3b[c * kH2 + o]) : 0.0f;
+  for (int o0 = 0; o0 < kH2; o0 += kOB) {
+    float sv[kOB];
+#pragma unroll
+    for (int u = 0; u < kOB; ++u) sv[u] = prm[oB2 + o0 + u];
+#pragma unroll 2
+    for (int k0 = 0; k0 < kH1; k0 += 8) {
+      // 8 weights of each row in one 16-byte load (rows of 64 bf16 are
+      // 128-byte aligned)
+      uint4 wv[kOB];
+#pragma unroll
+      for (int u = 0; u < kOB; ++u)
+        wv[u] = __ldg(reinterpret_cast<const uint4*>(w2b + (o0 + u) * kH1 + k0));
+#pragma unroll
+      for (int h = 0; h < 8; ++h) {
+        const float av = __bfloat162float(S.a1[c][k0 + h]);
+#pragma unroll
+        for (int u = 0; u < kOB; ++u) {
+          const __nv_bfloat16* w8 = reinterpret_cast<const __nv_bfloat16*>(&wv[u]);
+          sv[u] = fmaf(__bfloat162float(w8[h]), av, sv[u]);
+        }
+      }
+    }
+    float4 w3o;
+    float* w3p = &w3o.x;
+#pragma unroll
+    for (int u = 0; u < kOB; ++u) {
+      const float sz = sv[u];
+      const float a2 = __bfloat162float(__float2bfloat16_rn(fmaxf(sz, 0.0f)));
+      w3p[u] = gch * a2;
+      S.g2[c][o0 + u] = sz > 0.0f ? gch * __bfloat162float(w3b[c * kH2 + o0 + u]) : 0.0f;
+    }
+    *reinterpret_cast<float4*>(out + oW3 + c * kH2 + o0) = w3o;
   }
   out[oB3 + c] = gch;
   // dA1 = W2b^T dZ2, dZ1 = dA1 * (Z1 > 0)
@@ -572,17 +599,31 @@ __global__ void __launch_bounds__(256, 1) k_pn_encode_bwd(
   for (int o = 0; o < kH2; ++o) {
     const float gv = S.g2[c][o];
 #pragma unroll
-    for (int k = 0; k < kH1; ++k) dz1[k] = fmaf(__bfloat162float(w2b[o * kH1 + k]), gv, dz1[k]);
+    for (int k0 = 0; k0 < kH1; k0 += 8) {
+      const uint4 wv = __ldg(reinterpret_cast<const uint4*>(w2b + o * kH1 + k0));
+      const __nv_bfloat16* w8 = reinterpret_cast<const __nv_bfloat16*>(&wv);
+#pragma unroll
+      for (int h = 0; h < 8; ++h) dz1[k0 + h] = fmaf(__bfloat162float(w8[h]), gv, dz1[k0 + h]);
+    }
   }
 #pragma unroll
   for (int k = 0; k < kH1; ++k) dz1[k] = ((pos1 >> k) & 1ull) ? dz1[k] : 0.0f;
   __syncthreads();
   // dW2[o][k] = sum_c dZ2[c][o] A1[c][k],  db2[o] = sum_c dZ2[c][o]  (c in order)
-  for (int e = threadIdx.x; e < kH2 * kH1; e += 256) {
-    const int o = e / kH1, k = e % kH1;
-    float s = 0.0f;
-    for (int cc = 0; cc < kH3; ++cc) s = fmaf(S.g2[cc][o], __bfloat162float(S.a1[cc][k]), s);
-    out[oW2 + e] = s;
+  // four elements e, e + 256, ... at a time (each summed over channels in
+  // order): independent chains
+  static_assert((kH2 * kH1) % (4 * 256) == 0, "dW2 blocking");
+  for (int e0 = threadIdx.x; e0 < kH2 * kH1; e0 += 4 * 256) {
+    float sv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int cc = 0; cc < kH3; ++cc) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + 256 * u, o = e / kH1, k = e % kH1;
+        sv[u] = fmaf(S.g2[cc][o], __bfloat162float(S.a1[cc][k]), sv[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) out[oW2 + e0 + 256 * u] = sv[u];
   }
   if (threadIdx.x < kH2) {
     float s = 0.0f;
