@@ -121,10 +121,9 @@ cil_status cil_knn_ex(const float *ref, int64_t n_ref, const float *qry, int64_t
  *   - n_ref and n_qry must each be <= 32768, else CIL_ERR_CAPACITY (nothing is
  *     launched);
  *   - the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current: make it before any
- *     stream capture; the address is kept for the life of the process, so
- *     after a cudaDeviceReset of that device this entry point must not be
- *     called again;
+ *     (cudaGetSymbolAddress) with that device current; the address is kept
+ *     for the life of the process, so after a cudaDeviceReset of that device
+ *     this entry point must not be called again;
  *   - every call shares the one array: calls that overlap on the GPU race and
  *     corrupt each other's results; each call resets the state it needs;
  *   - the call synchronises `stream` and returns a device-detected error
