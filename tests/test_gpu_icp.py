@@ -188,6 +188,29 @@ def test_association_every_search_stage(dmax):
     assert abs(rg["n_inliers"] - o["n_inliers"]) <= 2
 
 
+def test_long_queue_lane_search_matches_oracle():
+    """A long first-round queue, one query per lane (more than 32 queued
+    queries per warp of the finish): a 200k-point wavy surface with the
+    source lifted 2-4 cm, so that nearly every query's ball leaves its 3x3x3
+    block; each lane walks the directory cells of its ball in shells and stops
+    once the rest is beyond its best distance.  The final association pass
+    (iters = 0) and three rounds against the oracle."""
+    p = synth.surface_pair(5, n=200_000)
+    rng = np.random.default_rng(5)
+    src = p.source + np.column_stack([np.zeros((len(p.source), 2)),
+                                      rng.uniform(0.02, 0.04, len(p.source))]).astype(np.float32)
+    on, _, _ = oracle.normals(p.target, 10, p.viewpoint, method="kdtree")
+    nrm = on.astype(np.float32)
+    Tg, rg = _gpu_icp(src, p.target, nrm, iters=0, max_corr_dist=0.05)
+    o = oracle.icp(src, p.target, nrm, iters=0, max_corr_dist=0.05, method="kdtree")
+    assert abs(rg["n_inliers"] - o["n_inliers"]) <= 2
+    assert abs(rg["rmse"] - o["rmse"]) <= 1e-5 * o["rmse"]
+    Tg, rg = _gpu_icp(src, p.target, nrm, iters=3, max_corr_dist=0.05)
+    o = oracle.icp(src, p.target, nrm, iters=3, max_corr_dist=0.05, method="kdtree")
+    _assert_same(Tg, o["T"], p.target)
+    assert abs(rg["n_inliers"] - o["n_inliers"]) <= 2
+
+
 def test_association_large_rejection_distance(surface):
     """A rejection distance of half the cloud: for points lifted 0.6 above
     the surface the directory of 4x cells is too large and the search takes
