@@ -1435,6 +1435,27 @@ __device__ __forceinline__ int point_contribution(const IcpArgs& a, int b, const
   return 1;
 }
 
+// The round's totals (every thread of the block, after the reduction):
+// recorded when asked, then the solve and pose update by warp 0.
+__device__ __forceinline__ void close_pair_round(const IcpArgs& a, int round, int b,
+                                                 const double* sm_tot, const long long& sm_cnt) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __syncthreads();
+  if (a.opt.sums && tid <= kIcpQ) {
+    double* o = a.opt.sums + ((int64_t)b * a.rounds + round) * (kIcpQ + 1);
+    o[tid] = tid < kIcpQ ? sm_tot[tid] : (double)sm_cnt;
+  }
+  if (warp == 0) {
+    IcpPairState& S = a.st[b];
+    close_round_warp(S, sm_tot, sm_cnt, round == a.rounds - 1, a.opt.metric, lane);
+    if (lane == 0) S.tiles_done = 0;
+  }
+}
+
+// A pair of at most this many tiles is reduced in one level (its last tile
+// block reads the tile partials directly); more, in groups of kIcpGroup.
+constexpr int kOneLevelTiles = 256;
+
 // Quantities per warp in the group and round reductions.
 constexpr int kQuantPerWarp = (kIcpQ + kIcpWarps - 1) / kIcpWarps;
 
@@ -1457,7 +1478,7 @@ __device__ __forceinline__ void merge_trees(KSum (&t)[kQuantPerWarp]) {
 // group reduction and, in the last block of a pair, the round's solve.
 __global__ void __launch_bounds__(kIcpThreads, 4) k_icp_accumulate(IcpArgs a, int round) {
   __shared__ float s_Rt[12];
-  __shared__ int s_last, s_gid, s_g0, s_gsize;
+  __shared__ int s_last, s_gid, s_g0, s_gsize, s_one;
   __shared__ float s_c[kIcpQ][kTileSrc + 8];  // contributions per tile point; +8 spreads banks
   __shared__ float s_ps[kIcpQ][kRowChunks], s_pc[kIcpQ][kRowChunks];
   __shared__ double sm_tot[kIcpQ];
@@ -1484,9 +1505,9 @@ __global__ void __launch_bounds__(kIcpThreads, 4) k_icp_accumulate(IcpArgs a, in
   const int j = pos < se ? a.corr[pos] : -1;
   // the tile's group (counted after the tile's partials)
   const int gl = (tt - tb) / kIcpGroup;
-  int gid = 0, gsize = 0;
+  int gid = 0, gsize = 0, ntiles_b = 0;
   if (tid == 0) {
-    const int ntiles_b = (a.pairs == 1 ? a.n_tiles : __ldg(a.tile_off + b + 1)) - tb;
+    ntiles_b = (a.pairs == 1 ? a.n_tiles : __ldg(a.tile_off + b + 1)) - tb;
     gid = a.st[b].grp_begin + gl;
     gsize = min(kIcpGroup, ntiles_b - gl * kIcpGroup);
   }
@@ -1537,14 +1558,63 @@ __global__ void __launch_bounds__(kIcpThreads, 4) k_icp_accumulate(IcpArgs a, in
   if (tid < kIcpQ || tid == 32) __threadfence();
   __syncthreads();
   if (tid == 0) {
-    const int old = atomicAdd(a.grp_done + gid, 1);
-    s_last = (old == gsize - 1);
-    s_gid = gid;
-    s_g0 = tb + gl * kIcpGroup;
-    s_gsize = gsize;
+    s_one = ntiles_b <= kOneLevelTiles;
+    if (s_one) {
+      // few tiles: the pair's last tile block reduces the tiles directly
+      const int old = atomicAdd(&a.st[b].tiles_done, 1);
+      s_last = (old == ntiles_b - 1);
+      s_g0 = tb;
+      s_gsize = ntiles_b;
+    } else {
+      const int old = atomicAdd(a.grp_done + gid, 1);
+      s_last = (old == gsize - 1);
+      s_gid = gid;
+      s_g0 = tb + gl * kIcpGroup;
+      s_gsize = gsize;
+    }
   }
   __syncthreads();
   if (!s_last) return;
+  if (s_one) {
+    // ---- the pair's tiles in order: lane-strided, then the shuffle trees ----
+    __threadfence();
+    const int t0 = s_g0, nt = s_gsize;
+    KSum t[kQuantPerWarp];
+#pragma unroll
+    for (int h = 0; h < kQuantPerWarp; ++h) t[h].zero();
+    for (int u = lane; u < nt; u += 64) {
+      float ls[2][kQuantPerWarp], lc[2][kQuantPerWarp];
+#pragma unroll
+      for (int v = 0; v < 2; ++v)
+#pragma unroll
+        for (int h = 0; h < kQuantPerWarp; ++h) {
+          const int q = warp + kIcpWarps * h;
+          const int uu = u + 32 * v;
+          ls[v][h] = (q < kIcpQ && uu < nt) ? __ldcg(a.part_s + (int64_t)(t0 + uu) * kIcpQ + q) : 0.0f;
+          lc[v][h] = (q < kIcpQ && uu < nt) ? __ldcg(a.part_c + (int64_t)(t0 + uu) * kIcpQ + q) : 0.0f;
+        }
+#pragma unroll
+      for (int v = 0; v < 2; ++v)
+#pragma unroll
+        for (int h = 0; h < kQuantPerWarp; ++h)
+          if (u + 32 * v < nt) t[h].merge(ls[v][h], lc[v][h]);
+    }
+    merge_trees(t);
+#pragma unroll
+    for (int h = 0; h < kQuantPerWarp; ++h) {
+      const int q = warp + kIcpWarps * h;
+      if (lane == 0 && q < kIcpQ) sm_tot[q] = (double)t[h].s + (double)t[h].c;
+    }
+    if (warp == kIcpWarps - 1) {
+      long long n = 0;
+      for (int u = lane; u < nt; u += 32) n += __ldcg(a.part_n + t0 + u);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) n += __shfl_down_sync(0xffffffffu, n, off);
+      if (lane == 0) sm_cnt = n;
+    }
+    close_pair_round(a, round, b, sm_tot, sm_cnt);
+    return;
+  }
 
   // ---- this block reduces its tile group: tile u of the group in lane u,
   // a fixed compensated shuffle tree ----
@@ -1631,16 +1701,7 @@ __global__ void __launch_bounds__(kIcpThreads, 4) k_icp_accumulate(IcpArgs a, in
       if (lane == 0) sm_cnt = n;
     }
   }
-  __syncthreads();
-  if (a.opt.sums && tid <= kIcpQ) {
-    double* o = a.opt.sums + ((int64_t)b * a.rounds + round) * (kIcpQ + 1);
-    o[tid] = tid < kIcpQ ? sm_tot[tid] : (double)sm_cnt;
-  }
-  if (warp == 0) {
-    IcpPairState& S = a.st[b];
-    close_round_warp(S, sm_tot, sm_cnt, round == a.rounds - 1, a.opt.metric, lane);
-    if (lane == 0) S.tiles_done = 0;
-  }
+  close_pair_round(a, round, b, sm_tot, sm_cnt);
 }
 
 __global__ void k_icp_export(const IcpPairState* st, int pairs, double* T_out,
