@@ -211,6 +211,27 @@ def test_long_queue_lane_search_matches_oracle():
     assert abs(rg["n_inliers"] - o["n_inliers"]) <= 2
 
 
+def test_rigid_motion_equivariant(surface):
+    """Moving both clouds by a rigid motion M (and the normals by its
+    rotation) conjugates the result: T' = M T M^-1, within the parity bar
+    (the moved inputs are rounded to FP32 again)."""
+    p, nrm = surface
+    rng = np.random.default_rng(41)
+    a = rng.normal(size=3)
+    a /= np.linalg.norm(a)
+    th = 0.7
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    R = np.eye(3) + np.sin(th) * K + (1 - np.cos(th)) * K @ K
+    M = np.eye(4)
+    M[:3, :3] = R
+    M[:3, 3] = [0.3, -0.2, 0.5]
+    mv = lambda x: (x.astype(np.float64) @ R.T + M[:3, 3]).astype(np.float32)  # noqa: E731
+    T, _ = _gpu_icp(p.source, p.target, nrm, iters=20, max_corr_dist=0.1)
+    Tm, _ = _gpu_icp(mv(p.source), mv(p.target), (nrm.astype(np.float64) @ R.T).astype(np.float32),
+                     iters=20, max_corr_dist=0.1)
+    _assert_same(Tm, M @ T @ np.linalg.inv(M), mv(p.target))
+
+
 def test_association_large_rejection_distance(surface):
     """A rejection distance of half the cloud: for points lifted 0.6 above
     the surface the directory of 4x cells is too large and the search takes

@@ -179,3 +179,20 @@ def test_staged_normals_and_batch_bitwise_equal():
         out.append((T.clone(), nrm.clone()))
         h.close()
     assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+
+
+def test_reference_permutation_equivariant():
+    """Permuting the reference points permutes the returned indices and
+    leaves the distances unchanged: with the reference points in another
+    order (another Morton-sort tie order inside each cell, another index
+    tie-break), every row's d2 is the same bit for bit and, in rows without
+    equal distances, the indices map through the permutation."""
+    ref = synth.surface_pair(21, n=20_000).target
+    qry = _cube(22, 3_000, scale=1.2)
+    perm = np.random.default_rng(23).permutation(len(ref))
+    gi, gd = _gpu_knn(ref, qry, 10)
+    pi, pd = _gpu_knn(ref[perm], qry, 10)
+    assert np.array_equal(gd, pd)
+    no_ties = np.all(np.diff(gd, axis=1) > 0, axis=1)
+    assert no_ties.mean() > 0.9
+    assert np.array_equal(perm[pi[no_ties]], gi[no_ties])

@@ -110,3 +110,16 @@ def test_deterministic():
     a = _gpu_normals(p.target, 10, p.viewpoint)
     b = _gpu_normals(p.target, 10, p.viewpoint)
     assert np.array_equal(a[0], b[0], equal_nan=True) and np.array_equal(a[1], b[1], equal_nan=True)
+
+
+def test_permutation_equivariant():
+    """Normals of permuted points are the permuted normals (the neighbourhood
+    of each point does not depend on the order the points come in)."""
+    p = synth.surface_pair(31, n=20_000).target
+    perm = np.random.default_rng(32).permutation(len(p))
+    vp = (0.0, 0.0, 10.0)
+    gn, gc = _gpu_normals(p, 10, vp)
+    pn, pc = _gpu_normals(p[perm], 10, vp)
+    fin = np.isfinite(gn).all(axis=1)
+    assert np.all(angle_unsigned(pn[fin], gn[perm][fin]) <= 1e-6)
+    np.testing.assert_allclose(pc, gc[perm], atol=1e-7, rtol=0)
