@@ -1001,17 +1001,8 @@ __global__ void k_icp_setup(IcpPairState* st, int pairs, const int* src_start, i
 
 constexpr int kRowChunks = 8;  // chunks of a tile's rows summed in parallel
 
-__device__ __forceinline__ int pair_of_tile(const int* tile_off, int pairs, int tt) {
-  int lo = 0, hi = pairs;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (__ldg(tile_off + mid) <= tt) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
-
-
+// the pair of tile (or point) v: the last entry of the prefix off[0..pairs)
+// that is <= v (no lookup for one pair)
 __device__ __forceinline__ int pair_of(const int* off, int pairs, int v) {
   int lo = 0, hi = pairs;
   while (hi - lo > 1) {
